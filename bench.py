@@ -1,0 +1,351 @@
+"""Benchmark of the LPP projected-tensor multipole estimator on GB300.
+
+One step = one complete estimate (sky frames, shears and harmonic weights; CIC/TSC
+assignment with interlacing; 3D FFTs; k-space contraction; FP64 shell sums;
+normalisation and shot noise) of the polar-cap survey workload: 512^3 grid, L = 4000
+Mpc/h, 1.5M shape galaxies, 15M randoms, TSC + interlacing, FP32 grids / FP64 sums,
+all ten moment slots (cross L=2,4,6; plus l=0,2,4; minus L=4,6,8; density monopole).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lpp|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank times an independent mock
+(seed + rank) of the same size: the path shards by catalogue with no exchange.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LPP tensor-multipole estimates/sec at 512^3; templates/sec surrogate vs plain"
+UNIT = "estimates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lpp", choices=["lpp", "reference"])
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--data", type=int, default=1_500_000)
+    ap.add_argument("--randoms", type=int, default=15_000_000)
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(args, seed):
+    from paper_2202_11839_gb300 import synthetic as S
+    return S.workload_survey(n_data=args.data, n_rand=args.randoms, n=args.n, seed=seed)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle timing
+def oracle_sample(wl, nfields_estimate: int, ns: int = 128):
+    """Time the oracle on a bounded sample of the workload and scale to one estimate.
+
+    Sample: one Cartesian field transform of the oracle (TSC, both interlaced sub-grids,
+    two FFTs, window deconvolution) on an ns^3 grid over the same box for the first
+    count * (ns/n)^3 shape galaxies, i.e. the same galaxies per cell.  The FFT part is
+    scaled by (n/ns)^3 log(n^3)/log(ns^3), the assignment part by the particle ratio, to
+    one transform of the full catalogue on the n^3 grid; an estimate is nfields_estimate
+    such transforms plus one of the randoms.  Returns (estimates/s, seconds, description).
+    """
+    from oracle import lpp_oracle as O
+    shp = wl.shapes
+    ratio = (wl.n / ns) ** 3
+    m = max(1, int(shp.count / ratio))
+    pos = shp.pos[:, :m].astype(np.float64)
+    vals = np.asarray(shp.shape[0, :m], dtype=np.float64)
+    t0 = time.perf_counter()
+    mg = O.ModeGrid(ns, wl.box)
+    st0 = O.assignment_stencil(pos, ns, wl.box, wl.origin, wl.scheme, 0.0)
+    st1 = O.assignment_stencil(pos, ns, wl.box, wl.origin, wl.scheme, 0.5)
+    g0 = O.grid_from_stencil(st0, vals, ns)
+    g1 = O.grid_from_stencil(st1, vals, ns)
+    t1 = time.perf_counter()
+    inv_w = 1.0 / O.window_compensation(mg, wl.scheme)
+    phase = np.exp(-1j * math.pi * (mg.nx + mg.ny + mg.nz) / ns)
+    f = 0.5 * (np.fft.fftn(g0) + phase * np.fft.fftn(g1)) * inv_w
+    t2 = time.perf_counter()
+    del f
+    t_assign = (t1 - t0) / m                                        # per particle
+    t_fft = (t2 - t1) * ratio * math.log(wl.n ** 3) / math.log(ns ** 3)
+    n_rand = wl.randoms.count if wl.randoms is not None else 0
+    t_field = t_fft + t_assign * shp.count
+    t_est = nfields_estimate * t_field + (t_fft + t_assign * n_rand)
+    work = t2 - t0
+    desc = (f"one oracle field transform on a {ns}^3 grid with {m} of {shp.count} shape galaxies "
+            f"({work:.2f} s), scaled to {wl.n}^3 and the full catalogue, times {nfields_estimate} Cartesian "
+            f"field transforms plus one of the {n_rand} randoms (numpy/pocketfft, 1 thread)")
+    return 1.0 / t_est, work, desc
+
+
+def oracle_field_count():
+    """Cartesian field transforms the oracle performs per estimate (all moments, cross E+B)."""
+    from oracle import lpp_oracle as O
+    sym2, sym4 = len(O.sym_index_sets(2)), len(O.sym_index_sets(4))
+    cnt = 0
+    for L in (2, 4, 6):
+        q = O.reduced_assoc_legendre(2, L)
+        cnt += sym2 * sum(len(O.monomials(p)) for p, c in enumerate(q) if c != 0)
+    for l in (0, 2, 4):
+        q = O.legendre_coeffs(l)
+        cnt += sum(len(O.monomials(p)) for p, c in enumerate(q) if c != 0)
+    for L in (4, 6, 8):
+        q = O.reduced_assoc_legendre(4, L)
+        cnt += sym4 * sum(len(O.monomials(p)) for p, c in enumerate(q) if c != 0)
+    return cnt + 3   # gamma, gamma* and the density partner
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    wl = workload(args, seed=0)
+    nf = oracle_field_count()
+    vals, works, desc = [], [], ""
+    for i in range(args.warmup + args.steps):
+        v, w, desc = oracle_sample(wl, nf)
+        if i >= args.warmup:
+            vals.append(v)
+            works.append(w)
+    v = statistics.median(vals)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "n": wl.n, "box": wl.box, "shape_galaxies": wl.shapes.count,
+                   "randoms": wl.randoms.count if wl.randoms is not None else 0, "scheme": "tsc", "interlace": True},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------- GPU arm
+def run_lpp(args):
+    import torch
+
+    from paper_2202_11839_gb300 import lpp as L
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    L.load_library()
+    wl = workload(args, seed=rank)
+    shp, rnd = wl.shapes, wl.randoms
+    tt = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    d_pos, d_shape, d_rpos, d_rnbar = tt(shp.pos), tt(shp.shape), tt(rnd.pos), tt(rnd.nbar)
+    common = dict(origin=wl.origin, observer=wl.observer, pole=wl.pole, scheme=L.LPP_TSC, interlace=True,
+                  compensate=True, precision=L.LPP_FP32, moments=L.LPP_WANT_ALL, max_shapes=shp.count,
+                  max_randoms=rnd.count, batch=args.batch)
+    plan = L.Plan(wl.n, wl.box, wl.k_edges, **common)
+    plan.assign(L.LPP_SHAPES, d_pos, None, None, d_shape, L.LPP_SHAPE_TENSOR6)
+    plan.assign(L.LPP_RANDOMS, d_rpos, None, d_rnbar)
+    stream = plan.stream
+    for _ in range(args.warmup):
+        est = plan.multipoles()
+    assert np.all(np.isfinite(est.p)), "non-finite estimate"
+    plan.set_timing(True)
+    clocks = ClockSampler(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = {k: {"ms": 0.0, "launches": 0, "bytes": 0.0} for k in L.KERNEL_KINDS}
+    for _ in range(args.steps):
+        est = plan.multipoles()
+        for k, v in plan.kernel_stats().items():
+            for f in ("ms", "launches", "bytes"):
+                stats[k][f] += v[f]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if pg:
+        t = torch.tensor([ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    plan.set_timing(False)
+    value = world * args.steps / (ms / 1000.0)
+    n_fields = plan.field_count()
+
+    # dominant kernel and its roofline
+    hbm, peak_src = measured_peaks()
+    dom = max((k for k in stats if k != "other"), key=lambda k: stats[k]["ms"])
+    d = stats[dom]
+    avg_s = d["ms"] / max(d["launches"], 1) / 1000.0
+    bytes_per_launch = d["bytes"] / max(d["launches"], 1)
+    achieved = bytes_per_launch / avg_s / 1e9 if avg_s > 0 else 0.0
+    kern = {k: {"ms_per_step": round(v["ms"] / args.steps, 3), "launches_per_step": v["launches"] // args.steps,
+                "gbs": round(v["bytes"] / (v["ms"] / 1000.0) / 1e9, 1) if v["ms"] > 0 else None}
+            for k, v in stats.items()}
+    launches = sum(v["launches"] for v in stats.values())
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        del plan
+        torch.cuda.empty_cache()
+        hplan = L.Plan(wl.n, wl.box, wl.k_edges, host_inputs=True, **common)
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory().numpy()
+        h_pos, h_shape, h_rpos, h_rnbar = pin(shp.pos), pin(shp.shape), pin(rnd.pos), pin(rnd.nbar)
+        h2d = (h_pos.nbytes + h_shape.nbytes + h_rpos.nbytes + h_rnbar.nbytes)
+        # FP64 shell sums of every channel and the two partner monopoles, the sums and the error flag
+        d2h = (n_fields - 1) * (len(wl.k_edges) - 1) * 2 * 8 + 8 * 8 + 4
+        for _ in range(1):
+            hplan.assign(L.LPP_SHAPES, h_pos, None, None, h_shape, L.LPP_SHAPE_TENSOR6)
+            hplan.assign(L.LPP_RANDOMS, h_rpos, None, h_rnbar)
+            hplan.multipoles()
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hplan.assign(L.LPP_SHAPES, h_pos, None, None, h_shape, L.LPP_SHAPE_TENSOR6)
+            hplan.assign(L.LPP_RANDOMS, h_rpos, None, h_rnbar)
+            hplan.multipoles()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if pg:
+            t = torch.tensor([te], device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * args.steps / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+        del hplan
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        v, work, desc = oracle_sample(wl, oracle_field_count())
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        with open(prof) as f:
+            tr = json.load(f)
+        if tr.get("kernel") == dom and tr.get("workload") == wl.name:
+            traffic = tr.get("bytes_per_launch")
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "n": wl.n, "box": wl.box, "shape_galaxies": shp.count,
+                   "randoms": rnd.count, "scheme": "tsc", "interlace": True, "fields": n_fields,
+                   "k_bins": len(wl.k_edges) - 1, "k_max": float(wl.k_edges[-1]),
+                   "l2": "inputs larger than L2 (each grid 1 GiB)", "parallelism": f"replicas{world}"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_source": peak_src, "traffic": traffic,
+                     "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_s * 1000.0},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "kernels": kern,
+    }
+    print(json.dumps(out), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_lpp(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * lpp.h -- C ABI of the GB300 LPP projected-tensor multipole library (liblpp.so).
+ *
+ * The library measures the multipoles of the power spectrum of a projected rank-2
+ * tensor field (galaxy shapes) with the local-plane-parallel (LPP) FFT estimators of
+ * Kurita & Takada (2022), "Analysis method for 3D power spectrum of projected tensor
+ * fields with fast estimator and window convolution modelling":
+ *
+ *   cross  P^(L)_gd, L = 2,4,6   Sec. 3.1.2, Eqs. lpp_estimator_cross_Xiij, def_of_Xiij
+ *   plus   P^(l)_+,  l = 0,2,4   Eq. lpp_estimator_auto_+ (Appendix B)
+ *   minus  P^(L)_-,  L = 4,6,8   Eqs. lpp_estimator_auto_-, def_of_Xiijkl (Appendix B)
+ *   density monopole P^(0)_dd    Eq. lpp_dens_app with l = 0
+ *
+ * The shear of each galaxy is gamma = e_ij(x) s_ij (Eq. gamma_def), with
+ * e_ij = e+_i e+_j and e+ = (e_theta + i e_phi)/sqrt(2) (Eqs. def_of_eij_+2,
+ * def_polarization_vector) in the sky frame about a plan pole p:
+ * e_phi = unit(p x xhat), e_theta = e_phi x xhat (for p = z this is the frame of
+ * the rotation S(d), Eq. def_standard_rotation).
+ *
+ * Conventions shared by every entry point:
+ *  - All device work runs asynchronously on the plan's stream; lpp_multipoles
+ *    synchronises that stream before it writes host outputs.
+ *  - The library never allocates device memory: the caller supplies one device
+ *    workspace of lpp_plan_workspace_size() bytes (e.g. a torch uint8 tensor).
+ *  - Every function returns an lpp_status; none aborts or throws.  On an error the
+ *    host outputs are left untouched.  After LPP_ERR_CUDA the plan must be destroyed.
+ *  - Grids are cubic: n^3 nodes over a box of side `box`, n a power of two in
+ *    [8, 1024].  Particles must lie in [origin, origin + box] on every axis.
+ */
+#ifndef LPP_H
+#define LPP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LPP_OK = 0,
+    LPP_ERR_INVALID_ARG = 1,  /* bad descriptor, size, pointer or flag                         */
+    LPP_ERR_CUDA = 2,         /* a CUDA runtime call failed; destroy the plan                  */
+    LPP_ERR_NOT_READY = 3,    /* workspace or required catalogue not supplied yet              */
+    LPP_ERR_WORKSPACE = 4,    /* workspace smaller than lpp_plan_workspace_size()              */
+    LPP_ERR_UNSUPPORTED = 5,  /* grid size or option combination not built                      */
+    LPP_ERR_DOMAIN = 6        /* a particle lies outside the box, on the observer or the pole  */
+} lpp_status;
+
+/* assignment schemes: the exponent p of the window sinc^p */
+enum { LPP_CIC = 2, LPP_TSC = 3 };
+/* arithmetic of grids, FFTs and per-mode products (shell sums are always FP64) */
+enum { LPP_FP32 = 0, LPP_FP64 = 1 };
+/* line of sight used for the projection / for the estimator:
+ * LOCAL = unit(x - observer) per galaxy (case (a) of Sec. 4.2),
+ * GLOBAL = the plan's los_global for every galaxy (cases (b), (c)). */
+enum { LPP_LOS_LOCAL = 0, LPP_LOS_GLOBAL = 1 };
+/* catalogue roles for lpp_assign */
+enum { LPP_SHAPES = 0, LPP_DENSITY = 1, LPP_RANDOMS = 2 };
+/* shape inputs */
+enum { LPP_SHAPE_NONE = 0, LPP_SHAPE_GAMMA12 = 1, LPP_SHAPE_TENSOR6 = 2 };
+
+/* Moment slots of every output array, in this order. */
+#define LPP_N_MOMENTS 10
+enum {
+    LPP_MOM_DD0 = 0,
+    LPP_MOM_CROSS2 = 1, LPP_MOM_CROSS4 = 2, LPP_MOM_CROSS6 = 3,
+    LPP_MOM_PLUS0 = 4, LPP_MOM_PLUS2 = 5, LPP_MOM_PLUS4 = 6,
+    LPP_MOM_MINUS4 = 7, LPP_MOM_MINUS6 = 8, LPP_MOM_MINUS8 = 9
+};
+/* bitmask of requested moments: bit i enables slot i; LPP_WANT_CROSS_B adds the
+ * B (imaginary) part of the cross moments, which costs 2L+1 extra fields per L. */
+#define LPP_WANT_ALL 0x3FFu
+#define LPP_WANT_CROSS_B (1u << 10)
+
+typedef struct lpp_plan_s* lpp_plan_t;
+
+typedef struct {
+    int n;                   /* grid side, power of two, 8..1024                               */
+    double box;              /* side of the cubic box                                          */
+    double origin[3];        /* lower corner of the box                                        */
+    double observer[3];      /* observer position (LOCAL line of sight)                        */
+    double pole[3];          /* pole p of the sky frame; must not be parallel to any LOS       */
+    int scheme;              /* LPP_CIC or LPP_TSC                                             */
+    int interlace;           /* 1: average with the grid shifted by half a cell (all axes)     */
+    int compensate;          /* 1: divide by the assignment window prod sinc^p                 */
+    int precision;           /* LPP_FP32 or LPP_FP64                                           */
+    int los_proj;            /* LPP_LOS_LOCAL / GLOBAL for gamma = e_ij(x) s_ij                 */
+    int los_est;             /* LPP_LOS_LOCAL / GLOBAL inside the estimator kernels            */
+    double los_global[3];    /* global line of sight (normalised by the library)               */
+    unsigned moments;        /* LPP_WANT_* bitmask                                             */
+    int n_bins;              /* number of |k| shells, 1..256                                   */
+    const double* k_edges;   /* host, n_bins+1 increasing edges; copied at create              */
+    double norm_override;    /* > 0: use this I for every moment instead of the estimate      */
+    int subtract_shot;       /* 1: subtract shot noise from P_+^(0) and P_dd^(0)               */
+    long long max_shapes;    /* capacity (particles) reserved in the workspace per role       */
+    long long max_density;
+    long long max_randoms;
+    int host_inputs;         /* 1: reserve staging so lpp_assign accepts host catalogues       */
+    int batch;               /* complex grids per field pass; 0 = library default             */
+} lpp_plan_desc;
+
+typedef struct {
+    const void* pos;    /* [3][count] SoA x,y,z; float for LPP_FP32 plans, double for FP64   */
+    const void* w;      /* [count] weights or NULL (all 1)                                   */
+    const void* nbar;   /* [count] mean density (randoms, for I = alpha sum nbar w^2) or NULL */
+    const void* shape;  /* TENSOR6: [6][count] (xx,yy,zz,xy,xz,yz); GAMMA12: [2][count]       */
+    long long count;    /* number of particles, 0..max for the role                          */
+    int shape_kind;     /* LPP_SHAPE_*; only the LPP_SHAPES role reads shapes                */
+    int on_host;        /* 1: pointers are host memory (copied during lpp_assign)            */
+} lpp_particles;
+
+typedef struct {
+    double* p;            /* out [LPP_N_MOMENTS][n_bins][2] normalised (re, im)               */
+    double* raw;          /* out, optional: the same before normalisation and shot noise      */
+    double* k_mean;       /* out, optional [n_bins]: mean |k| of the modes in each shell      */
+    long long* n_modes;   /* out, optional [n_bins]: modes of the n^3 grid in each shell      */
+    double norm_auto;     /* out: I for plus/minus                                            */
+    double norm_cross;    /* out: I for cross                                                 */
+    double norm_dd;       /* out: I for the density monopole                                  */
+    double shot_plus;     /* out: sum_s w^2 |gamma|^2 / I (subtracted from P_+^(0))           */
+    double shot_dd;       /* out: density shot noise (subtracted from P_dd^(0))               */
+    double alpha;         /* out: sum w_density / sum w_randoms (0 without randoms)           */
+} lpp_result;
+
+/* Create a plan from a descriptor; validates sizes and flags on the host only. */
+lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* plan);
+void lpp_plan_destroy(lpp_plan_t plan);
+
+/* Device bytes the caller must provide through lpp_plan_set_workspace. */
+lpp_status lpp_plan_workspace_size(lpp_plan_t plan, size_t* bytes);
+/* Hand the plan a device buffer of at least lpp_plan_workspace_size() bytes,
+ * 256-byte aligned; the caller keeps ownership and must keep it alive. */
+lpp_status lpp_plan_set_workspace(lpp_plan_t plan, void* device_ptr, size_t bytes);
+/* CUDA stream (cudaStream_t) for all work of this plan; NULL = legacy default stream. */
+lpp_status lpp_plan_set_stream(lpp_plan_t plan, void* stream);
+/* Number of real k-space fields one estimate transforms (channels plus partners). */
+lpp_status lpp_plan_field_count(lpp_plan_t plan, int* n_fields);
+
+/* Attach a catalogue to a role.  Device pointers are referenced (they must stay valid
+ * until lpp_multipoles returns); host pointers are copied into the workspace on the
+ * plan's stream.  LPP_SHAPES is required; LPP_DENSITY defaults to the shapes'
+ * positions and weights; LPP_RANDOMS is optional (none = periodic box). */
+lpp_status lpp_assign(lpp_plan_t plan, int role, const lpp_particles* particles);
+/* Forget a role's catalogue (e.g. to run a periodic estimate after a survey one). */
+lpp_status lpp_clear(lpp_plan_t plan, int role);
+
+/* Run the estimator (Secs. 3.1.1-3.1.2): sky frames and shears, harmonic weights,
+ * CIC/TSC assignment with optional interlacing, 3D FFTs, k-space contraction with
+ * the partner field and FP64 shell sums; then normalise and subtract shot noise.
+ * Synchronises the plan's stream.  Returns LPP_ERR_DOMAIN if a particle was outside
+ * the box, at the observer, or on the frame pole. */
+lpp_status lpp_multipoles(lpp_plan_t plan, lpp_result* result);
+
+/* Legendre multipoles of P_gE (l = 0,2), P_EE and P_BB (l = 0,2,4) from normalised
+ * native moments p[LPP_N_MOMENTS][n_bins][2] (real parts), by the completeness of
+ * {Lm_L/(1-mu^2)^(m/2)} (Sec. 2.4) and P_EE/BB = (P_+ +- P_-)/2 (Eq. relation_pm_EB).
+ * Outputs ge[2][n_bins], ee[3][n_bins], bb[3][n_bins].  Host-only arithmetic. */
+lpp_status lpp_derive_eb(const double* p, int n_bins, double* ge, double* ee, double* bb);
+
+/* Per-kernel device timing of the last lpp_multipoles call (enabled by
+ * lpp_plan_set_timing(plan, 1); events are recorded on the plan's stream).
+ * kind: 0 assign, 1 fft, 2 combine, 3 coefficients, 4 partner unpack, 5 other (catalogue
+ * sums and the randoms ratio alpha).
+ * ms = summed event time, launches = number of launches, bytes = algorithmic DRAM
+ * bytes those launches must move. */
+lpp_status lpp_plan_set_timing(lpp_plan_t plan, int enable);
+lpp_status lpp_plan_kernel_stats(lpp_plan_t plan, int kind, double* ms, long long* launches,
+                                 double* bytes);
+
+const char* lpp_status_string(lpp_status status);
+/* Last error message recorded on this plan (empty string if none). */
+const char* lpp_plan_last_error(lpp_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LPP_H */

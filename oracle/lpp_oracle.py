@@ -32,7 +32,8 @@ Readings where the paper is silent (each listed in the design doc):
   gamma(-k) := conj(FT[gamma*]);  the shell average is the mean over all modes of the
   n^3 DFT grid (numpy fftfreq frequencies) with kf*sqrt(n^2) in [edge_b, edge_b+1), k != 0;
 * normalisation I: periodic box (Sum w)^2/V (auto) and (Sum w_s)(Sum w_d)/V (cross),
-  with randoms alpha * Sum_r nbar w^2; shot noise Sum_s w^2|gamma|^2 / I on P_+^(0) only.
+  with randoms alpha * Sum_r nbar w^2; shot noise Sum_s w^2|gamma|^2 / I on P_+^(0) only;
+  a shell that contains no mode of the grid reports 0 (no estimate, no shot-noise term).
 """
 from __future__ import annotations
 
@@ -462,6 +463,7 @@ def multipoles(plan: Plan, shapes_pos, shapes_w=None, shapes_s6=None, shapes_g12
             p[i] = p[i] - shot_plus
         if kind == "dd":
             p[i] = p[i] - shot_dd
+        p[i] = np.where(n_modes > 0, p[i], 0.0)   # a shell without modes has no estimate: report 0
     return Result(p, raw, n_modes, k_mean, norm_auto, norm_cross, norm_dd, shot_plus, shot_dd, alpha)
 
 

@@ -1,0 +1,744 @@
+// C ABI of liblpp: plan bookkeeping, workspace layout and the estimate pipeline.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "lpp_internal.h"
+#include "lpp_kernels.h"
+
+using namespace lpp;
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Catalogue {
+    bool set = false;
+    long long count = 0;
+    int shape_kind = LPP_SHAPE_NONE;
+    const void* pos = nullptr;
+    const void* w = nullptr;
+    const void* nbar = nullptr;
+    const void* shape = nullptr;
+};
+
+}  // namespace
+
+struct lpp_plan_s {
+    lpp_plan_desc d;
+    std::vector<double> edges;
+    bool fp64 = false;
+    size_t es = 4;   // real element size
+    int n = 0;
+    double box = 0;
+    int nb = 0;
+    // kept frequency range and geometry
+    int nk_pos = 0, nk_neg = 0, nky = 0, nzi = 0;
+    FftGeom geom;
+    std::vector<int> thr;
+    std::vector<long long> n_modes;
+    std::vector<double> k_mean;
+    // channels
+    std::vector<Channel> channels;
+    std::vector<CoeffGroup> groups;
+    int n_coeff_rows = 2;
+    bool need_d = false, need_g = false;
+    int batch = 8;
+    int batch_ch = 8;
+    // host tables
+    std::vector<double> polys;
+    Quadrature quad[4];
+    KernelPolys kp;
+    // workspace
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    size_t ws_need = 0;
+    size_t off_sums = 0, off_err = 0, off_out = 0, off_thr = 0, off_tw = 0, off_iw = 0, off_ph = 0;
+    size_t off_quad_dirs[4] = {0}, off_quad_tab[4] = {0}, off_polys = 0, off_coeff = 0;
+    size_t off_partner = 0, off_grids = 0, off_stage[3] = {0, 0, 0};
+    int n_partner = 0;
+    int out_rows = 0;
+    bool tables_ready = false;
+    cudaStream_t stream = nullptr;
+    Catalogue cat[3];
+    Timer timer;
+    std::string err;
+    int n_sm = 152;
+};
+
+static lpp_status fail(lpp_plan_t p, lpp_status s, const std::string& msg) {
+    if (p) p->err = msg;
+    return s;
+}
+
+static lpp_status cuda_fail(lpp_plan_t p, cudaError_t e, const char* where) {
+    return fail(p, LPP_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LPP_CUDA(call)                                                 \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return cuda_fail(plan, e_, #call);      \
+    } while (0)
+
+static double norm_factor(int m, int L) {
+    double r = 2.0 * L + 1.0;
+    for (int j = L - m + 1; j <= L + m; ++j) r /= j;
+    return r;
+}
+
+static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// ------------------------------------------------------------------ plan create
+extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out) {
+    if (!desc || !out) return LPP_ERR_INVALID_ARG;
+    *out = nullptr;
+    const lpp_plan_desc& d = *desc;
+    if (!is_pow2(d.n) || d.n < 8 || d.n > 1024) return LPP_ERR_UNSUPPORTED;
+    if (!(d.box > 0) || d.n_bins < 1 || d.n_bins > 256 || !d.k_edges) return LPP_ERR_INVALID_ARG;
+    if (d.scheme != LPP_CIC && d.scheme != LPP_TSC) return LPP_ERR_INVALID_ARG;
+    if (d.precision != LPP_FP32 && d.precision != LPP_FP64) return LPP_ERR_INVALID_ARG;
+    if ((d.los_proj != LPP_LOS_LOCAL && d.los_proj != LPP_LOS_GLOBAL) ||
+        (d.los_est != LPP_LOS_LOCAL && d.los_est != LPP_LOS_GLOBAL))
+        return LPP_ERR_INVALID_ARG;
+    if ((d.moments & LPP_WANT_ALL) == 0) return LPP_ERR_INVALID_ARG;
+    if (d.max_shapes < 0 || d.max_density < 0 || d.max_randoms < 0) return LPP_ERR_INVALID_ARG;
+    if (d.batch < 0 || d.batch > kMaxSlots) return LPP_ERR_INVALID_ARG;
+    for (int i = 0; i < d.n_bins; ++i)
+        if (!(d.k_edges[i] < d.k_edges[i + 1])) return LPP_ERR_INVALID_ARG;
+    const double pn = sqrt(d.pole[0] * d.pole[0] + d.pole[1] * d.pole[1] + d.pole[2] * d.pole[2]);
+    if (!(pn > 0)) return LPP_ERR_INVALID_ARG;
+    const double gn = sqrt(d.los_global[0] * d.los_global[0] + d.los_global[1] * d.los_global[1] +
+                           d.los_global[2] * d.los_global[2]);
+    if ((d.los_proj == LPP_LOS_GLOBAL || d.los_est == LPP_LOS_GLOBAL) && !(gn > 0)) return LPP_ERR_INVALID_ARG;
+
+    lpp_plan_t plan = new lpp_plan_s();
+    plan->d = d;
+    plan->edges.assign(d.k_edges, d.k_edges + d.n_bins + 1);
+    plan->d.k_edges = plan->edges.data();
+    for (int a = 0; a < 3; ++a) {
+        plan->d.pole[a] = d.pole[a] / pn;
+        plan->d.los_global[a] = gn > 0 ? d.los_global[a] / gn : 0.0;
+    }
+    plan->fp64 = d.precision == LPP_FP64;
+    plan->es = plan->fp64 ? 8 : 4;
+    plan->n = d.n;
+    plan->box = d.box;
+    plan->nb = d.n_bins;
+    const int n = d.n, nb = d.n_bins;
+
+    // thresholds on the integer |f|^2: mode in shell b iff thr[b] <= q < thr[b+1],
+    // the same decision as kf*sqrt(q) in [edge_b, edge_b+1) in FP64
+    const double kf = 2.0 * kPi / d.box;
+    const long long qmax = 3LL * (n / 2) * (n / 2);
+    plan->thr.resize(nb + 1);
+    for (int b = 0; b <= nb; ++b) {
+        const double e = d.k_edges[b];
+        long long q;
+        if (e <= 0) q = 0;
+        else {
+            const double t = e / kf;
+            q = (long long)floor(t * t);
+            if (q > qmax + 1) q = qmax + 1;
+            while (q > 0 && kf * sqrt((double)(q - 1)) >= e) --q;
+            while (q <= qmax && kf * sqrt((double)q) < e) ++q;
+        }
+        plan->thr[b] = (int)q;
+    }
+    const int tmax = plan->thr[nb];
+    int nk = 0;
+    while ((long long)(nk + 1) * (nk + 1) < tmax && nk < n / 2) ++nk;
+    plan->nk_pos = std::min(nk, n / 2 - 1);
+    plan->nk_neg = std::min(nk, n / 2);
+    plan->geom = fft_geometry(n, plan->nk_pos, plan->nk_neg);
+    plan->nky = plan->geom.nky;
+    plan->nzi = plan->nk_pos + 1 + (plan->nk_neg == n / 2 ? 1 : 0);
+
+    // modes per shell and mean |k| over the kept cube
+    plan->n_modes.assign(nb, 0);
+    std::vector<double> ksum(nb, 0.0);
+    for (int fx = -plan->nk_neg; fx <= plan->nk_pos; ++fx)
+        for (int fy = -plan->nk_neg; fy <= plan->nk_pos; ++fy) {
+            const long long qxy = (long long)fx * fx + (long long)fy * fy;
+            if (qxy >= tmax) continue;
+            for (int fz = -plan->nk_neg; fz <= plan->nk_pos; ++fz) {
+                const long long q = qxy + (long long)fz * fz;
+                if (q == 0 || q < plan->thr[0] || q >= tmax) continue;
+                int lo = 0, hi = nb;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) / 2;
+                    if (q >= plan->thr[mid]) lo = mid; else hi = mid;
+                }
+                plan->n_modes[lo] += 1;
+                ksum[lo] += kf * sqrt((double)q);
+            }
+        }
+    plan->k_mean.assign(nb, 0.0);
+    for (int b = 0; b < nb; ++b) plan->k_mean[b] = plan->n_modes[b] ? ksum[b] / plan->n_modes[b] : 0.0;
+
+    // kernel polynomials and quadratures
+    build_kernel_polys(plan->kp);
+    for (int qi = 0; qi < 4; ++qi) build_quadrature(2 * (qi + 1), plan->quad[qi]);
+
+    // channel groups: (kind, L) -> 2L+1 coefficient rows per projected part
+    const unsigned m = d.moments;
+    const bool cross_b = (m & LPP_WANT_CROSS_B) != 0;
+    int row = 2;  // rows 0, 1: w gamma_1, w gamma_2
+    auto add_group = [&](int kind, int L, int has_im, const double* poly, int npoly, int slot) {
+        CoeffGroup g;
+        g.kind = kind;
+        g.L = L;
+        g.has_im = has_im;
+        g.row_re = row;
+        row += 2 * L + 1;
+        g.row_im = has_im ? row : -1;
+        if (has_im) row += 2 * L + 1;
+        g.poly = (int)plan->polys.size();
+        g.npoly = npoly;
+        plan->polys.insert(plan->polys.end(), poly, poly + npoly);
+        g.quad = L / 2 - 1;
+        plan->groups.push_back(g);
+        for (int part = 0; part <= has_im; ++part)
+            for (int nn = -L; nn <= L; ++nn) {
+                Channel c;
+                c.kind = kind;
+                c.L = L;
+                c.n = nn;
+                c.part = part;
+                c.moment = slot;
+                c.coeff = (part ? g.row_im : g.row_re) + nn + L;
+                plan->channels.push_back(c);
+            }
+    };
+    const int crossSlot[3] = {LPP_MOM_CROSS2, LPP_MOM_CROSS4, LPP_MOM_CROSS6};
+    for (int i = 0; i < 3; ++i)
+        if (m & (1u << crossSlot[i])) add_group(KIND_CROSS, 2 * (i + 1), cross_b ? 1 : 0, plan->kp.cross[i], 2 * i + 1, crossSlot[i]);
+    if (m & (1u << LPP_MOM_PLUS2)) add_group(KIND_PLUS, 2, 1, plan->kp.plus[1], 3, LPP_MOM_PLUS2);
+    if (m & (1u << LPP_MOM_PLUS4)) add_group(KIND_PLUS, 4, 1, plan->kp.plus[2], 5, LPP_MOM_PLUS4);
+    const int minusSlot[3] = {LPP_MOM_MINUS4, LPP_MOM_MINUS6, LPP_MOM_MINUS8};
+    for (int i = 0; i < 3; ++i)
+        if (m & (1u << minusSlot[i])) add_group(KIND_MINUS, 4 + 2 * i, 1, plan->kp.minus[i], 2 * i + 1, minusSlot[i]);
+    plan->n_coeff_rows = row;
+    plan->need_d = (m & ((1u << LPP_MOM_DD0) | (1u << LPP_MOM_CROSS2) | (1u << LPP_MOM_CROSS4) |
+                         (1u << LPP_MOM_CROSS6))) != 0;
+    plan->need_g = (m & ((1u << LPP_MOM_PLUS0) | (1u << LPP_MOM_PLUS2) | (1u << LPP_MOM_PLUS4) |
+                         (1u << LPP_MOM_MINUS4) | (1u << LPP_MOM_MINUS6) | (1u << LPP_MOM_MINUS8))) != 0;
+    plan->n_partner = (plan->need_d ? 1 : 0) + (plan->need_g ? 2 : 0);
+    plan->out_rows = (int)plan->channels.size() + 2;
+
+    // batch: grids per field pass; the partner pass needs up to 3 (interlaced) grids
+    int batch = d.batch > 0 ? d.batch : 8;
+    const int per_grid = d.interlace ? 1 : 2;
+    // shared-memory partials of the combine: channels x bins x 2 <= 8192 values
+    int max_ch = std::min(kMaxBatchCh, 4096 / nb);
+    if (max_ch < 1) max_ch = 1;
+    batch = std::min(batch, std::max(1, max_ch / per_grid));
+    const int partner_grids = d.interlace ? plan->n_partner : (plan->need_g ? 1 : 0) + (plan->need_d ? 1 : 0);
+    plan->batch = std::max(batch, partner_grids);
+    plan->batch_ch = std::min(batch * per_grid, max_ch);
+
+    // workspace layout
+    const size_t es = plan->es, cs = 2 * es;
+    const size_t n3 = (size_t)n * n * n;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+    plan->off_sums = take(SUM_COUNT * sizeof(double));
+    plan->off_err = take(sizeof(int));
+    plan->off_out = take((size_t)plan->out_rows * nb * 2 * sizeof(double));
+    plan->off_thr = take((nb + 1) * sizeof(int));
+    plan->off_tw = take(n * cs);
+    plan->off_iw = take(n * es);
+    plan->off_ph = take(n * cs);
+    for (int qi = 0; qi < 4; ++qi) {
+        plan->off_quad_dirs[qi] = take(plan->quad[qi].dirs.size() * es);
+        plan->off_quad_tab[qi] = take(plan->quad[qi].table.size() * es);
+    }
+    plan->off_polys = take(std::max<size_t>(1, plan->polys.size()) * es);
+    plan->off_coeff = take((size_t)plan->n_coeff_rows * std::max<long long>(1, d.max_shapes) * es);
+    plan->off_partner = take((size_t)plan->n_partner * n3 * cs);
+    plan->off_grids = take((size_t)plan->batch * n3 * cs);
+    if (d.host_inputs) {
+        plan->off_stage[LPP_SHAPES] = take((size_t)(3 + 1 + 6) * d.max_shapes * es);
+        plan->off_stage[LPP_DENSITY] = take((size_t)(3 + 1) * d.max_density * es);
+        plan->off_stage[LPP_RANDOMS] = take((size_t)(3 + 1 + 1) * d.max_randoms * es);
+    }
+    plan->ws_need = off;
+    *out = plan;
+    return LPP_OK;
+}
+
+extern "C" void lpp_plan_destroy(lpp_plan_t plan) {
+    if (!plan) return;
+    if (plan->timer.created)
+        for (int i = 0; i < Timer::kMaxEvents; ++i) cudaEventDestroy(plan->timer.ev[i]);
+    delete plan;
+}
+
+extern "C" lpp_status lpp_plan_workspace_size(lpp_plan_t plan, size_t* bytes) {
+    if (!plan || !bytes) return LPP_ERR_INVALID_ARG;
+    *bytes = plan->ws_need;
+    return LPP_OK;
+}
+
+extern "C" lpp_status lpp_plan_field_count(lpp_plan_t plan, int* n_fields) {
+    if (!plan || !n_fields) return LPP_ERR_INVALID_ARG;
+    *n_fields = (int)plan->channels.size() + plan->n_partner;
+    return LPP_OK;
+}
+
+extern "C" lpp_status lpp_plan_set_stream(lpp_plan_t plan, void* stream) {
+    if (!plan) return LPP_ERR_INVALID_ARG;
+    plan->stream = (cudaStream_t)stream;
+    return LPP_OK;
+}
+
+template <typename T>
+static lpp_status write_tables(lpp_plan_t plan) {
+    const int n = plan->n;
+    auto put = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
+        return cudaMemcpyAsync(plan->ws + off, src, bytes, cudaMemcpyHostToDevice, plan->stream);
+    };
+    LPP_CUDA(put(plan->off_thr, plan->thr.data(), plan->thr.size() * sizeof(int)));
+    // twiddles e^{-2 pi i j / n}
+    std::vector<T> tw(2 * n), iw(n), ph(2 * n);
+    for (int j = 0; j < n; ++j) {
+        tw[2 * j] = (T)cos(2.0 * kPi * j / n);
+        tw[2 * j + 1] = (T)(-sin(2.0 * kPi * j / n));
+        const int f = j < n / 2 ? j : j - n;
+        // assignment window sinc^p(pi f / n) and the half-cell interlacing phase
+        const double xarg = kPi * f / n;
+        const double sinc = f == 0 ? 1.0 : sin(xarg) / xarg;
+        iw[j] = (T)(plan->d.compensate ? 1.0 / pow(sinc, plan->d.scheme) : 1.0);
+        ph[2 * j] = (T)cos(xarg);
+        ph[2 * j + 1] = (T)(-sin(xarg));
+    }
+    // host copies stay alive until the stream has consumed them (synchronised below)
+    std::vector<std::vector<T>> keep;
+    keep.reserve(16);
+    keep.push_back(tw);
+    keep.push_back(iw);
+    keep.push_back(ph);
+    LPP_CUDA(put(plan->off_tw, keep[0].data(), keep[0].size() * sizeof(T)));
+    LPP_CUDA(put(plan->off_iw, keep[1].data(), keep[1].size() * sizeof(T)));
+    LPP_CUDA(put(plan->off_ph, keep[2].data(), keep[2].size() * sizeof(T)));
+    for (int qi = 0; qi < 4; ++qi) {
+        keep.emplace_back(plan->quad[qi].dirs.begin(), plan->quad[qi].dirs.end());
+        LPP_CUDA(put(plan->off_quad_dirs[qi], keep.back().data(), keep.back().size() * sizeof(T)));
+        keep.emplace_back(plan->quad[qi].table.begin(), plan->quad[qi].table.end());
+        LPP_CUDA(put(plan->off_quad_tab[qi], keep.back().data(), keep.back().size() * sizeof(T)));
+    }
+    if (!plan->polys.empty()) {
+        keep.emplace_back(plan->polys.begin(), plan->polys.end());
+        LPP_CUDA(put(plan->off_polys, keep.back().data(), keep.back().size() * sizeof(T)));
+    }
+    LPP_CUDA(cudaStreamSynchronize(plan->stream));
+    plan->tables_ready = true;
+    return LPP_OK;
+}
+
+extern "C" lpp_status lpp_plan_set_workspace(lpp_plan_t plan, void* device_ptr, size_t bytes) {
+    if (!plan || !device_ptr) return LPP_ERR_INVALID_ARG;
+    if (((uintptr_t)device_ptr & 255) != 0) return fail(plan, LPP_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (bytes < plan->ws_need) return fail(plan, LPP_ERR_WORKSPACE, "workspace too small");
+    plan->ws = (char*)device_ptr;
+    plan->ws_bytes = bytes;
+    plan->tables_ready = false;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            plan->n_sm = sms;
+    }
+    return plan->fp64 ? write_tables<double>(plan) : write_tables<float>(plan);
+}
+
+extern "C" lpp_status lpp_plan_set_timing(lpp_plan_t plan, int enable) {
+    if (!plan) return LPP_ERR_INVALID_ARG;
+    if (enable && !plan->timer.created) {
+        for (int i = 0; i < Timer::kMaxEvents; ++i) LPP_CUDA(cudaEventCreate(&plan->timer.ev[i]));
+        plan->timer.created = true;
+    }
+    plan->timer.enabled = enable != 0;
+    plan->timer.reset();
+    return LPP_OK;
+}
+
+extern "C" lpp_status lpp_plan_kernel_stats(lpp_plan_t plan, int kind, double* ms, long long* launches,
+                                            double* bytes) {
+    if (!plan || kind < 0 || kind >= KK_COUNT) return LPP_ERR_INVALID_ARG;
+    if (ms) *ms = plan->timer.ms[kind];
+    if (launches) *launches = plan->timer.launches[kind];
+    if (bytes) *bytes = plan->timer.total_bytes[kind];
+    return LPP_OK;
+}
+
+// ------------------------------------------------------------------ catalogues
+extern "C" lpp_status lpp_assign(lpp_plan_t plan, int role, const lpp_particles* p) {
+    if (!plan || !p || role < 0 || role > 2) return LPP_ERR_INVALID_ARG;
+    const long long cap = role == LPP_SHAPES ? plan->d.max_shapes
+                                             : (role == LPP_DENSITY ? plan->d.max_density : plan->d.max_randoms);
+    if (p->count < 0 || p->count > cap) return fail(plan, LPP_ERR_INVALID_ARG, "particle count exceeds the plan capacity");
+    if (p->count > 0 && !p->pos) return fail(plan, LPP_ERR_INVALID_ARG, "null positions");
+    int sk = role == LPP_SHAPES ? p->shape_kind : LPP_SHAPE_NONE;
+    if (sk != LPP_SHAPE_NONE && sk != LPP_SHAPE_GAMMA12 && sk != LPP_SHAPE_TENSOR6)
+        return fail(plan, LPP_ERR_INVALID_ARG, "bad shape kind");
+    if (role == LPP_SHAPES && plan->need_g + (plan->channels.empty() ? 0 : 1) > 0 && sk == LPP_SHAPE_NONE)
+        return fail(plan, LPP_ERR_INVALID_ARG, "the requested moments need shapes");
+    if (sk != LPP_SHAPE_NONE && p->count > 0 && !p->shape) return fail(plan, LPP_ERR_INVALID_ARG, "null shapes");
+    Catalogue c;
+    c.set = true;
+    c.count = p->count;
+    c.shape_kind = sk;
+    if (!p->on_host) {
+        c.pos = p->pos;
+        c.w = p->w;
+        c.nbar = role == LPP_RANDOMS ? p->nbar : nullptr;
+        c.shape = sk != LPP_SHAPE_NONE ? p->shape : nullptr;
+    } else {
+        if (!plan->d.host_inputs) return fail(plan, LPP_ERR_INVALID_ARG, "plan was created without host staging");
+        if (!plan->ws) return fail(plan, LPP_ERR_NOT_READY, "workspace not set");
+        const size_t es = plan->es;
+        const long long cnt = p->count;
+        char* base = plan->ws + plan->off_stage[role];
+        char* dst = base;
+        LPP_CUDA(cudaMemcpyAsync(dst, p->pos, 3 * cnt * es, cudaMemcpyHostToDevice, plan->stream));
+        c.pos = dst;
+        dst += 3 * cap * es;
+        if (p->w) {
+            LPP_CUDA(cudaMemcpyAsync(dst, p->w, cnt * es, cudaMemcpyHostToDevice, plan->stream));
+            c.w = dst;
+        }
+        dst += cap * es;
+        if (role == LPP_RANDOMS && p->nbar) {
+            LPP_CUDA(cudaMemcpyAsync(dst, p->nbar, cnt * es, cudaMemcpyHostToDevice, plan->stream));
+            c.nbar = dst;
+        }
+        if (role == LPP_SHAPES && sk != LPP_SHAPE_NONE) {
+            const int comps = sk == LPP_SHAPE_TENSOR6 ? 6 : 2;
+            LPP_CUDA(cudaMemcpyAsync(dst, p->shape, comps * cnt * es, cudaMemcpyHostToDevice, plan->stream));
+            c.shape = dst;
+        }
+    }
+    plan->cat[role] = c;
+    return LPP_OK;
+}
+
+extern "C" lpp_status lpp_clear(lpp_plan_t plan, int role) {
+    if (!plan || role < 0 || role > 2) return LPP_ERR_INVALID_ARG;
+    plan->cat[role] = Catalogue();
+    return LPP_OK;
+}
+
+// ------------------------------------------------------------------ estimate
+template <typename T>
+static lpp_status run(lpp_plan_t plan, lpp_result* res) {
+    const int n = plan->n, nb = plan->nb;
+    const size_t n3 = (size_t)n * n * n;
+    cudaStream_t st = plan->stream;
+    Timer* tm = plan->timer.enabled ? &plan->timer : nullptr;
+    if (tm) tm->reset();
+    double* sums = (double*)(plan->ws + plan->off_sums);
+    int* err = (int*)(plan->ws + plan->off_err);
+    double* out = (double*)(plan->ws + plan->off_out);
+    c2<T>* grids = (c2<T>*)(plan->ws + plan->off_grids);
+    c2<T>* partner = (c2<T>*)(plan->ws + plan->off_partner);
+    T* coeff = (T*)(plan->ws + plan->off_coeff);
+    const long long stride = std::max<long long>(1, plan->d.max_shapes);
+    const Catalogue& sh = plan->cat[LPP_SHAPES];
+    const Catalogue& de = plan->cat[LPP_DENSITY].set ? plan->cat[LPP_DENSITY] : plan->cat[LPP_SHAPES];
+    const Catalogue& ra = plan->cat[LPP_RANDOMS];
+    const bool has_rand = ra.set;
+
+    LPP_CUDA(cudaMemsetAsync(sums, 0, SUM_COUNT * sizeof(double), st));
+    LPP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    LPP_CUDA(cudaMemsetAsync(out, 0, (size_t)plan->out_rows * nb * 2 * sizeof(double), st));
+
+    // 1. sky frames, shears and harmonic weights of the shape catalogue
+    CoeffArgs<T> ca;
+    memset(&ca, 0, sizeof(ca));
+    ca.pos = (const T*)sh.pos;
+    ca.w = (const T*)sh.w;
+    ca.shape = (const T*)sh.shape;
+    ca.count = sh.count;
+    ca.shape_kind = sh.shape_kind;
+    for (int a = 0; a < 3; ++a) {
+        ca.observer[a] = plan->d.observer[a];
+        ca.pole[a] = plan->d.pole[a];
+        ca.los_global[a] = plan->d.los_global[a];
+    }
+    ca.los_proj = plan->d.los_proj;
+    ca.los_est = plan->d.los_est;
+    ca.coeff = coeff;
+    ca.stride = stride;
+    ca.n_groups = (int)plan->groups.size();
+    for (int g = 0; g < ca.n_groups; ++g) ca.groups[g] = plan->groups[g];
+    for (int qi = 0; qi < 4; ++qi) {
+        ca.quad_dirs[qi] = (const T*)(plan->ws + plan->off_quad_dirs[qi]);
+        ca.quad_tab[qi] = (const T*)(plan->ws + plan->off_quad_tab[qi]);
+        ca.quad_S[qi] = plan->quad[qi].S;
+    }
+    ca.polys = (const T*)(plan->ws + plan->off_polys);
+    ca.sums = sums;
+    ca.err = err;
+    if (sh.shape_kind != LPP_SHAPE_NONE) {
+        if (tm) tm->begin(KK_COEFF, st);
+        LPP_CUDA(launch_coeffs<T>(ca, st));
+        if (tm) tm->end(KK_COEFF, st, (double)sh.count * plan->es * (3 + 1 + 6 + plan->n_coeff_rows));
+    } else {
+        if (tm) tm->begin(KK_OTHER, st);
+        LPP_CUDA(launch_sums<T>((const T*)sh.w, nullptr, sh.count, sums, SUM_W_SHAPES, -1, -1, st));
+        if (tm) tm->end(KK_OTHER, st, (double)sh.count * plan->es);
+    }
+    if (tm) tm->begin(KK_OTHER, st);
+    LPP_CUDA(launch_sums<T>((const T*)de.w, nullptr, de.count, sums, SUM_W_DENS, SUM_W2_DENS, -1, st));
+    if (tm) tm->end(KK_OTHER, st, (double)de.count * plan->es);
+    if (has_rand) {
+        if (tm) tm->begin(KK_OTHER, st);
+        LPP_CUDA(launch_sums<T>((const T*)ra.w, (const T*)ra.nbar, ra.count, sums, SUM_W_RAND, SUM_W2_RAND,
+                                SUM_NW2_RAND, st));
+        if (tm) tm->end(KK_OTHER, st, (double)ra.count * plan->es * 2);
+    }
+    if (tm) tm->begin(KK_OTHER, st);
+    LPP_CUDA(launch_alpha(sums, has_rand ? 1 : 0, st));
+    if (tm) tm->end(KK_OTHER, st, 0.0);
+
+    const FftGeom& geom = plan->geom;
+    const c2<T>* tw = (const c2<T>*)(plan->ws + plan->off_tw);
+    CombineArgs<T> cb;
+    memset(&cb, 0, sizeof(cb));
+    cb.grids = grids;
+    cb.grid_stride = (long long)n3;
+    cb.n = n;
+    cb.interlace = plan->d.interlace;
+    c2<T>* pG1 = partner;
+    c2<T>* pG2 = plan->need_g ? partner + n3 : nullptr;
+    c2<T>* pD = plan->need_d ? partner + (plan->need_g ? 2 : 0) * n3 : nullptr;
+    if (!plan->need_g) pG1 = nullptr;
+    cb.pD = pD;
+    cb.pG1 = pG1;
+    cb.pG2 = pG2;
+    cb.inv_w = (const T*)(plan->ws + plan->off_iw);
+    cb.phase = (const c2<T>*)(plan->ws + plan->off_ph);
+    cb.thr = (const int*)(plan->ws + plan->off_thr);
+    cb.nb = nb;
+    cb.nk_pos = plan->nk_pos;
+    cb.nk_neg = plan->nk_neg;
+    cb.nky = plan->nky;
+    cb.nzi = plan->nzi;
+    cb.out = out;
+    const int n_ch = (int)plan->channels.size();
+    cb.row_dd0 = n_ch;
+    cb.row_plus0 = n_ch + 1;
+
+    AssignArgs<T> aa;
+    memset(&aa, 0, sizeof(aa));
+    aa.grids = grids;
+    aa.grid_stride = (long long)n3;
+    aa.n = n;
+    aa.box = plan->box;
+    for (int a = 0; a < 3; ++a) aa.origin[a] = plan->d.origin[a];
+    aa.sums = sums;
+    aa.err = err;
+    const double pbytes = (double)plan->es;
+    auto assign_cat = [&](const Catalogue& c) -> lpp_status {
+        aa.pos = (const T*)c.pos;
+        aa.count = c.count;
+        if (tm) tm->begin(KK_ASSIGN, st);
+        LPP_CUDA(launch_assign<T>(aa, plan->d.scheme, plan->d.interlace, st));
+        if (tm) tm->end(KK_ASSIGN, st, (double)c.count * pbytes * (3 + aa.n_slots));
+        return LPP_OK;
+    };
+
+    // modes that fall in some shell: what the combine must read per field
+    double shell_modes = 0.0;
+    for (int b = 0; b < nb; ++b) shell_modes += (double)plan->n_modes[b];
+
+    // 2. partner fields: G1, G2 (shapes) and D = density - alpha randoms
+    const int il = plan->d.interlace;
+    int pgrids = 0;
+    {
+        LPP_CUDA(cudaMemsetAsync(grids, 0, (size_t)plan->batch * n3 * sizeof(c2<T>), st));
+        // slots written from the shape catalogue
+        aa.n_slots = 0;
+        int g_slot = 0, d_slot = -1;
+        if (plan->need_g) {
+            if (il) {
+                aa.slots[aa.n_slots++] = AssignSlot{coeff, nullptr, 0, 0, 0};
+                aa.slots[aa.n_slots++] = AssignSlot{coeff + stride, nullptr, 1, 0, 0};
+                g_slot = 2;
+            } else {
+                aa.slots[aa.n_slots++] = AssignSlot{coeff, coeff + stride, 0, 0, 0};
+                g_slot = 1;
+            }
+        }
+        if (plan->need_d) d_slot = g_slot;
+        pgrids = plan->need_d ? d_slot + 1 : g_slot;
+        const bool dens_is_shapes = !plan->cat[LPP_DENSITY].set;
+        if (plan->need_d && dens_is_shapes)
+            aa.slots[aa.n_slots++] = AssignSlot{sh.w, nullptr, d_slot, 0, sh.w == nullptr};
+        if (aa.n_slots > 0 && sh.count > 0) { lpp_status s = assign_cat(sh); if (s != LPP_OK) return s; }
+        if (plan->need_d && !dens_is_shapes) {
+            aa.n_slots = 1;
+            aa.slots[0] = AssignSlot{de.w, nullptr, d_slot, 0, de.w == nullptr};
+            lpp_status s = assign_cat(de);
+            if (s != LPP_OK) return s;
+        }
+        if (plan->need_d && has_rand) {
+            aa.n_slots = 1;
+            aa.slots[0] = AssignSlot{ra.w, nullptr, d_slot, 1, ra.w == nullptr};
+            lpp_status s = assign_cat(ra);
+            if (s != LPP_OK) return s;
+        }
+        LPP_CUDA(fft3d<T>(grids, pgrids, n, tw, geom, false, st, tm));
+        cb.partner_mode = 1;
+        cb.has_d = plan->need_d;
+        cb.has_g = plan->need_g;
+        cb.n_ch = 0;
+        if (tm) tm->begin(KK_PARTNER, st);
+        LPP_CUDA(launch_combine<T>(cb, plan->n_sm, st));
+        if (tm) tm->end(KK_PARTNER, st, shell_modes * sizeof(c2<T>) * (pgrids + plan->n_partner));
+    }
+
+    // 3. channel fields, a batch of grids at a time
+    const int per_grid = il ? 1 : 2;
+    cb.partner_mode = 0;
+    for (int c0 = 0; c0 < n_ch; c0 += plan->batch_ch) {
+        const int c1 = std::min(n_ch, c0 + plan->batch_ch);
+        const int nch = c1 - c0;
+        const int ngr = (nch + per_grid - 1) / per_grid;
+        LPP_CUDA(cudaMemsetAsync(grids, 0, (size_t)ngr * n3 * sizeof(c2<T>), st));
+        aa.n_slots = 0;
+        cb.n_ch = nch;
+        cb.has_d = 0;
+        cb.has_g = 0;
+        for (int gi = 0; gi < ngr; ++gi) {
+            const int ca0 = c0 + gi * per_grid;
+            const T* sa = coeff + (long long)plan->channels[ca0].coeff * stride;
+            const T* sb = (!il && ca0 + 1 < c1) ? coeff + (long long)plan->channels[ca0 + 1].coeff * stride : nullptr;
+            aa.slots[aa.n_slots++] = AssignSlot{sa, sb, gi, 0, 0};
+        }
+        for (int ci = 0; ci < nch; ++ci) {
+            const Channel& ch = plan->channels[c0 + ci];
+            CombineChan& cc = cb.ch[ci];
+            cc.slot = ci / per_grid;
+            cc.sub = il ? 0 : ci % 2;
+            cc.kind = ch.kind;
+            cc.L = ch.L;
+            cc.n = ch.n;
+            cc.part = ch.part;
+            cc.out_row = c0 + ci;
+            cc.ynorm = ylm_norm(ch.L, ch.n);
+            if (ch.kind == KIND_CROSS) cb.has_d = 1; else cb.has_g = 1;
+        }
+        { lpp_status s = assign_cat(sh); if (s != LPP_OK) return s; }
+        LPP_CUDA(fft3d<T>(grids, ngr, n, tw, geom, false, st, tm));
+        if (tm) tm->begin(KK_COMBINE, st);
+        LPP_CUDA(launch_combine<T>(cb, plan->n_sm, st));
+        if (tm) tm->end(KK_COMBINE, st, shell_modes * sizeof(c2<T>) * (ngr + (cb.has_d ? 1 : 0) + (cb.has_g ? 2 : 0)));
+    }
+
+    // 4. results to the host
+    std::vector<double> h_out((size_t)plan->out_rows * nb * 2);
+    double h_sums[SUM_COUNT];
+    int h_err = 0;
+    LPP_CUDA(cudaMemcpyAsync(h_out.data(), out, h_out.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LPP_CUDA(cudaMemcpyAsync(h_sums, sums, sizeof(h_sums), cudaMemcpyDeviceToHost, st));
+    LPP_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LPP_CUDA(cudaStreamSynchronize(st));
+    if (tm) tm->collect();
+    if (h_err) {
+        std::string msg = "particle outside the domain:";
+        if (h_err & ERRF_DOMAIN) msg += " outside the box";
+        if (h_err & ERRF_POLE) msg += " on the frame pole";
+        if (h_err & ERRF_OBSERVER) msg += " at the observer";
+        return fail(plan, LPP_ERR_DOMAIN, msg);
+    }
+
+    // 5. normalisation and shot noise (host, FP64)
+    const double vol = plan->box * plan->box * plan->box;
+    const double alpha = h_sums[SUM_ALPHA];
+    double i_auto, i_cross, i_dd, shot_dd_num;
+    if (has_rand) {
+        const double I = alpha * h_sums[SUM_NW2_RAND];
+        i_auto = i_cross = i_dd = I;
+        shot_dd_num = h_sums[SUM_W2_DENS] + alpha * alpha * h_sums[SUM_W2_RAND];
+    } else {
+        i_auto = h_sums[SUM_W_SHAPES] * h_sums[SUM_W_SHAPES] / vol;
+        i_cross = h_sums[SUM_W_SHAPES] * h_sums[SUM_W_DENS] / vol;
+        i_dd = h_sums[SUM_W_DENS] * h_sums[SUM_W_DENS] / vol;
+        shot_dd_num = h_sums[SUM_W2_DENS];
+    }
+    if (plan->d.norm_override > 0) i_auto = i_cross = i_dd = plan->d.norm_override;
+    const double shot_plus = plan->d.subtract_shot && i_auto != 0 ? h_sums[SUM_W2G2_SHAPES] / i_auto : 0.0;
+    const double shot_dd = plan->d.subtract_shot && i_dd != 0 ? shot_dd_num / i_dd : 0.0;
+
+    std::vector<double> mom((size_t)LPP_N_MOMENTS * nb * 2, 0.0);
+    for (int c = 0; c < n_ch; ++c) {
+        const int slot = plan->channels[c].moment;
+        for (int k = 0; k < nb * 2; ++k) mom[(size_t)slot * nb * 2 + k] += h_out[(size_t)c * nb * 2 + k];
+    }
+    for (int k = 0; k < nb * 2; ++k) {
+        mom[(size_t)LPP_MOM_DD0 * nb * 2 + k] = h_out[(size_t)n_ch * nb * 2 + k];
+        mom[(size_t)LPP_MOM_PLUS0 * nb * 2 + k] = h_out[(size_t)(n_ch + 1) * nb * 2 + k];
+    }
+    const unsigned want = plan->d.moments;
+    for (int s = 0; s < LPP_N_MOMENTS; ++s) {
+        double C = 1.0, I = i_auto, shot = 0.0;
+        if (s == LPP_MOM_DD0) { I = i_dd; shot = shot_dd; }
+        else if (s >= LPP_MOM_CROSS2 && s <= LPP_MOM_CROSS6) { C = norm_factor(2, 2 * s); I = i_cross; }
+        else if (s >= LPP_MOM_PLUS0 && s <= LPP_MOM_PLUS4) {
+            const int l = 2 * (s - LPP_MOM_PLUS0);
+            C = 2.0 * l + 1.0;
+            if (l == 0) shot = shot_plus;
+        } else { C = norm_factor(4, 4 + 2 * (s - LPP_MOM_MINUS4)); }
+        const bool on = (want & (1u << s)) != 0;
+        for (int b = 0; b < nb; ++b) {
+            const size_t k = ((size_t)s * nb + b) * 2;
+            const double nm = (double)plan->n_modes[b];
+            const double rre = on && nm > 0 ? C * mom[k] / nm : 0.0;
+            const double rim = on && nm > 0 ? C * mom[k + 1] / nm : 0.0;
+            if (res->raw) { res->raw[k] = rre; res->raw[k + 1] = rim; }
+            if (res->p) {
+                res->p[k] = on && I != 0 ? rre / I - (nm > 0 ? shot : 0.0) : 0.0;
+                res->p[k + 1] = on && I != 0 ? rim / I : 0.0;
+            }
+        }
+    }
+    if (res->k_mean) for (int b = 0; b < nb; ++b) res->k_mean[b] = plan->k_mean[b];
+    if (res->n_modes) for (int b = 0; b < nb; ++b) res->n_modes[b] = plan->n_modes[b];
+    res->norm_auto = i_auto;
+    res->norm_cross = i_cross;
+    res->norm_dd = i_dd;
+    res->shot_plus = shot_plus;
+    res->shot_dd = shot_dd;
+    res->alpha = alpha;
+    return LPP_OK;
+}
+
+extern "C" lpp_status lpp_multipoles(lpp_plan_t plan, lpp_result* res) {
+    if (!plan || !res) return LPP_ERR_INVALID_ARG;
+    if (!plan->ws || !plan->tables_ready) return fail(plan, LPP_ERR_NOT_READY, "workspace not set");
+    if (!plan->cat[LPP_SHAPES].set) return fail(plan, LPP_ERR_NOT_READY, "no shape catalogue assigned");
+    plan->err.clear();
+    return plan->fp64 ? run<double>(plan, res) : run<float>(plan, res);
+}
+
+extern "C" const char* lpp_status_string(lpp_status s) {
+    switch (s) {
+        case LPP_OK: return "ok";
+        case LPP_ERR_INVALID_ARG: return "invalid argument";
+        case LPP_ERR_CUDA: return "CUDA error";
+        case LPP_ERR_NOT_READY: return "not ready";
+        case LPP_ERR_WORKSPACE: return "workspace too small";
+        case LPP_ERR_UNSUPPORTED: return "unsupported";
+        case LPP_ERR_DOMAIN: return "particle outside the domain";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* lpp_plan_last_error(lpp_plan_t plan) { return plan ? plan->err.c_str() : ""; }

@@ -1,0 +1,303 @@
+// k-space combination and FP64 shell sums (Sec. 3.1.2 estimators).
+//
+// A batch grid Z holds two real fields packed as Z = a + i b: either the two
+// interlaced sub-grids of one field, or two different fields.  Their DFTs are
+// recovered exactly from the pair of modes (m, -m):
+//   A(m) = (Z(m) + conj Z(-m)) / 2,   B(m) = -i (Z(m) - conj Z(-m)) / 2,
+//   A(-m) = conj A(m),  B(-m) = conj B(m).
+// Interlaced fields become F = (A + e^{-i pi (fx+fy+fz)/n} B) / 2, and every field is
+// divided by the assignment window prod_a sinc^p(pi f_a / n) when compensation is on.
+//
+// One CTA walks rows (fz, fy) of kept modes; its lanes cover fx >= 0 (first half)
+// and fx < 0 (second half), so |k| grows monotonically along each warp and equal
+// shells form contiguous lane runs.  Per-mode products are reduced within a warp by a
+// segmented scan, added to FP32 shared-memory partials per row, and folded after every
+// row into compensated (two-float) or FP64 accumulators that the CTA flushes to the
+// global FP64 shell sums once at the end.
+#include "lpp_internal.h"
+#include "lpp_kernels.h"
+
+namespace lpp {
+
+template <typename T> struct Owned;
+template <> struct Owned<float> {
+    // compensated sum (Knuth two-sum) in two floats
+    static __device__ __forceinline__ void add(float* hi, float* lo, float v) {
+        const float s = *hi + v;
+        const float bp = s - *hi;
+        const float err = (*hi - (s - bp)) + (v - bp);
+        *hi = s;
+        *lo += err;
+    }
+    static __device__ __forceinline__ double value(const float* hi, const float* lo) {
+        return (double)*hi + (double)*lo;
+    }
+    static constexpr int words = 2;
+};
+template <> struct Owned<double> {
+    static __device__ __forceinline__ void add(double* hi, double*, double v) { *hi += v; }
+    static __device__ __forceinline__ double value(const double* hi, const double*) { return *hi; }
+    static constexpr int words = 1;
+};
+
+template <typename T>
+__device__ __forceinline__ int freq_of(int i, int n) { return i < n / 2 ? i : i - n; }
+
+// segmented inclusive scan of (re, im) over lanes with equal, monotone shell labels;
+// the last lane of each run adds the run total to acc[bin][2].
+template <typename T>
+__device__ __forceinline__ void warp_bin_add(T re, T im, int bin, T* acc) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int ob = __shfl_up_sync(full, bin, d);
+        const T ore = __shfl_up_sync(full, re, d);
+        const T oim = __shfl_up_sync(full, im, d);
+        if (lane >= d && ob == bin) {
+            re += ore;
+            im += oim;
+        }
+    }
+    const int nb = __shfl_down_sync(full, bin, 1);
+    const bool last = (lane == 31) || (nb != bin);
+    if (last && bin >= 0) {
+        atomicAdd(acc + 2 * bin, re);
+        atomicAdd(acc + 2 * bin + 1, im);
+    }
+}
+
+template <typename T>
+struct ModeCtx {
+    c2<T> ph_m, ph_p;   // interlace phases at m and -m
+    T iw_m, iw_p;       // inverse windows
+    long long im, ip;   // linear indices of m and of its mirror
+    bool self;          // m == -m (index-wise)
+};
+
+// DFTs of the two packed fields at m; the values at the mirror are their conjugates.
+template <typename T>
+__device__ __forceinline__ void unpack(const c2<T>* g, const ModeCtx<T>& c, c2<T>& A, c2<T>& B) {
+    const c2<T> zm = g[c.im];
+    const c2<T> zp = g[c.ip];
+    const T h = (T)0.5;
+    A = mk<T>(h * (zm.x + zp.x), h * (zm.y - zp.y));
+    // B = -i (zm - conj zp) / 2
+    const T dr = zm.x - zp.x, di = zm.y + zp.y;
+    B = mk<T>(h * di, -h * dr);
+}
+
+// k-space field at m and -m for sub-field `sub` of a slot.
+template <typename T>
+__device__ __forceinline__ void field_at(const c2<T>* g, int sub, int interlace, const ModeCtx<T>& c, c2<T>& Fm,
+                                         c2<T>& Fp) {
+    c2<T> A, B;
+    unpack<T>(g, c, A, B);
+    if (interlace) {
+        const T h = (T)0.5;
+        Fm = cscale<T>(cadd<T>(A, cmul<T>(c.ph_m, B)), h * c.iw_m);
+        Fp = cscale<T>(cadd<T>(cconj<T>(A), cmul<T>(c.ph_p, cconj<T>(B))), h * c.iw_p);
+    } else {
+        const c2<T> X = sub ? B : A;
+        Fm = cscale<T>(X, c.iw_m);
+        Fp = cscale<T>(cconj<T>(X), c.iw_p);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_combine(CombineArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = a.n;
+    const int nb = a.nb;
+    const int nacc = a.partner_mode ? 2 : a.n_ch;
+    const int E = nacc * nb * 2;
+    T* acc = reinterpret_cast<T*>(smem_raw);                       // [nacc][nb][2] per-row partials
+    T* own = acc + E;                                              // [E][words] owned accumulators
+    T* iw = own + E * Owned<T>::words;                             // [n]
+    c2<T>* ph = reinterpret_cast<c2<T>*>(iw + n + (n & 1));        // [n]
+    int* thr = reinterpret_cast<int*>(ph + n);                     // [nb+1]
+
+    const int tid = threadIdx.x;
+    const int nthr = blockDim.x;
+    for (int i = tid; i < E; i += nthr) acc[i] = (T)0;
+    for (int i = tid; i < E * Owned<T>::words; i += nthr) own[i] = (T)0;
+    for (int i = tid; i < n; i += nthr) { iw[i] = a.inv_w[i]; ph[i] = a.phase[i]; }
+    for (int i = tid; i <= nb; i += nthr) thr[i] = a.thr[i];
+    __syncthreads();
+
+    const int P = nthr / 2;
+    const int fx = tid < P ? tid : -1 - (tid - P);
+    const bool xvalid = tid < P ? (fx <= a.nk_pos) : (-fx <= a.nk_neg);
+    const int x = fx >= 0 ? fx : n + fx;
+    const int xp = (n - x) & (n - 1);
+    const int fxp = freq_of<T>(xp, n);
+    const long long n2l = (long long)n * n;
+    const int rows = a.nzi * a.nky;
+
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int zi = row / a.nky;
+        const int yj = row - zi * a.nky;
+        const int z = zi <= a.nk_pos ? zi : n / 2;
+        const int y = yj <= a.nk_pos ? yj : n - (a.nky - yj);
+        const int zp = (n - z) & (n - 1);
+        const int yp = (n - y) & (n - 1);
+        const int fz = freq_of<T>(z, n), fy = freq_of<T>(y, n);
+        const int fzp = freq_of<T>(zp, n), fyp = freq_of<T>(yp, n);
+
+        // shell label (contiguous along the warp) and whether this lane owns the pair
+        const int q2 = fx * fx + fy * fy + fz * fz;
+        int bin = -1;
+        if (xvalid && q2 > 0 && q2 >= thr[0] && q2 < thr[nb]) {
+            int lo = 0, hi = nb;  // thr[lo] <= q2 < thr[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (q2 >= thr[mid]) lo = mid; else hi = mid;
+            }
+            bin = lo;
+        }
+        bool own_pair = bin >= 0;
+        ModeCtx<T> c;
+        c.self = false;
+        if (own_pair && z == zp) {
+            // self-conjugate plane: take each pair once, from its lexicographically smaller member
+            if (y > yp || (y == yp && x > xp)) own_pair = false;
+            c.self = (y == yp && x == xp);
+        }
+        T kx = 0, ky = 0, kz = 0, kxp = 0, kyp = 0, kzp = 0;
+        if (own_pair) {
+            c.im = ((long long)z * n + y) * n + x;
+            c.ip = ((long long)zp * n + yp) * n + xp;
+            c.iw_m = iw[x] * iw[y] * iw[z];
+            c.iw_p = iw[xp] * iw[yp] * iw[zp];
+            c.ph_m = cmul<T>(cmul<T>(ph[x], ph[y]), ph[z]);
+            c.ph_p = cmul<T>(cmul<T>(ph[xp], ph[yp]), ph[zp]);
+            const T inv = (T)1 / sqrt((T)q2);
+            kx = fx * inv; ky = fy * inv; kz = fz * inv;
+            kxp = fxp * inv; kyp = fyp * inv; kzp = fzp * inv;
+        }
+        if (a.partner_mode) {
+            T dd = 0, gg = 0;
+            if (own_pair) {
+                // partner grids: interlaced -> G1 | G2 | D one field per grid;
+                // otherwise (G1, G2) packed in one grid, then (D, -)
+                const c2<T>* g0 = a.grids;
+                int slot = 0;
+                c2<T> Dm = mk<T>(0, 0), Dp = Dm, G1m = Dm, G1p = Dm, G2m = Dm, G2p = Dm;
+                if (a.interlace) {
+                    if (a.has_g) {
+                        field_at<T>(g0 + (slot++) * a.grid_stride, 0, 1, c, G1m, G1p);
+                        field_at<T>(g0 + (slot++) * a.grid_stride, 0, 1, c, G2m, G2p);
+                    }
+                    if (a.has_d) field_at<T>(g0 + slot * a.grid_stride, 0, 1, c, Dm, Dp);
+                } else {
+                    if (a.has_g) {
+                        field_at<T>(g0, 0, 0, c, G1m, G1p);
+                        field_at<T>(g0, 1, 0, c, G2m, G2p);
+                        ++slot;
+                    }
+                    if (a.has_d) field_at<T>(g0 + slot * a.grid_stride, 0, 0, c, Dm, Dp);
+                }
+                if (a.has_d) {
+                    a.pD[c.im] = Dm;
+                    a.pD[c.ip] = Dp;
+                    dd = Dm.x * Dm.x + Dm.y * Dm.y;
+                    if (!c.self) dd += Dp.x * Dp.x + Dp.y * Dp.y;
+                }
+                if (a.has_g) {
+                    a.pG1[c.im] = G1m;
+                    a.pG1[c.ip] = G1p;
+                    a.pG2[c.im] = G2m;
+                    a.pG2[c.ip] = G2p;
+                    // G = G1 + i G2: the transform of the complex shear field
+                    const T gr = G1m.x - G2m.y, gi = G1m.y + G2m.x;
+                    gg = gr * gr + gi * gi;
+                    if (!c.self) {
+                        const T hr = G1p.x - G2p.y, hi2 = G1p.y + G2p.x;
+                        gg += hr * hr + hi2 * hi2;
+                    }
+                }
+            }
+            warp_bin_add<T>(dd, (T)0, bin, acc);
+            warp_bin_add<T>(gg, (T)0, bin, acc + 2 * nb);
+        } else {
+            c2<T> Dm = mk<T>(0, 0), Dp = Dm, G1m = Dm, G1p = Dm, G2m = Dm, G2p = Dm;
+            if (own_pair) {
+                if (a.has_d) { Dm = a.pD[c.im]; Dp = a.pD[c.ip]; }
+                if (a.has_g) { G1m = a.pG1[c.im]; G1p = a.pG1[c.ip]; G2m = a.pG2[c.im]; G2p = a.pG2[c.ip]; }
+            }
+            for (int ci = 0; ci < a.n_ch; ++ci) {
+                const CombineChan& ch = a.ch[ci];
+                T tre = 0, tim = 0;
+                if (own_pair) {
+                    c2<T> Fm, Fp;
+                    field_at<T>(a.grids + ch.slot * a.grid_stride, ch.sub, a.interlace, c, Fm, Fp);
+                    if (ch.part == PART_IM) {
+                        Fm = mk<T>(-Fm.y, Fm.x);
+                        Fp = mk<T>(-Fp.y, Fp.x);
+                    }
+                    // partner: delta(-k) = conj D; gamma*(-k) = conj G1 - i conj G2;
+                    // gamma(-k) = conj G1 + i conj G2
+                    c2<T> Pm, Pp;
+                    if (ch.kind == KIND_CROSS) {
+                        Pm = cconj<T>(Dm);
+                        Pp = cconj<T>(Dp);
+                    } else {
+                        const T s = ch.kind == KIND_PLUS ? (T)-1 : (T)1;
+                        // conj(G1) + s i conj(G2)
+                        Pm = mk<T>(G1m.x + s * G2m.y, -G1m.y + s * G2m.x);
+                        Pp = mk<T>(G1p.x + s * G2p.y, -G1p.y + s * G2p.x);
+                    }
+                    const T yn = (T)ch.ynorm;
+                    const T ym = yn * ylm_poly<T>(ch.L, ch.n, kx, ky, kz);
+                    c2<T> t = cscale<T>(cmul<T>(Fm, Pm), ym);
+                    if (!c.self) {
+                        const T yp2 = yn * ylm_poly<T>(ch.L, ch.n, kxp, kyp, kzp);
+                        t = cadd<T>(t, cscale<T>(cmul<T>(Fp, Pp), yp2));
+                    }
+                    tre = t.x;
+                    tim = t.y;
+                }
+                warp_bin_add<T>(tre, tim, bin, acc + ci * 2 * nb);
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < E; i += nthr) {
+            const T v = acc[i];
+            if (v != (T)0) {
+                Owned<T>::add(own + i, own + E + i, v);
+                acc[i] = (T)0;
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < E; i += nthr) {
+        const double v = Owned<T>::value(own + i, own + E + i);
+        if (v != 0.0) {
+            const int ci = i / (2 * nb);
+            const int rem = i - ci * 2 * nb;
+            const int row_out = a.partner_mode ? (ci == 0 ? a.row_dd0 : a.row_plus0) : a.ch[ci].out_row;
+            if (row_out >= 0) atomicAdd(a.out + (long long)row_out * 2 * nb + rem, v);
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_combine(const CombineArgs<T>& a, int n_sm, cudaStream_t st) {
+    const int P = ((a.nk_pos + 1) + 31) / 32 * 32;
+    const int threads = 2 * P;
+    const int nacc = a.partner_mode ? 2 : a.n_ch;
+    const int E = nacc * a.nb * 2;
+    size_t smem = (size_t)E * sizeof(T) * (1 + Owned<T>::words) + (size_t)(a.n + (a.n & 1)) * sizeof(T) +
+                  (size_t)a.n * sizeof(c2<T>) + (size_t)(a.nb + 1) * sizeof(int);
+    cudaFuncSetAttribute(k_combine<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int rows = a.nzi * a.nky;
+    int blocks = n_sm * (threads <= 256 ? 8 : (threads <= 512 ? 4 : 2));
+    if (blocks > rows) blocks = rows;
+    k_combine<T><<<blocks, threads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_combine<float>(const CombineArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_combine<double>(const CombineArgs<double>&, int, cudaStream_t);
+
+}  // namespace lpp

@@ -1,0 +1,187 @@
+// Launch interfaces of the liblpp kernels (internal).
+#pragma once
+
+#include "lpp_internal.h"
+
+namespace lpp {
+
+// ------------------------------------------------------------------------ timing
+// Optional CUDA-event timing of individual launches on the launching stream.
+struct Timer {
+    static constexpr int kMaxEvents = 2048;
+    bool enabled = false;
+    int used = 0;
+    cudaEvent_t ev[kMaxEvents];
+    int kind[kMaxEvents / 2];
+    double bytes[kMaxEvents / 2];
+    bool created = false;
+    double ms[KK_COUNT];
+    long long launches[KK_COUNT];
+    double total_bytes[KK_COUNT];
+
+    void reset() {
+        used = 0;
+        for (int k = 0; k < KK_COUNT; ++k) { ms[k] = 0; launches[k] = 0; total_bytes[k] = 0; }
+    }
+    void begin(int k, cudaStream_t st) {
+        if (!enabled || used + 2 > kMaxEvents) return;
+        cudaEventRecord(ev[used], st);
+        kind[used / 2] = k;
+    }
+    void end(int k, cudaStream_t st, double b) {
+        if (!enabled || used + 2 > kMaxEvents) return;
+        cudaEventRecord(ev[used + 1], st);
+        bytes[used / 2] = b;
+        (void)k;
+        used += 2;
+    }
+    // after the stream is synchronised
+    void collect() {
+        for (int i = 0; i < used; i += 2) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+            ms[kind[i / 2]] += t;
+            launches[kind[i / 2]] += 1;
+            total_bytes[kind[i / 2]] += bytes[i / 2];
+        }
+        used = 0;
+    }
+};
+
+// ------------------------------------------------------------------------- FFT
+struct FftGeom {
+    int W;       // pencils per CTA
+    int nk_pos;  // kept frequencies 0..nk_pos
+    int nk_neg;  // kept frequencies -nk_neg..-1
+    int ntx;     // kept x tiles (of W columns)
+    int nlo;     // x tiles taken from the low end
+    int nky;     // kept y indices
+};
+
+int fft_tile_width(int n);
+FftGeom fft_geometry(int n, int nk_pos, int nk_neg);
+template <typename T>
+cudaError_t fft3d(c2<T>* data, int n_grids, int n, const c2<T>* tw, const FftGeom& g, bool inverse,
+                  cudaStream_t st, Timer* timer);
+
+// ---------------------------------------------------------- per-particle weights
+constexpr int kMaxGroups = 16;
+constexpr int kMaxSlots = 8;       // complex grids per batch
+constexpr int kMaxBatchCh = 16;    // real fields per batch
+
+struct CoeffGroup {
+    int kind;    // Kind
+    int L;
+    int has_im;  // also project the imaginary part of the kernel
+    int row_re;  // first coefficient row of the real part (rows row_re + n + L)
+    int row_im;  // first row of the imaginary part
+    int poly;    // offset of the mu-polynomial in the poly table
+    int npoly;   // number of coefficients
+    int quad;    // index into the quadrature table list (L/2 - 1)
+};
+
+template <typename T>
+struct CoeffArgs {
+    const T* pos;       // [3][count]
+    const T* w;         // [count] or null
+    const T* shape;     // [6 or 2][count]
+    long long count;
+    int shape_kind;
+    double observer[3];
+    double pole[3];
+    double los_global[3];
+    int los_proj, los_est;
+    T* coeff;           // [rows][stride]
+    long long stride;
+    int n_groups;
+    CoeffGroup groups[kMaxGroups];
+    const T* quad_dirs[4];   // per L = 2,4,6,8: [S][3]
+    const T* quad_tab[4];    // per L: [2L+1][S]
+    int quad_S[4];
+    const T* polys;          // concatenated mu-polynomial coefficients
+    double* sums;            // FP64 reductions (see SumSlot)
+    int* err;
+};
+
+enum SumSlot {
+    SUM_W_SHAPES = 0, SUM_W2G2_SHAPES = 1, SUM_W_DENS = 2, SUM_W2_DENS = 3,
+    SUM_W_RAND = 4, SUM_NW2_RAND = 5, SUM_W2_RAND = 6, SUM_ALPHA = 7, SUM_COUNT = 8
+};
+
+// error flag bits
+enum { ERRF_DOMAIN = 1, ERRF_POLE = 2, ERRF_OBSERVER = 4 };
+
+template <typename T>
+cudaError_t launch_coeffs(const CoeffArgs<T>& a, cudaStream_t st);
+
+// plain weight sums of a catalogue: sums[s_w] += w, sums[s_w2] += w^2, sums[s_nw2] += nbar w^2
+template <typename T>
+cudaError_t launch_sums(const T* w, const T* nbar, long long count, double* sums, int s_w, int s_w2, int s_nw2,
+                        cudaStream_t st);
+cudaError_t launch_alpha(double* sums, int has_randoms, cudaStream_t st);
+
+// --------------------------------------------------------------------- assignment
+struct AssignSlot {
+    const void* src_a;   // values for the real part (sub-grid 0), or the field a
+    const void* src_b;   // values for the imaginary part when not interlaced (field b), may be null
+    int grid;            // grid index in the batch
+    int scale_alpha;     // multiply the values by -alpha (randoms into the density field)
+    int unit_a;          // src_a is null: value 1 for every particle
+};
+
+template <typename T>
+struct AssignArgs {
+    const T* pos;
+    long long count;
+    c2<T>* grids;
+    long long grid_stride;
+    int n;
+    double box;
+    double origin[3];
+    int n_slots;
+    AssignSlot slots[kMaxSlots];
+    const double* sums;   // for alpha
+    int* err;
+};
+
+template <typename T>
+cudaError_t launch_assign(const AssignArgs<T>& a, int scheme, int interlace, cudaStream_t st);
+
+// --------------------------------------------------------------------- combine
+struct CombineChan {
+    int slot;      // grid in the batch
+    int sub;       // 0: real-part field (or interlaced pair), 1: imaginary-part field
+    int kind;      // Kind
+    int L, n;      // harmonic
+    int part;      // Part: multiply the field by 1 or by i
+    int out_row;   // row of the FP64 output [row][bin][2]
+    double ynorm;  // normalisation of Y_{L,n}
+};
+
+template <typename T>
+struct CombineArgs {
+    const c2<T>* grids;
+    long long grid_stride;
+    int n;
+    int interlace;
+    int n_ch;
+    CombineChan ch[kMaxBatchCh];
+    // partner spectra (full n^3 arrays, valid on kept modes)
+    c2<T>* pD;
+    c2<T>* pG1;
+    c2<T>* pG2;
+    int partner_mode;      // 1: unpack partners (slots hold D, G1, G2) and sum DD0/PLUS0
+    int has_d, has_g;      // partner fields present
+    int row_dd0, row_plus0;
+    const T* inv_w;        // [n] per-index 1/sinc^p (1 without compensation)
+    const c2<T>* phase;    // [n] per-index e^{-i pi f/n}
+    const int* thr;        // [nb+1] thresholds on n^2
+    int nb;
+    int nk_pos, nk_neg, nky, nzi;
+    double* out;           // [rows][nb][2]
+};
+
+template <typename T>
+cudaError_t launch_combine(const CombineArgs<T>& a, int n_sm, cudaStream_t st);
+
+}  // namespace lpp

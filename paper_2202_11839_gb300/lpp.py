@@ -1,0 +1,264 @@
+"""Thin ctypes binding of liblpp (include/lpp.h).
+
+Argument marshalling only: every step of the estimator runs in the CUDA library.
+Device memory (the plan workspace, device catalogues) and streams come from
+PyTorch.  Importing this module raises if liblpp.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblpp.so")
+
+# ----------------------------------------------------------------- constants
+LPP_OK, LPP_ERR_INVALID_ARG, LPP_ERR_CUDA, LPP_ERR_NOT_READY, LPP_ERR_WORKSPACE, LPP_ERR_UNSUPPORTED, \
+    LPP_ERR_DOMAIN = range(7)
+LPP_CIC, LPP_TSC = 2, 3
+LPP_FP32, LPP_FP64 = 0, 1
+LPP_LOS_LOCAL, LPP_LOS_GLOBAL = 0, 1
+LPP_SHAPES, LPP_DENSITY, LPP_RANDOMS = 0, 1, 2
+LPP_SHAPE_NONE, LPP_SHAPE_GAMMA12, LPP_SHAPE_TENSOR6 = 0, 1, 2
+LPP_N_MOMENTS = 10
+MOMENT_NAMES = ["dd0", "cross2", "cross4", "cross6", "plus0", "plus2", "plus4", "minus4", "minus6", "minus8"]
+LPP_WANT_ALL = 0x3FF
+LPP_WANT_CROSS_B = 1 << 10
+KERNEL_KINDS = ["assign", "fft", "combine", "coeffs", "partner", "other"]
+
+
+class LppError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+class PlanDesc(C.Structure):
+    _fields_ = [
+        ("n", C.c_int), ("box", C.c_double), ("origin", C.c_double * 3), ("observer", C.c_double * 3),
+        ("pole", C.c_double * 3), ("scheme", C.c_int), ("interlace", C.c_int), ("compensate", C.c_int),
+        ("precision", C.c_int), ("los_proj", C.c_int), ("los_est", C.c_int), ("los_global", C.c_double * 3),
+        ("moments", C.c_uint), ("n_bins", C.c_int), ("k_edges", C.POINTER(C.c_double)),
+        ("norm_override", C.c_double), ("subtract_shot", C.c_int), ("max_shapes", C.c_longlong),
+        ("max_density", C.c_longlong), ("max_randoms", C.c_longlong), ("host_inputs", C.c_int),
+        ("batch", C.c_int),
+    ]
+
+
+class Particles(C.Structure):
+    _fields_ = [("pos", C.c_void_p), ("w", C.c_void_p), ("nbar", C.c_void_p), ("shape", C.c_void_p),
+                ("count", C.c_longlong), ("shape_kind", C.c_int), ("on_host", C.c_int)]
+
+
+class Result(C.Structure):
+    _fields_ = [("p", C.POINTER(C.c_double)), ("raw", C.POINTER(C.c_double)), ("k_mean", C.POINTER(C.c_double)),
+                ("n_modes", C.POINTER(C.c_longlong)), ("norm_auto", C.c_double), ("norm_cross", C.c_double),
+                ("norm_dd", C.c_double), ("shot_plus", C.c_double), ("shot_dd", C.c_double),
+                ("alpha", C.c_double)]
+
+
+EXPORTS = {
+    "lpp_plan_create": (C.c_int, [C.POINTER(PlanDesc), C.POINTER(C.c_void_p)]),
+    "lpp_plan_destroy": (None, [C.c_void_p]),
+    "lpp_plan_workspace_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "lpp_plan_set_workspace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "lpp_plan_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lpp_plan_field_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "lpp_assign": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Particles)]),
+    "lpp_clear": (C.c_int, [C.c_void_p, C.c_int]),
+    "lpp_multipoles": (C.c_int, [C.c_void_p, C.POINTER(Result)]),
+    "lpp_derive_eb": (C.c_int, [C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                C.POINTER(C.c_double)]),
+    "lpp_plan_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "lpp_plan_kernel_stats": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                                        C.POINTER(C.c_double)]),
+    "lpp_status_string": (C.c_char_p, [C.c_int]),
+    "lpp_plan_last_error": (C.c_char_p, [C.c_void_p]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load liblpp.so; raises ImportError if it is missing (there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"liblpp.so not built at {path}: run paper_2202_11839_gb300.build")
+    lib = C.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(lib, status: int, plan=None):
+    if status != LPP_OK:
+        msg = lib.lpp_status_string(status).decode()
+        if plan:
+            extra = lib.lpp_plan_last_error(plan).decode()
+            if extra:
+                msg += ": " + extra
+        raise LppError(status, msg)
+
+
+def _ptr(a):
+    """Device or host address of a torch tensor / numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+@dataclass
+class Estimate:
+    p: np.ndarray          # (10, nb) complex, normalised
+    raw: np.ndarray        # (10, nb) complex
+    k_mean: np.ndarray
+    n_modes: np.ndarray
+    norm_auto: float
+    norm_cross: float
+    norm_dd: float
+    shot_plus: float
+    shot_dd: float
+    alpha: float
+    extra: dict = field(default_factory=dict)
+
+
+class Plan:
+    """An LPP estimator plan on the current CUDA device.
+
+    ``workspace`` must be a 256-byte aligned device buffer (a torch uint8 tensor) of at
+    least ``workspace_bytes`` bytes; it is allocated here with torch if not given.
+    """
+
+    def __init__(self, n: int, box: float, k_edges, *, origin=(0.0, 0.0, 0.0), observer=(0.0, 0.0, 0.0),
+                 pole=(-1.0, 0.0, 0.0), scheme: int = LPP_CIC, interlace: bool = False, compensate: bool = True,
+                 precision: int = LPP_FP32, los_proj: int = LPP_LOS_LOCAL, los_est: int = LPP_LOS_LOCAL,
+                 los_global=(0.0, 0.0, 1.0), moments: int = LPP_WANT_ALL, norm_override: float = 0.0,
+                 subtract_shot: bool = True, max_shapes: int = 0, max_density: int = 0, max_randoms: int = 0,
+                 host_inputs: bool = False, batch: int = 0, stream=None, workspace=None, device=None):
+        import torch
+        self.lib = load_library()
+        self.torch = torch
+        self.edges = np.ascontiguousarray(k_edges, dtype=np.float64)
+        self.nb = len(self.edges) - 1
+        d = PlanDesc()
+        d.n, d.box = n, box
+        d.origin[:] = origin
+        d.observer[:] = observer
+        d.pole[:] = pole
+        d.scheme, d.interlace, d.compensate, d.precision = scheme, int(interlace), int(compensate), precision
+        d.los_proj, d.los_est = los_proj, los_est
+        d.los_global[:] = los_global
+        d.moments = moments
+        d.n_bins = self.nb
+        d.k_edges = self.edges.ctypes.data_as(C.POINTER(C.c_double))
+        d.norm_override, d.subtract_shot = norm_override, int(subtract_shot)
+        d.max_shapes, d.max_density, d.max_randoms = max_shapes, max_density, max_randoms
+        d.host_inputs, d.batch = int(host_inputs), batch
+        self.desc = d
+        self.precision = precision
+        self.dtype = np.float64 if precision == LPP_FP64 else np.float32
+        self.tdtype = torch.float64 if precision == LPP_FP64 else torch.float32
+        h = C.c_void_p()
+        _check(self.lib, self.lib.lpp_plan_create(C.byref(d), C.byref(h)))
+        self.h = h
+        sz = C.c_size_t()
+        _check(self.lib, self.lib.lpp_plan_workspace_size(h, C.byref(sz)), h)
+        self.workspace_bytes = sz.value
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        _check(self.lib, self.lib.lpp_plan_set_stream(h, C.c_void_p(self.stream.cuda_stream)), h)
+        if workspace is None:
+            workspace = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
+        addr = workspace.data_ptr()
+        off = (-addr) % 256
+        self.workspace = workspace
+        _check(self.lib, self.lib.lpp_plan_set_workspace(h, C.c_void_p(addr + off),
+                                                         C.c_size_t(workspace.numel() - off)), h)
+        self._keep = {}
+
+    def field_count(self) -> int:
+        v = C.c_int()
+        _check(self.lib, self.lib.lpp_plan_field_count(self.h, C.byref(v)), self.h)
+        return v.value
+
+    def set_timing(self, on: bool = True):
+        _check(self.lib, self.lib.lpp_plan_set_timing(self.h, int(on)), self.h)
+
+    def kernel_stats(self) -> dict:
+        out = {}
+        for k, name in enumerate(KERNEL_KINDS):
+            ms, nl, b = C.c_double(), C.c_longlong(), C.c_double()
+            _check(self.lib, self.lib.lpp_plan_kernel_stats(self.h, k, C.byref(ms), C.byref(nl), C.byref(b)), self.h)
+            out[name] = {"ms": ms.value, "launches": nl.value, "bytes": b.value}
+        return out
+
+    def assign(self, role: int, pos, w=None, nbar=None, shape=None, shape_kind: int = LPP_SHAPE_NONE):
+        """Attach a catalogue: torch CUDA tensors (referenced) or numpy arrays (copied)."""
+        on_host = not hasattr(pos, "data_ptr") or not pos.is_cuda
+        arrs = [pos, w, nbar, shape]
+        for a in arrs:
+            if a is None:
+                continue
+            if hasattr(a, "data_ptr"):
+                if a.dtype != self.tdtype or not a.is_contiguous():
+                    raise ValueError("catalogue tensors must be contiguous and match the plan precision")
+            else:
+                if a.dtype != self.dtype or not a.flags["C_CONTIGUOUS"]:
+                    raise ValueError("catalogue arrays must be C-contiguous and match the plan precision")
+        count = int(pos.shape[-1])
+        p = Particles(_ptr(pos), _ptr(w), _ptr(nbar), _ptr(shape), count, shape_kind, int(on_host))
+        self._keep[role] = arrs
+        _check(self.lib, self.lib.lpp_assign(self.h, role, C.byref(p)), self.h)
+
+    def clear(self, role: int):
+        _check(self.lib, self.lib.lpp_clear(self.h, role), self.h)
+        self._keep.pop(role, None)
+
+    def multipoles(self) -> Estimate:
+        nb = self.nb
+        p = np.zeros((LPP_N_MOMENTS, nb, 2))
+        raw = np.zeros((LPP_N_MOMENTS, nb, 2))
+        km = np.zeros(nb)
+        nm = np.zeros(nb, dtype=np.int64)
+        r = Result()
+        r.p = p.ctypes.data_as(C.POINTER(C.c_double))
+        r.raw = raw.ctypes.data_as(C.POINTER(C.c_double))
+        r.k_mean = km.ctypes.data_as(C.POINTER(C.c_double))
+        r.n_modes = nm.ctypes.data_as(C.POINTER(C.c_longlong))
+        _check(self.lib, self.lib.lpp_multipoles(self.h, C.byref(r)), self.h)
+        return Estimate(p[..., 0] + 1j * p[..., 1], raw[..., 0] + 1j * raw[..., 1], km, nm, r.norm_auto,
+                        r.norm_cross, r.norm_dd, r.shot_plus, r.shot_dd, r.alpha)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lpp_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def derive_eb(p: np.ndarray):
+    """Legendre multipoles (gE l=0,2; EE, BB l=0,2,4) from normalised native moments (10, nb) complex."""
+    lib = load_library()
+    nb = p.shape[1]
+    pr = np.ascontiguousarray(np.stack([p.real, p.imag], axis=-1), dtype=np.float64)
+    ge = np.zeros((2, nb))
+    ee = np.zeros((3, nb))
+    bb = np.zeros((3, nb))
+    dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    _check(lib, lib.lpp_derive_eb(dp(pr), nb, dp(ge), dp(ee), dp(bb)))
+    return ge, ee, bb

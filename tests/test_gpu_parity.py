@@ -1,0 +1,188 @@
+"""CUDA path vs the FP64 oracle, element by element over every moment and shell.
+
+Tolerances: relative to the per-bin scale |P| + sqrt(P_+^(0) P_dd^(0)); 1e-10 for the
+FP64 path and 1e-5 for the FP32 bulk path (FP32 grids and products, FP64 shell sums).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import lpp_oracle as O
+from tests import parity_util as U
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2202_11839_gb300 import lpp
+    lpp.load_library()
+    return lpp
+
+
+def _cfg(n, box, **kw):
+    c = dict(n=n, box=box, observer=(box / 2, box / 2, -800.0), scheme=2, interlace=False,
+             k_edges=U.default_edges(n, box, kw.pop("nb", 8), kw.pop("frac", 1.0)))
+    c.update(kw)
+    return c
+
+
+CASES64 = {
+    "cic_periodic": (_cfg(16, 300.0), dict(count=1500)),
+    "tsc_interlaced_randoms_density": (_cfg(16, 300.0, scheme=3, interlace=True),
+                                       dict(count=1200, n_rand=3000, separate_density=True)),
+    "gpp_global_los": (_cfg(16, 300.0, los_proj=1, los_est=1, los_global=(0.2, -0.1, 0.97)), dict(count=1000)),
+    "inconsistent_los_case_b": (_cfg(16, 300.0, los_proj=0, los_est=1), dict(count=1000)),
+    "pruned_k_range_n32": (_cfg(32, 400.0, scheme=3, interlace=True, frac=0.35, nb=5), dict(count=2500)),
+    "no_compensation_gamma12": (_cfg(16, 250.0, compensate=False), dict(count=900, gamma12=True)),
+    "tiny_grid_n8": (_cfg(8, 100.0, scheme=3, nb=3), dict(count=300)),
+    "batch1_ragged": (_cfg(16, 300.0, batch=1, scheme=3, interlace=True), dict(count=700)),
+    "batch3_noninterlaced": (_cfg(16, 300.0, batch=3), dict(count=700)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES64))
+def test_fp64_parity(L, name):
+    cfg, ck = CASES64[name]
+    cat = U.make_case(name, cfg["n"], seed=11, box=cfg["box"], dtype=np.float64, **ck)
+    ref = U.run_oracle(cfg, cat)
+    gpu = U.run_gpu(cfg, cat, L.LPP_FP64)
+    U.assert_parity(gpu, ref, TOL64, name)
+
+
+CASES32 = {
+    "tsc_interlaced_n32": (_cfg(32, 500.0, scheme=3, interlace=True), dict(count=6000)),
+    "cic_randoms_n32": (_cfg(32, 500.0, scheme=2, frac=0.5), dict(count=4000, n_rand=12000)),
+    "gamma12_n64_pruned": (_cfg(64, 800.0, scheme=3, interlace=True, frac=0.4, nb=6), dict(count=5000, gamma12=True)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES32))
+def test_fp32_parity(L, name):
+    cfg, ck = CASES32[name]
+    cat = U.make_case(name, cfg["n"], seed=5, box=cfg["box"], dtype=np.float32, **ck)
+    ref = U.run_oracle(cfg, cat)
+    gpu = U.run_gpu(cfg, cat, L.LPP_FP32)
+    U.assert_parity(gpu, ref, TOL32, name)
+
+
+def test_host_inputs_match_device_inputs(L):
+    cfg, ck = CASES32["tsc_interlaced_n32"]
+    cat = U.make_case("h", cfg["n"], seed=9, box=cfg["box"], dtype=np.float32, **ck)
+    a = U.run_gpu(cfg, cat, L.LPP_FP32, device_inputs=True)
+    b = U.run_gpu(cfg, cat, L.LPP_FP32, device_inputs=False)
+    ref = U.run_oracle(cfg, cat)
+    sc = U.scale(ref)
+    assert np.max(np.abs(a.p - b.p) / np.where(sc > 0, sc, 1)) < 1e-6
+
+
+def test_repeat_runs_agree(L):
+    """Atomic accumulation order varies between runs; results stay within the FP32 tolerance."""
+    cfg, ck = CASES32["cic_randoms_n32"]
+    cat = U.make_case("r", cfg["n"], seed=3, box=cfg["box"], dtype=np.float32, **ck)
+    ref = U.run_oracle(cfg, cat)
+    a = U.run_gpu(cfg, cat, L.LPP_FP32)
+    b = U.run_gpu(cfg, cat, L.LPP_FP32)
+    sc = U.scale(ref)
+    assert np.max(np.abs(a.p - b.p) / np.where(sc > 0, sc, 1)) < 1e-6
+
+
+def test_particle_outside_box_is_an_error(L):
+    import torch
+    cfg = _cfg(16, 100.0)
+    cat = U.make_case("o", 16, count=50, seed=1, box=100.0, dtype=np.float64)
+    cat["pos"][0, 3] = 100.5   # beyond origin + box
+    with pytest.raises(L.LppError) as ei:
+        U.run_gpu(cfg, cat, L.LPP_FP64)
+    assert ei.value.status == L.LPP_ERR_DOMAIN
+
+
+def test_upper_face_wraps_to_zero(L):
+    """A particle exactly on origin + box is accepted and wraps onto node 0 (periodic)."""
+    cfg = _cfg(16, 100.0)
+    cat = U.make_case("f", 16, count=60, seed=2, box=100.0, dtype=np.float64)
+    cat["pos"][:, 0] = (100.0, 50.0, 100.0)
+    ref = U.run_oracle(cfg, cat)
+    gpu = U.run_gpu(cfg, cat, L.LPP_FP64)
+    U.assert_parity(gpu, ref, TOL64, "upper face")
+
+
+def test_particle_on_frame_pole_is_an_error(L):
+    cfg = _cfg(16, 100.0, observer=(50.0, 50.0, 50.0), pole=(0.0, 0.0, 1.0))
+    cat = U.make_case("p", 16, count=40, seed=4, box=100.0, dtype=np.float64)
+    cat["pos"][:, 7] = (50.0, 50.0, 80.0)   # straight above the observer, on the pole
+    with pytest.raises(L.LppError) as ei:
+        U.run_gpu(cfg, cat, L.LPP_FP64)
+    assert ei.value.status == L.LPP_ERR_DOMAIN
+
+
+def test_on_node_512_matches_direct_sum(L):
+    """Full 512^3 grid (the timed configuration's size) with particles on nodes, CIC, no window
+    deconvolution: the lowest shells equal the direct, unexpanded per-mode sums exactly
+    (to FP32 rounding), which exercises every FFT pass, pruning and the combine at size."""
+    n, box = 512, 4000.0
+    rng = np.random.default_rng(12)
+    cnt = 400
+    cells = rng.integers(0, n, (3, cnt))
+    h = box / n
+    pos = (cells * h).astype(np.float32)
+    shape = rng.standard_normal((6, cnt)).astype(np.float32)
+    w = rng.uniform(0.5, 1.5, cnt).astype(np.float32)
+    edges = np.array([0.0, 0.004, 0.007, 0.01])
+    obs = (2000.0, 2000.0, 200.0)
+    cfg = dict(n=n, box=box, observer=obs, scheme=2, interlace=False, compensate=False, k_edges=edges,
+               norm_override=1.0, subtract_shot=False, cross_b=True)
+    gpu = U.run_gpu(cfg, dict(pos=pos, w=w, shape=shape), L.LPP_FP32)
+    # direct sums over every mode of the three shells
+    kf = 2 * math.pi / box
+    m = int(edges[-1] / kf) + 1
+    f = np.arange(-m, m + 1)
+    fx, fy, fz = np.meshgrid(f, f, f, indexing="ij")
+    q = (fx ** 2 + fy ** 2 + fz ** 2).ravel()
+    kint = np.stack([fx.ravel(), fy.ravel(), fz.ravel()], 1)
+    kmag = kf * np.sqrt(q)
+    b = np.searchsorted(edges, kmag, side="right") - 1
+    sel = (q > 0) & (b >= 0) & (b < len(edges) - 1)
+    kint, b = kint[sel], b[sel]
+    kvec = kint * kf
+    khat = kint / np.linalg.norm(kint, axis=1)[:, None]
+    p64 = pos.astype(np.float64)
+    xh = O.line_of_sight(p64, obs)
+    et, ep = O.sky_frame(xh, (-1, 0, 0))
+    g = O.shear(shape.astype(np.float64), None, O.helicity_tensor(et, ep))
+    w64 = w.astype(np.float64)
+    D = O.direct_ft(kvec, p64, np.broadcast_to(w64, (len(kvec), cnt)))
+    G = O.direct_ft(kvec, p64, np.broadcast_to(w64 * g, (len(kvec), cnt)))
+    Gc = O.direct_ft(kvec, p64, np.broadcast_to(w64 * np.conj(g), (len(kvec), cnt)))
+    nmodes = np.bincount(b, minlength=3)
+    np.testing.assert_array_equal(gpu.n_modes, nmodes)
+    partner = {"cross": np.conj(D), "plus": np.conj(G), "minus": np.conj(Gc)}
+    for (kind, Lm) in [("cross", 2), ("cross", 4), ("plus", 2), ("minus", 4), ("minus", 8)]:
+        F = O.direct_ft(kvec, p64, w64[None, :] * O.direct_kernel(kind, Lm, khat, xh, et, ep, g))
+        fac = O.norm_factor({"cross": 2, "plus": 0, "minus": 4}[kind], Lm)
+        val = F * partner[kind]
+        want = fac * (np.bincount(b, weights=val.real, minlength=3) + 1j * np.bincount(b, weights=val.imag, minlength=3)) / nmodes
+        got = gpu.p[O.M_INDEX[(kind, Lm)]]
+        ref_scale = np.sqrt((np.bincount(b, weights=np.abs(G) ** 2, minlength=3) / nmodes) *
+                            (np.bincount(b, weights=np.abs(D) ** 2, minlength=3) / nmodes))
+        assert np.max(np.abs(got - want) / (np.abs(want) + ref_scale)) < TOL32, (kind, Lm)
+
+
+@pytest.mark.slow
+def test_periodic_fp64_workload_full_size(L):
+    """The FP64 periodic workload at full size: 64^3 CIC, 50k galaxies, 20 bins to k_Ny."""
+    from paper_2202_11839_gb300 import synthetic as S
+    wl = S.workload_periodic_fp64()
+    cat = dict(pos=wl.shapes.pos, shape=wl.shapes.shape)
+    cfg = dict(n=wl.n, box=wl.box, observer=wl.observer, pole=wl.pole, scheme=wl.scheme,
+               interlace=wl.interlace, k_edges=wl.k_edges, cross_b=False)
+    ref = U.run_oracle(cfg, cat)
+    gpu = U.run_gpu(cfg, cat, L.LPP_FP64)
+    U.assert_parity(gpu, ref, TOL64, wl.name)
