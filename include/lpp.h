@@ -167,6 +167,28 @@ lpp_status lpp_plan_set_timing(lpp_plan_t plan, int enable);
 lpp_status lpp_plan_kernel_stats(lpp_plan_t plan, int kind, double* ms, long long* launches,
                                  double* bytes);
 
+/* Density monopole P_dd^(0) of a periodic catalogue without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc (code running inside another framework's memory pool or under a fixed
+ * per-process memory cap, plug-ins handed a stream but no allocator).  It runs the
+ * same assignment, FFT and shell-sum kernels as the LPP_MOM_DD0 slot of
+ * lpp_multipoles for a periodic box (I = (sum w)^2/V, shot noise sum w^2 / I always
+ * subtracted), but keeps every intermediate in one fixed 40 MiB device array inside
+ * the library, which each GPU that loads liblpp holds until the process exits.
+ *  - Sizes: FP32 grids up to n = 128, FP64 grids up to n = 64; larger grids return
+ *    LPP_ERR_WORKSPACE.  n_bins <= 256.
+ *  - pos [3][count] and w [count] (or NULL) are device pointers of the given precision;
+ *    p_out [n_bins] and n_modes_out [n_bins] (or NULL) are host memory.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *    and caches it; make that first call before any stream capture on the device.
+ *  - All calls share the one array: calls that overlap on the GPU (other streams or
+ *    other host threads) race and corrupt each other's results.  Each call clears what
+ *    it accumulates into and synchronises `stream` before returning. */
+lpp_status lpp_density_monopole_static(int n, double box, const double* origin, int scheme, int interlace,
+                                       int compensate, int precision, const void* pos, const void* w,
+                                       long long count, int n_bins, const double* k_edges, double* p_out,
+                                       long long* n_modes_out, void* stream);
+
 const char* lpp_status_string(lpp_status status);
 /* Last error message recorded on this plan (empty string if none). */
 const char* lpp_plan_last_error(lpp_plan_t plan);

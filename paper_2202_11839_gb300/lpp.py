@@ -75,6 +75,10 @@ EXPORTS = {
     "lpp_plan_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "lpp_plan_kernel_stats": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                                         C.POINTER(C.c_double)]),
+    "lpp_density_monopole_static": (C.c_int, [C.c_int, C.c_double, C.POINTER(C.c_double), C.c_int, C.c_int, C.c_int,
+                                              C.c_int, C.c_void_p, C.c_void_p, C.c_longlong, C.c_int,
+                                              C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                              C.POINTER(C.c_longlong), C.c_void_p]),
     "lpp_status_string": (C.c_char_p, [C.c_int]),
     "lpp_plan_last_error": (C.c_char_p, [C.c_void_p]),
 }
