@@ -133,8 +133,9 @@ __global__ void __launch_bounds__(256) k_coeffs(CoeffArgs<T> a) {
     double sw = 0.0, sg = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.count;
          i += (long long)gridDim.x * blockDim.x) {
+        const long long si = a.perm ? (long long)a.perm[i] : i;  // input index of output particle i
         T xl[3];
-        unit_los(a.pos, a.count, i, a.observer, xl, a.err);
+        unit_los(a.pos, a.count, si, a.observer, xl, a.err);
         T xg[3] = {(T)a.los_global[0], (T)a.los_global[1], (T)a.los_global[2]};
         const T* xp = a.los_proj == LPP_LOS_GLOBAL ? xg : xl;
         const T* xe = a.los_est == LPP_LOS_GLOBAL ? xg : xl;
@@ -149,8 +150,8 @@ __global__ void __launch_bounds__(256) k_coeffs(CoeffArgs<T> a) {
         if (a.shape_kind == LPP_SHAPE_TENSOR6) {
             const T* s = a.shape;
             const long long c = a.count;
-            const T sxx = s[i], syy = s[c + i], szz = s[2 * c + i], sxy = s[3 * c + i], sxz = s[4 * c + i],
-                    syz = s[5 * c + i];
+            const T sxx = s[si], syy = s[c + si], szz = s[2 * c + si], sxy = s[3 * c + si], sxz = s[4 * c + si],
+                    syz = s[5 * c + si];
             const T st0 = sxx * etp[0] + sxy * etp[1] + sxz * etp[2];
             const T st1 = sxy * etp[0] + syy * etp[1] + syz * etp[2];
             const T st2 = sxz * etp[0] + syz * etp[1] + szz * etp[2];
@@ -163,10 +164,10 @@ __global__ void __launch_bounds__(256) k_coeffs(CoeffArgs<T> a) {
             g1 = (T)0.5 * (stt - spp);  // gamma = e_ij s_ij (Eq. gamma_def)
             g2 = stp;
         } else {
-            g1 = a.shape[i];
-            g2 = a.shape[a.count + i];
+            g1 = a.shape[si];
+            g2 = a.shape[a.count + si];
         }
-        const T w = a.w ? a.w[i] : (T)1;
+        const T w = a.w ? a.w[si] : (T)1;
         a.coeff[i] = w * g1;              // row 0: w gamma_1
         a.coeff[a.stride + i] = w * g2;   // row 1: w gamma_2
         sw += (double)w;

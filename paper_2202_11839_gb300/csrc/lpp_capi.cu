@@ -61,6 +61,10 @@ struct lpp_plan_s {
     size_t off_sums = 0, off_err = 0, off_out = 0, off_thr = 0, off_tw = 0, off_iw = 0, off_ph = 0;
     size_t off_quad_dirs[4] = {0}, off_quad_tab[4] = {0}, off_polys = 0, off_coeff = 0;
     size_t off_partner = 0, off_grids = 0, off_stage[3] = {0, 0, 0};
+    // pencil-sorted catalogues: key, cell coordinates, weights, key offsets; shapes permutation
+    size_t off_key[3] = {0, 0, 0}, off_su[3] = {0, 0, 0}, off_sw[3] = {0, 0, 0}, off_koff[3] = {0, 0, 0};
+    size_t off_perm = 0, off_counts = 0, off_cursor = 0;
+    int fty = 4, ftz = 4;
     int n_partner = 0;
     int out_rows = 0;
     bool tables_ready = false;
@@ -260,6 +264,22 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
     }
     plan->off_polys = take(std::max<size_t>(1, plan->polys.size()) * es);
     plan->off_coeff = take((size_t)plan->n_coeff_rows * std::max<long long>(1, d.max_shapes) * es);
+    {
+        int ipt, thr;
+        size_t sm;
+        fused_geometry(n, es, &plan->fty, &plan->ftz, &ipt, &thr, &sm);
+    }
+    const long long caps[3] = {std::max<long long>(1, d.max_shapes), std::max<long long>(1, d.max_density),
+                               std::max<long long>(1, d.max_randoms)};
+    for (int r = 0; r < 3; ++r) {
+        plan->off_key[r] = take((size_t)caps[r] * sizeof(int));
+        plan->off_su[r] = take((size_t)3 * caps[r] * es);
+        plan->off_sw[r] = take((size_t)caps[r] * es);
+        plan->off_koff[r] = take(((size_t)n * n + 1) * sizeof(int));
+    }
+    plan->off_perm = take((size_t)caps[0] * sizeof(int));
+    plan->off_counts = take((size_t)n * n * sizeof(int));
+    plan->off_cursor = take((size_t)n * n * sizeof(int));
     plan->off_partner = take((size_t)plan->n_partner * n3 * cs);
     plan->off_grids = take((size_t)plan->batch * n3 * cs);
     if (d.host_inputs) {
@@ -458,9 +478,29 @@ static lpp_status run(lpp_plan_t plan, lpp_result* res) {
     LPP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
     LPP_CUDA(cudaMemsetAsync(out, 0, (size_t)plan->out_rows * nb * 2 * sizeof(double), st));
 
-    // 1. sky frames, shears and harmonic weights of the shape catalogue
+    // 0. pencil sort of every catalogue (cell coordinates and weights in x-pencil key order)
+    const long long caps[3] = {std::max<long long>(1, plan->d.max_shapes), std::max<long long>(1, plan->d.max_density),
+                               std::max<long long>(1, plan->d.max_randoms)};
+    int* perm = (int*)(plan->ws + plan->off_perm);
+    auto sort_cat = [&](int role, const Catalogue& c) -> lpp_status {
+        if (tm) tm->begin(KK_OTHER, st);
+        LPP_CUDA(launch_pencil_sort<T>((const T*)c.pos, (const T*)c.w, c.count, caps[role], n, plan->box,
+                                       plan->d.origin, (int*)(plan->ws + plan->off_key[role]),
+                                       (int*)(plan->ws + plan->off_counts), (int*)(plan->ws + plan->off_koff[role]),
+                                       (int*)(plan->ws + plan->off_cursor), (T*)(plan->ws + plan->off_su[role]),
+                                       (T*)(plan->ws + plan->off_sw[role]), role == LPP_SHAPES ? perm : nullptr, err,
+                                       st));
+        if (tm) tm->end(KK_OTHER, st, (double)c.count * (plan->es * 8 + 12));
+        return LPP_OK;
+    };
+    { lpp_status s0 = sort_cat(LPP_SHAPES, sh); if (s0 != LPP_OK) return s0; }
+    if (plan->cat[LPP_DENSITY].set) { lpp_status s0 = sort_cat(LPP_DENSITY, de); if (s0 != LPP_OK) return s0; }
+    if (has_rand) { lpp_status s0 = sort_cat(LPP_RANDOMS, ra); if (s0 != LPP_OK) return s0; }
+
+    // 1. sky frames, shears and harmonic weights of the shape catalogue (in sorted order)
     CoeffArgs<T> ca;
     memset(&ca, 0, sizeof(ca));
+    ca.perm = perm;
     ca.pos = (const T*)sh.pos;
     ca.w = (const T*)sh.w;
     ca.shape = (const T*)sh.shape;
@@ -535,22 +575,30 @@ static lpp_status run(lpp_plan_t plan, lpp_result* res) {
     cb.row_dd0 = n_ch;
     cb.row_plus0 = n_ch + 1;
 
-    AssignArgs<T> aa;
-    memset(&aa, 0, sizeof(aa));
-    aa.grids = grids;
-    aa.grid_stride = (long long)n3;
-    aa.n = n;
-    aa.box = plan->box;
-    for (int a = 0; a < 3; ++a) aa.origin[a] = plan->d.origin[a];
-    aa.sums = sums;
-    aa.err = err;
-    const double pbytes = (double)plan->es;
-    auto assign_cat = [&](const Catalogue& c) -> lpp_status {
-        aa.pos = (const T*)c.pos;
-        aa.count = c.count;
+    FusedArgs<T> fa;
+    memset(&fa, 0, sizeof(fa));
+    for (int r = 0; r < 3; ++r) {
+        fa.cat[r].su = plan->ws + plan->off_su[r];
+        fa.cat[r].sw = plan->ws + plan->off_sw[r];
+        fa.cat[r].off = (const int*)(plan->ws + plan->off_koff[r]);
+        fa.cat[r].cap = caps[r];
+    }
+    fa.grids = grids;
+    fa.grid_stride = (long long)n3;
+    fa.n = n;
+    fa.ty = plan->fty;
+    fa.tz = plan->ftz;
+    fa.scheme = plan->d.scheme;
+    fa.interlace = plan->d.interlace;
+    fa.nk_pos = plan->nk_pos;
+    fa.nk_neg = plan->nk_neg;
+    fa.tw = tw;
+    fa.sums = sums;
+    const double xbytes = (double)n * n * plan->nky * sizeof(c2<T>);   // kept x pencils of one grid
+    auto assign_fused = [&](long long particles) -> lpp_status {
         if (tm) tm->begin(KK_ASSIGN, st);
-        LPP_CUDA(launch_assign<T>(aa, plan->d.scheme, plan->d.interlace, st));
-        if (tm) tm->end(KK_ASSIGN, st, (double)c.count * pbytes * (3 + aa.n_slots));
+        LPP_CUDA(launch_assign_xfft<T>(fa, st));
+        if (tm) tm->end(KK_ASSIGN, st, fa.n_slots * (xbytes + (double)particles * 4 * plan->es));
         return LPP_OK;
     };
 
@@ -560,41 +608,44 @@ static lpp_status run(lpp_plan_t plan, lpp_result* res) {
 
     // 2. partner fields: G1, G2 (shapes) and D = density - alpha randoms
     const int il = plan->d.interlace;
+    const int dens_cat = plan->cat[LPP_DENSITY].set ? LPP_DENSITY : LPP_SHAPES;
     int pgrids = 0;
     {
-        LPP_CUDA(cudaMemsetAsync(grids, 0, (size_t)plan->batch * n3 * sizeof(c2<T>), st));
-        // slots written from the shape catalogue
-        aa.n_slots = 0;
-        int g_slot = 0, d_slot = -1;
+        fa.n_slots = 0;
+        long long parts = 0;
         if (plan->need_g) {
             if (il) {
-                aa.slots[aa.n_slots++] = AssignSlot{coeff, nullptr, 0, 0, 0};
-                aa.slots[aa.n_slots++] = AssignSlot{coeff + stride, nullptr, 1, 0, 0};
-                g_slot = 2;
+                FusedSlot g1{};
+                g1.n_src = 1;
+                g1.src[0] = FusedSrc{LPP_SHAPES, coeff, 0};
+                g1.grid = pgrids++;
+                fa.slots[fa.n_slots++] = g1;
+                FusedSlot g2{};
+                g2.n_src = 1;
+                g2.src[0] = FusedSrc{LPP_SHAPES, coeff + stride, 0};
+                g2.grid = pgrids++;
+                fa.slots[fa.n_slots++] = g2;
             } else {
-                aa.slots[aa.n_slots++] = AssignSlot{coeff, coeff + stride, 0, 0, 0};
-                g_slot = 1;
+                FusedSlot g{};
+                g.n_src = 1;
+                g.src[0] = FusedSrc{LPP_SHAPES, coeff, 0};
+                g.vals_b = coeff + stride;
+                g.grid = pgrids++;
+                fa.slots[fa.n_slots++] = g;
             }
+            parts += sh.count;
         }
-        if (plan->need_d) d_slot = g_slot;
-        pgrids = plan->need_d ? d_slot + 1 : g_slot;
-        const bool dens_is_shapes = !plan->cat[LPP_DENSITY].set;
-        if (plan->need_d && dens_is_shapes)
-            aa.slots[aa.n_slots++] = AssignSlot{sh.w, nullptr, d_slot, 0, sh.w == nullptr};
-        if (aa.n_slots > 0 && sh.count > 0) { lpp_status s = assign_cat(sh); if (s != LPP_OK) return s; }
-        if (plan->need_d && !dens_is_shapes) {
-            aa.n_slots = 1;
-            aa.slots[0] = AssignSlot{de.w, nullptr, d_slot, 0, de.w == nullptr};
-            lpp_status s = assign_cat(de);
-            if (s != LPP_OK) return s;
+        if (plan->need_d) {
+            FusedSlot dsl{};
+            dsl.n_src = 1;
+            dsl.src[0] = FusedSrc{dens_cat, nullptr, 0};
+            if (has_rand) dsl.src[dsl.n_src++] = FusedSrc{LPP_RANDOMS, nullptr, 1};
+            dsl.grid = pgrids++;
+            fa.slots[fa.n_slots++] = dsl;
+            parts += de.count + (has_rand ? ra.count : 0);
         }
-        if (plan->need_d && has_rand) {
-            aa.n_slots = 1;
-            aa.slots[0] = AssignSlot{ra.w, nullptr, d_slot, 1, ra.w == nullptr};
-            lpp_status s = assign_cat(ra);
-            if (s != LPP_OK) return s;
-        }
-        LPP_CUDA(fft3d<T>(grids, pgrids, n, tw, geom, false, st, tm));
+        { lpp_status s0 = assign_fused(parts); if (s0 != LPP_OK) return s0; }
+        LPP_CUDA(fft_yz<T>(grids, pgrids, n, tw, geom, false, st, tm));
         cb.partner_mode = 1;
         cb.has_d = plan->need_d;
         cb.has_g = plan->need_g;
@@ -611,16 +662,18 @@ static lpp_status run(lpp_plan_t plan, lpp_result* res) {
         const int c1 = std::min(n_ch, c0 + plan->batch_ch);
         const int nch = c1 - c0;
         const int ngr = (nch + per_grid - 1) / per_grid;
-        LPP_CUDA(cudaMemsetAsync(grids, 0, (size_t)ngr * n3 * sizeof(c2<T>), st));
-        aa.n_slots = 0;
+        fa.n_slots = 0;
         cb.n_ch = nch;
         cb.has_d = 0;
         cb.has_g = 0;
         for (int gi = 0; gi < ngr; ++gi) {
             const int ca0 = c0 + gi * per_grid;
-            const T* sa = coeff + (long long)plan->channels[ca0].coeff * stride;
-            const T* sb = (!il && ca0 + 1 < c1) ? coeff + (long long)plan->channels[ca0 + 1].coeff * stride : nullptr;
-            aa.slots[aa.n_slots++] = AssignSlot{sa, sb, gi, 0, 0};
+            FusedSlot fs{};
+            fs.n_src = 1;
+            fs.src[0] = FusedSrc{LPP_SHAPES, coeff + (long long)plan->channels[ca0].coeff * stride, 0};
+            fs.vals_b = (!il && ca0 + 1 < c1) ? coeff + (long long)plan->channels[ca0 + 1].coeff * stride : nullptr;
+            fs.grid = gi;
+            fa.slots[fa.n_slots++] = fs;
         }
         for (int ci = 0; ci < nch; ++ci) {
             const Channel& ch = plan->channels[c0 + ci];
@@ -635,8 +688,8 @@ static lpp_status run(lpp_plan_t plan, lpp_result* res) {
             cc.ynorm = ylm_norm(ch.L, ch.n);
             if (ch.kind == KIND_CROSS) cb.has_d = 1; else cb.has_g = 1;
         }
-        { lpp_status s = assign_cat(sh); if (s != LPP_OK) return s; }
-        LPP_CUDA(fft3d<T>(grids, ngr, n, tw, geom, false, st, tm));
+        { lpp_status s0 = assign_fused(sh.count); if (s0 != LPP_OK) return s0; }
+        LPP_CUDA(fft_yz<T>(grids, ngr, n, tw, geom, false, st, tm));
         if (tm) tm->begin(KK_COMBINE, st);
         LPP_CUDA(launch_combine<T>(cb, plan->n_sm, st));
         if (tm) tm->end(KK_COMBINE, st, shell_modes * sizeof(c2<T>) * (ngr + (cb.has_d ? 1 : 0) + (cb.has_g ? 2 : 0)));

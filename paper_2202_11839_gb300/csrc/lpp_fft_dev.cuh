@@ -1,0 +1,138 @@
+// Device-side building blocks of the shared-memory pencil FFT (internal).
+//
+// A tile holds W pencils of N complex points in shared memory as tile[e * ld + c]
+// (point e of pencil c, ld >= W).  Every thread owns IPT pencils c, c + W/IPT, ...
+// and, in each Stockham stage, the 8 points of one radix-8 butterfly (or two radix-4 /
+// four radix-2 butterflies) of each of them.  Consecutive threads own consecutive
+// pencils, so shared-memory accesses of a warp are contiguous.
+#pragma once
+
+#include "lpp_internal.h"
+
+namespace lpp {
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft4(c2<T>* v) {
+    c2<T> a0 = cadd<T>(v[0], v[2]), a1 = csub<T>(v[0], v[2]);
+    c2<T> b0 = cadd<T>(v[1], v[3]), b1 = csub<T>(v[1], v[3]);
+    b1 = INV ? mk<T>(-b1.y, b1.x) : mk<T>(b1.y, -b1.x);  // * (+i) or * (-i)
+    v[0] = cadd<T>(a0, b0);
+    v[2] = csub<T>(a0, b0);
+    v[1] = cadd<T>(a1, b1);
+    v[3] = csub<T>(a1, b1);
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft2(c2<T>* v) {
+    c2<T> a = v[0];
+    v[0] = cadd<T>(a, v[1]);
+    v[1] = csub<T>(a, v[1]);
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft8(c2<T>* v) {
+    c2<T> e[4] = {v[0], v[2], v[4], v[6]};
+    c2<T> o[4] = {v[1], v[3], v[5], v[7]};
+    dft4<T, INV>(e);
+    dft4<T, INV>(o);
+    const T r = (T)0.70710678118654752440;
+    c2<T> t1, t2, t3;
+    if (!INV) {
+        t1 = mk<T>((o[1].x + o[1].y) * r, (o[1].y - o[1].x) * r);   // * (1 - i)/sqrt2
+        t2 = mk<T>(o[2].y, -o[2].x);                               // * (-i)
+        t3 = mk<T>((o[3].y - o[3].x) * r, -(o[3].x + o[3].y) * r);  // * (-1 - i)/sqrt2
+    } else {
+        t1 = mk<T>((o[1].x - o[1].y) * r, (o[1].x + o[1].y) * r);
+        t2 = mk<T>(-o[2].y, o[2].x);
+        t3 = mk<T>(-(o[3].x + o[3].y) * r, (o[3].x - o[3].y) * r);
+    }
+    v[0] = cadd<T>(e[0], o[0]);
+    v[4] = csub<T>(e[0], o[0]);
+    v[1] = cadd<T>(e[1], t1);
+    v[5] = csub<T>(e[1], t1);
+    v[2] = cadd<T>(e[2], t2);
+    v[6] = csub<T>(e[2], t2);
+    v[3] = cadd<T>(e[3], t3);
+    v[7] = csub<T>(e[3], t3);
+}
+
+// One Stockham stage of radix R on every pencil of the tile.  The thread owns pencils
+// c + k wc (k < IPT) and butterflies j = u + q N/8 (q < 8/R) of each.
+template <typename T, int N, int R, bool INV, int IPT>
+__device__ __forceinline__ void stockham_stage(c2<T>* tile, int ld, int c, int wc, int u, int Ns, const c2<T>* tw) {
+    constexpr int Q = 8 / R;
+    c2<T> v[IPT][8];
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+        const int col = c + k * wc;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int j = u + q * (N / 8);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[k][q * R + r] = tile[(j + r * (N / R)) * ld + col];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+        const int col = c + k * wc;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int j = u + q * (N / 8);
+            const int jm = j & (Ns - 1);
+            const int step = jm * (N / (Ns * R));
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                c2<T> w = tw[step * r];
+                if (INV) w.y = -w.y;
+                v[k][q * R + r] = cmul<T>(v[k][q * R + r], w);
+            }
+            if (R == 8) dft8<T, INV>(v[k] + q * R);
+            else if (R == 4) dft4<T, INV>(v[k] + q * R);
+            else dft2<T, INV>(v[k] + q * R);
+            const int idxD = (j - jm) * R + jm;
+#pragma unroll
+            for (int r = 0; r < R; ++r) tile[(idxD + r * Ns) * ld + col] = v[k][q * R + r];
+        }
+    }
+    __syncthreads();
+}
+
+// Forward (or inverse, unnormalised) FFT of length N = 2^LOGN along every pencil.
+template <typename T, int LOGN, bool INV, int IPT>
+__device__ __forceinline__ void fft_columns(c2<T>* tile, int ld, int c, int wc, int u, const c2<T>* tw) {
+    // c = thread's first pencil, wc = W / IPT, u = butterfly slot (0 .. N/8 - 1)
+    constexpr int N = 1 << LOGN;
+    constexpr int rem = LOGN % 3;
+    int Ns = 1;
+    if (rem == 1) { stockham_stage<T, N, 2, INV, IPT>(tile, ld, c, wc, u, Ns, tw); Ns = 2; }
+    if (rem == 2) { stockham_stage<T, N, 4, INV, IPT>(tile, ld, c, wc, u, Ns, tw); Ns = 4; }
+#pragma unroll
+    for (int s = 0; s < LOGN / 3; ++s) {
+        stockham_stage<T, N, 8, INV, IPT>(tile, ld, c, wc, u, Ns, tw);
+        Ns *= 8;
+    }
+}
+
+__host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
+
+// Shape of the pencil passes for n = 2^LOGN: W pencils per CTA (W n / 8 <= 1024 butterfly
+// slots, segments of up to 32 complex), IPT pencils per thread, THREADS per CTA.
+template <int LOGN>
+struct PassShape {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int W0 = (8192 >> LOGN) > 32 ? 32 : (8192 >> LOGN);
+    static constexpr int W = W0 > N ? N : W0;
+    static constexpr int LOGW = ilog2(W);
+    static constexpr int IPT = LOGN >= 8 ? 2 : 1;
+    static constexpr int THREADS = W * N / (8 * IPT);
+    static constexpr int LD = W + 1;
+    static constexpr int PER = N * W / THREADS;   // tile elements per thread
+};
+
+// Frequency index e is kept when f(e) lies in [-nk_neg, nk_pos].
+__device__ __forceinline__ bool kept(int e, int n, int nk_pos, int nk_neg) {
+    return e <= nk_pos || e >= n - nk_neg;
+}
+
+}  // namespace lpp

@@ -63,6 +63,10 @@ FftGeom fft_geometry(int n, int nk_pos, int nk_neg);
 template <typename T>
 cudaError_t fft3d(c2<T>* data, int n_grids, int n, const c2<T>* tw, const FftGeom& g, bool inverse,
                   cudaStream_t st, Timer* timer);
+// y and z passes only (the x pass fused into the assignment kernel)
+template <typename T>
+cudaError_t fft_yz(c2<T>* data, int n_grids, int n, const c2<T>* tw, const FftGeom& g, bool inverse,
+                   cudaStream_t st, Timer* timer);
 
 // ---------------------------------------------------------- per-particle weights
 constexpr int kMaxGroups = 16;
@@ -82,6 +86,7 @@ struct CoeffGroup {
 
 template <typename T>
 struct CoeffArgs {
+    const int* perm;    // optional: particle i of the output order is input perm[i]
     const T* pos;       // [3][count]
     const T* w;         // [count] or null
     const T* shape;     // [6 or 2][count]
@@ -146,6 +151,47 @@ struct AssignArgs {
 
 template <typename T>
 cudaError_t launch_assign(const AssignArgs<T>& a, int scheme, int interlace, cudaStream_t st);
+
+// ---------------------------------------------------- pencil sort + fused assign/x-FFT
+// Catalogue sorted by x-pencil key: cell coordinates su[3][cap], weights sw[cap],
+// offsets off[n*n + 1] of every key.
+struct PencilCat {
+    const void* su;
+    const void* sw;
+    const int* off;
+    long long cap;
+};
+struct FusedSrc {
+    int cat;            // index into FusedArgs::cat
+    const void* vals;   // per-particle values in sorted order, or null for the sorted weights
+    int neg_alpha;      // multiply by -alpha (randoms into the density field)
+};
+struct FusedSlot {
+    int n_src;
+    FusedSrc src[2];
+    const void* vals_b;  // non-interlaced: second field (same catalogue as src[0]) in the imaginary part
+    int grid;
+};
+template <typename T>
+struct FusedArgs {
+    PencilCat cat[3];
+    int n_slots;
+    FusedSlot slots[kMaxSlots];
+    c2<T>* grids;
+    long long grid_stride;
+    int n, ty, tz, scheme, interlace;
+    int nk_pos, nk_neg;
+    const c2<T>* tw;
+    const double* sums;
+};
+
+void fused_geometry(int n, size_t elem_bytes, int* ty, int* tz, int* ipt, int* threads, size_t* smem);
+template <typename T>
+cudaError_t launch_pencil_sort(const T* pos, const T* w, long long count, long long cap, int n, double box,
+                               const double origin[3], int* key, int* counts, int* off, int* cursor, T* su, T* sw,
+                               int* perm, int* err, cudaStream_t st);
+template <typename T>
+cudaError_t launch_assign_xfft(const FusedArgs<T>& a, cudaStream_t st);
 
 // --------------------------------------------------------------------- combine
 struct CombineChan {

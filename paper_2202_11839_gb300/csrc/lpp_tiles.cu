@@ -1,0 +1,324 @@
+// Pencil sort of the catalogues and the fused assignment + x-FFT kernel.
+//
+// Sort.  Every particle gets the key iz * n + iy of the x pencil of the cell holding it
+// (iy = floor(u_y) mod n, u = (x - origin) n / L); a counting sort (histogram, scan,
+// scatter) stores the cell coordinates u and the weight of each particle in key order.
+//
+// Fused kernel.  One CTA owns a tile of TY x TZ x-pencils (all n points along x) of one
+// batch grid.  CIC and TSC stencils, on the grid and on the half-cell shifted grid,
+// reach the rows floor(u) - 1 .. floor(u) + 2, so the particles that touch the tile are
+// exactly those with keys in rows [y0 - 2, y0 + TY] x [z0 - 2, z0 + TZ]: TZ + 3
+// contiguous key ranges of the sorted arrays.  The CTA scatters them into the tile with
+// shared-memory atomics (sub-grid 0 into the real part and the shifted sub-grid into the
+// imaginary part, or two fields), runs the x-FFT of its pencils in place and writes only
+// the kept x frequencies.  The grid is never zeroed, never touched by global atomics and
+// never read back for an x pass.
+#include <string.h>
+
+#include "lpp_internal.h"
+#include "lpp_kernels.h"
+#include "lpp_fft_dev.cuh"
+
+namespace lpp {
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pencil_count(const T* __restrict__ pos, long long count, int n, T ih,
+                                                      T ox, T oy, T oz, int* __restrict__ key,
+                                                      int* __restrict__ counts, int* err) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const T u0 = (pos[i] - ox) * ih;
+        const T u1 = (pos[count + i] - oy) * ih;
+        const T u2 = (pos[2 * count + i] - oz) * ih;
+        int k = 0;
+        if (!(u0 >= (T)0 && u0 <= (T)n && u1 >= (T)0 && u1 <= (T)n && u2 >= (T)0 && u2 <= (T)n)) {
+            // flagged (the estimate is rejected) but still sorted, under key 0, so that
+            // the sorted arrays and the permutation cover every particle
+            atomicOr(err, ERRF_DOMAIN);
+        } else {
+            const int iy = ((int)floor(u1)) & (n - 1);
+            const int iz = ((int)floor(u2)) & (n - 1);
+            k = iz * n + iy;
+        }
+        key[i] = k;
+        atomicAdd(counts + k, 1);
+    }
+}
+
+// Exclusive scan of counts[0..nk) into off[0..nk] and cursor[0..nk) (one CTA of 1024 threads).
+__global__ void __launch_bounds__(1024) k_scan_offsets(const int* __restrict__ counts, int nk, int* __restrict__ off,
+                                                       int* __restrict__ cursor) {
+    __shared__ long long part[1024];
+    const int t = threadIdx.x;
+    const int chunk = (nk + 1023) / 1024;
+    const int b = t * chunk, e = min(nk, b + chunk);
+    long long s = 0;
+    for (int i = b; i < e; ++i) s += counts[i];
+    part[t] = s;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {
+        const long long v = t >= d ? part[t - d] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    long long run = part[t] - s;  // exclusive prefix of this chunk
+    for (int i = b; i < e; ++i) {
+        off[i] = (int)run;
+        cursor[i] = (int)run;
+        run += counts[i];
+    }
+    if (t == 1023) off[nk] = (int)part[1023];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pencil_scatter(const T* __restrict__ pos, const T* __restrict__ w,
+                                                        long long count, long long cap, T ih, T ox, T oy, T oz,
+                                                        const int* __restrict__ key, int* __restrict__ cursor,
+                                                        T* __restrict__ su, T* __restrict__ sw,
+                                                        int* __restrict__ perm) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k = key[i];
+        const int j = atomicAdd(cursor + k, 1);
+        su[j] = (pos[i] - ox) * ih;
+        su[cap + j] = (pos[count + i] - oy) * ih;
+        su[2 * cap + j] = (pos[2 * count + i] - oz) * ih;
+        sw[j] = w ? w[i] : (T)1;
+        if (perm) perm[j] = (int)i;
+    }
+}
+
+template <typename T>
+cudaError_t launch_pencil_sort(const T* pos, const T* w, long long count, long long cap, int n, double box,
+                               const double origin[3], int* key, int* counts, int* off, int* cursor, T* su, T* sw,
+                               int* perm, int* err, cudaStream_t st) {
+    const int nk = n * n;
+    cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)nk * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    const T ih = (T)((double)n / box);
+    const T ox = (T)origin[0], oy = (T)origin[1], oz = (T)origin[2];
+    long long blocks = (count + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    if (count > 0) k_pencil_count<T><<<(int)blocks, 256, 0, st>>>(pos, count, n, ih, ox, oy, oz, key, counts, err);
+    k_scan_offsets<<<1, 1024, 0, st>>>(counts, nk, off, cursor);
+    if (count > 0)
+        k_pencil_scatter<T><<<(int)blocks, 256, 0, st>>>(pos, w, count, cap, ih, ox, oy, oz, key, cursor, su, sw,
+                                                         perm);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ fused kernel
+template <typename T>
+__device__ __forceinline__ void stencil1(T u, int n, int P, int cells[3], T w[3]) {
+    if (P == 2) {
+        const T fl = floor(u);
+        const T f = u - fl;
+        const int i0 = (int)fl;
+        w[0] = (T)1 - f;
+        w[1] = f;
+        w[2] = (T)0;
+        cells[0] = i0;
+        cells[1] = i0 + 1;
+        cells[2] = i0 + 1;
+    } else {
+        const T ic = floor(u + (T)0.5);
+        const T d = u - ic;
+        const int c = (int)ic;
+        const T hm = (T)0.5 - d, hp = (T)0.5 + d;
+        w[0] = (T)0.5 * hm * hm;
+        w[1] = (T)0.75 - d * d;
+        w[2] = (T)0.5 * hp * hp;
+        cells[0] = c - 1;
+        cells[1] = c;
+        cells[2] = c + 1;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) cells[k] &= (n - 1);   // periodic wrap (n is a power of two)
+}
+
+// Scatter one particle's weights (stencil at offset `shift` cells) into the tile part `im`.
+// The loops run to the fixed bound 3 with a guard on P so the stencil stays in registers.
+template <typename T>
+__device__ __forceinline__ void scatter_one(T* tilef, int ld, int n, int P, T ux, T uy, T uz, T shift, int y0,
+                                            int z0, int ty, int tz, T va, T vb, bool two_fields, int im) {
+    int cx[3], cy[3], cz[3];
+    T wx[3], wy[3], wz[3];
+    stencil1<T>(ux - shift, n, P, cx, wx);
+    stencil1<T>(uy - shift, n, P, cy, wy);
+    stencil1<T>(uz - shift, n, P, cz, wz);
+#pragma unroll
+    for (int kz = 0; kz < 3; ++kz) {
+        const int lz = (cz[kz] - z0) & (n - 1);
+        if (kz >= P || lz >= tz) continue;
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky) {
+            const int ly = (cy[ky] - y0) & (n - 1);
+            if (ky >= P || ly >= ty) continue;
+            const int line = lz * ty + ly;
+            const T wyz = wz[kz] * wy[ky];
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx) {
+                if (kx >= P) continue;
+                const int idx = 2 * (cx[kx] * ld + line);
+                const T ww = wyz * wx[kx];
+                atomicAdd(tilef + idx + im, va * ww);
+                if (two_fields) atomicAdd(tilef + idx + 1, vb * ww);
+            }
+        }
+    }
+}
+
+// Tile of TY x TZ pencils: TY = 4 (TY = 2 when the FP64 1024-point tile would not fit).
+template <typename T, int LOGN>
+struct FusedShape {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int TY = (sizeof(T) == 8 && LOGN >= 10) ? 2 : 4;
+    static constexpr int TZ = 4;
+    static constexpr int W = TY * TZ;
+    static constexpr int LD = W + 1;
+    static constexpr int IPT = (W * N / 8) <= 512 ? 1 : ((W * N / 8) <= 1024 ? 2 : 4);
+    static constexpr int THREADS = W * N / (8 * IPT);
+    static constexpr int MAXR = 2 * 2 * (TZ + 3);   // key ranges: sources x z rows x (1 or 2)
+};
+
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(FusedShape<T, LOGN>::THREADS)
+k_assign_xfft(FusedArgs<T> a) {
+    using S = FusedShape<T, LOGN>;
+    constexpr int N = S::N, TY = S::TY, TZ = S::TZ, W = S::W, LD = S::LD;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int r_begin[S::MAXR], r_pref[S::MAXR + 1], r_src[S::MAXR];
+    __shared__ int n_ranges;
+    c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
+    c2<T>* tile = tw + N;
+    T* tilef = reinterpret_cast<T*>(tile);
+    const int tid = threadIdx.x;
+    const int y0 = (blockIdx.x & (N / TY - 1)) * TY;
+    const int z0 = (blockIdx.x >> (LOGN - ilog2(TY))) * TZ;
+    const FusedSlot& sl = a.slots[blockIdx.y];
+    c2<T>* out = a.grids + (size_t)sl.grid * a.grid_stride + ((size_t)z0 * N + y0) * N;
+
+    // the particles touching the tile: TZ+3 z rows of keys y0-2 .. y0+TY per source,
+    // one or two contiguous ranges each (the y window may wrap)
+    if (tid == 0) {
+        int nr = 0, acc = 0;
+        for (int s = 0; s < sl.n_src; ++s) {
+            const int* off = a.cat[sl.src[s].cat].off;
+            for (int dz = 0; dz < TZ + 3; ++dz) {
+                const int zr = (z0 - 2 + dz) & (N - 1);
+                const int ylo = y0 - 2, yhi = y0 + TY;   // inclusive
+                int bb[2], ee[2], m = 0;
+                bb[m] = off[zr * N + (ylo < 0 ? 0 : ylo)];
+                ee[m++] = off[zr * N + (yhi >= N ? N - 1 : yhi) + 1];
+                if (ylo < 0) { bb[m] = off[zr * N + N + ylo]; ee[m++] = off[zr * N + N]; }
+                if (yhi >= N) { bb[m] = off[zr * N]; ee[m++] = off[zr * N + (yhi - N) + 1]; }
+                for (int q = 0; q < m; ++q) {
+                    if (ee[q] <= bb[q]) continue;
+                    r_begin[nr] = bb[q];
+                    r_src[nr] = s;
+                    r_pref[nr] = acc;
+                    acc += ee[q] - bb[q];
+                    ++nr;
+                }
+            }
+        }
+        r_pref[nr] = acc;
+        n_ranges = nr;
+    }
+    __syncthreads();
+    const int nr = n_ranges;
+    const int total = r_pref[nr];
+    if (total == 0) {
+        // no particle reaches these pencils: their transform is zero
+#pragma unroll 4
+        for (int idx = tid; idx < N * W; idx += S::THREADS) {
+            const int e = idx & (N - 1), c = idx >> LOGN;
+            if (kept(e, N, a.nk_pos, a.nk_neg))
+                out[((c / TY) * N + (c & (TY - 1))) * N + e] = mk<T>((T)0, (T)0);
+        }
+        return;
+    }
+    for (int i = tid; i < N; i += S::THREADS) tw[i] = a.tw[i];
+    for (int i = tid; i < N * LD; i += S::THREADS) tile[i] = mk<T>((T)0, (T)0);
+    __syncthreads();
+    const T alpha = (T)a.sums[SUM_ALPHA];
+    const int P = a.scheme;
+    const T* vb_ptr = (!a.interlace && sl.vals_b) ? static_cast<const T*>(sl.vals_b) : nullptr;
+    int r = 0;
+    for (int t = tid; t < total; t += S::THREADS) {
+        while (r + 1 < nr && r_pref[r + 1] <= t) ++r;   // t increases, so the range index only grows
+        const int j = r_begin[r] + (t - r_pref[r]);
+        const FusedSrc& src = sl.src[r_src[r]];
+        const PencilCat& cat = a.cat[src.cat];
+        const T* su = static_cast<const T*>(cat.su);
+        const T* vals = src.vals ? static_cast<const T*>(src.vals) : static_cast<const T*>(cat.sw);
+        const long long cap = cat.cap;
+        const T ux = su[j], uy = su[cap + j], uz = su[2 * cap + j];
+        T va = vals[j];
+        if (src.neg_alpha) va *= -alpha;
+        const bool two = vb_ptr != nullptr && r_src[r] == 0;
+        const T vb = two ? vb_ptr[j] : (T)0;
+        scatter_one<T>(tilef, LD, N, P, ux, uy, uz, (T)0, y0, z0, TY, TZ, va, vb, two, 0);
+        if (a.interlace) scatter_one<T>(tilef, LD, N, P, ux, uy, uz, (T)0.5, y0, z0, TY, TZ, va, (T)0, false, 1);
+    }
+    __syncthreads();
+    constexpr int WC = W / S::IPT;
+    fft_columns<T, LOGN, false, S::IPT>(tile, LD, tid & (WC - 1), WC, tid >> ilog2(WC), tw);
+#pragma unroll 4
+    for (int idx = tid; idx < N * W; idx += S::THREADS) {
+        const int e = idx & (N - 1), c = idx >> LOGN;
+        if (kept(e, N, a.nk_pos, a.nk_neg)) out[((c / TY) * N + (c & (TY - 1))) * N + e] = tile[e * LD + c];
+    }
+}
+
+// Tile shape (TY, TZ), pencils per thread, threads and shared memory of the fused kernel
+// (mirrors FusedShape).
+void fused_geometry(int n, size_t elem_bytes, int* ty, int* tz, int* ipt, int* threads, size_t* smem) {
+    *ty = (elem_bytes == 8 && n >= 1024) ? 2 : 4;
+    *tz = 4;
+    const int w = *ty * *tz;
+    const int t1 = w * n / 8;
+    *ipt = t1 <= 512 ? 1 : (t1 <= 1024 ? 2 : 4);
+    *threads = t1 / *ipt;
+    *smem = (size_t)(n + n * (w + 1)) * 2 * elem_bytes;
+}
+
+template <typename T, int LOGN>
+static cudaError_t launch_fused_n(const FusedArgs<T>& a, int n_tiles, cudaStream_t st) {
+    using S = FusedShape<T, LOGN>;
+    if (a.ty != S::TY || a.tz != S::TZ) return cudaErrorInvalidConfiguration;
+    const size_t smem = (size_t)(S::N + S::N * S::LD) * sizeof(c2<T>);
+    cudaFuncSetAttribute(k_assign_xfft<T, LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_assign_xfft<T, LOGN><<<dim3(n_tiles, a.n_slots), S::THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_assign_xfft(const FusedArgs<T>& a, cudaStream_t st) {
+    if (a.n_slots == 0) return cudaSuccess;
+    const int n_tiles = (a.n / a.ty) * (a.n / a.tz);
+    switch (a.n) {
+        case 8: return launch_fused_n<T, 3>(a, n_tiles, st);
+        case 16: return launch_fused_n<T, 4>(a, n_tiles, st);
+        case 32: return launch_fused_n<T, 5>(a, n_tiles, st);
+        case 64: return launch_fused_n<T, 6>(a, n_tiles, st);
+        case 128: return launch_fused_n<T, 7>(a, n_tiles, st);
+        case 256: return launch_fused_n<T, 8>(a, n_tiles, st);
+        case 512: return launch_fused_n<T, 9>(a, n_tiles, st);
+        case 1024: return launch_fused_n<T, 10>(a, n_tiles, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template cudaError_t launch_pencil_sort<float>(const float*, const float*, long long, long long, int, double,
+                                               const double*, int*, int*, int*, int*, float*, float*, int*, int*,
+                                               cudaStream_t);
+template cudaError_t launch_pencil_sort<double>(const double*, const double*, long long, long long, int, double,
+                                                const double*, int*, int*, int*, int*, double*, double*, int*, int*,
+                                                cudaStream_t);
+template cudaError_t launch_assign_xfft<float>(const FusedArgs<float>&, cudaStream_t);
+template cudaError_t launch_assign_xfft<double>(const FusedArgs<double>&, cudaStream_t);
+
+}  // namespace lpp
