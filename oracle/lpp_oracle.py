@@ -508,3 +508,104 @@ def direct_ft(kvec: np.ndarray, pos: np.ndarray, values: np.ndarray) -> np.ndarr
     """sum_g values[k, g] e^{-i k.x_g} for wave vectors kvec (nk, 3)."""
     phase = np.exp(-1j * (kvec @ pos))
     return np.sum(values * phase, axis=1)
+
+
+# ------------------------------------------------------------------ window multipoles
+@dataclass
+class WindowResult:
+    q: np.ndarray          # (5, nb) for l = 0, 2, 4, 6, 8
+    n_points: np.ndarray   # separation grid points per shell
+    s_mean: np.ndarray
+    norm: float
+
+
+def _separations(n: int, box: float):
+    """Minimal-image separation of every grid offset (same index order as the DFT grid)."""
+    h = box / n
+    f = np.fft.fftfreq(n, d=1.0 / n)
+    sx, sy, sz = np.meshgrid(f, f, f, indexing="ij")
+    return sx, sy, sz, h
+
+
+def window_multipoles(n: int, box: float, origin, observer, rand_pos, rand_w, rand_nbar, alpha: float,
+                      s_edges, scheme: int = 2, compensate: bool = True, ells=(0, 2, 4, 6, 8)) -> WindowResult:
+    """Q_l(s) = (2l+1) < int_x W(x) W(x+s) L_l(s.x) >_shell / I (Eq. windowQ_ell, endpoint d = x).
+
+    W(x) = alpha sum_r w_r delta_D(x - x_r) from the randoms; I = alpha sum_r nbar w^2 (the
+    estimator's normalisation, so that Q_0 -> 1 at small s for a window much larger than s).
+    L_l(s.x) is expanded into Cartesian monomials of s and x; every monomial field is
+    cross-correlated with W by FFT (sum_x A(x) B(x+s) = IFFT[conj FT A . FT B](s)); the shell
+    average runs over the grid separations s (minimal image) with h sqrt(q) in [edge_b,
+    edge_b+1), s = 0 excluded.
+    """
+    rp = np.asarray(rand_pos, dtype=np.float64)
+    nr = rp.shape[1]
+    w = np.ones(nr) if rand_w is None else np.asarray(rand_w, dtype=np.float64)
+    nb_ = np.ones(nr) if rand_nbar is None else np.asarray(rand_nbar, dtype=np.float64)
+    norm = alpha * np.sum(nb_ * w * w)
+    mg = ModeGrid(n, box)
+    ft = FieldTransformer(rp, n, box, origin, scheme, False, compensate, mg)
+    bft = ft.ft(w.astype(np.complex128))
+    xh = line_of_sight(rp, observer)
+    sx, sy, sz, h = _separations(n, box)
+    q2 = sx * sx + sy * sy + sz * sz
+    smag = h * np.sqrt(q2)
+    edges = np.asarray(s_edges, dtype=np.float64)
+    b = np.searchsorted(edges, smag, side="right") - 1
+    nbins = len(edges) - 1
+    valid = (b >= 0) & (b < nbins) & (q2 > 0)
+    b = np.where(valid, b, nbins)
+    npts = np.bincount(b.ravel(), minlength=nbins + 1)[:nbins]
+    smean = np.bincount(b.ravel(), weights=smag.ravel(), minlength=nbins + 1)[:nbins] / np.maximum(npts, 1)
+    rn = np.sqrt(np.maximum(q2, 1e-300))
+    shat = (sx / rn, sy / rn, sz / rn)
+    out = np.zeros((len(ells), nbins))
+    for li, ell in enumerate(ells):
+        c = legendre_coeffs(ell)
+        acc = np.zeros((n, n, n))
+        for p, cp in enumerate(c):
+            if cp == 0.0:
+                continue
+            for e, mn in monomials(p):
+                aft = ft.ft((w * _pow3(xh.T, e)).astype(np.complex128))
+                corr = np.real(np.fft.ifftn(np.conj(aft) * bft))
+                acc += (cp * mn) * _pow3(shat, e) * corr
+        vals = (2 * ell + 1) * alpha * alpha * acc / (h ** 3 * norm)
+        out[li] = np.bincount(b.ravel(), weights=vals.ravel(), minlength=nbins + 1)[:nbins] / np.maximum(npts, 1)
+    out = np.where(npts[None, :] > 0, out, 0.0)
+    return WindowResult(out, npts.astype(np.int64), np.where(npts > 0, smean, 0.0), norm)
+
+
+def window_pair_count(n: int, box: float, observer, rand_pos, rand_w, rand_nbar, alpha: float, s_edges,
+                      ells=(0, 2, 4, 6, 8)) -> np.ndarray:
+    """Brute-force endpoint pair sums for particles on grid nodes (pin of window_multipoles):
+    Q_l(b) = (2l+1) alpha^2 / (N_b h^3 I) sum_{r,r'} w w' L_l(s_rr'.x_r) [s_rr' in b], with the
+    minimal-image separation s_rr' = x_r' - x_r and N_b the grid separations in shell b."""
+    from scipy.special import eval_legendre
+    rp = np.asarray(rand_pos, dtype=np.float64)
+    nr = rp.shape[1]
+    w = np.ones(nr) if rand_w is None else np.asarray(rand_w, dtype=np.float64)
+    nb_ = np.ones(nr) if rand_nbar is None else np.asarray(rand_nbar, dtype=np.float64)
+    norm = alpha * np.sum(nb_ * w * w)
+    d = rp.T[None, :, :] - rp.T[:, None, :]          # [r, r', 3] = x_r' - x_r
+    d = d - box * np.round(d / box)
+    s = np.linalg.norm(d, axis=2)
+    xh = line_of_sight(rp, observer)
+    sx, sy, sz, h = _separations(n, box)
+    q2 = sx * sx + sy * sy + sz * sz
+    edges = np.asarray(s_edges, dtype=np.float64)
+    bg = np.searchsorted(edges, h * np.sqrt(q2), side="right") - 1
+    nbins = len(edges) - 1
+    npts = np.array([np.sum((bg == i) & (q2 > 0)) for i in range(nbins)])
+    # separations of node pairs are exact multiples of h: bin them through the same expression
+    qpair = np.round(np.sum((d / h) ** 2, axis=2))
+    bp = np.searchsorted(edges, h * np.sqrt(qpair), side="right") - 1
+    ok = (qpair > 0) & (bp >= 0) & (bp < nbins)
+    mu = np.einsum("rsa,ra->rs", d, xh) / np.where(s > 0, s, 1.0)
+    ww = w[:, None] * w[None, :]
+    out = np.zeros((len(ells), nbins))
+    for li, ell in enumerate(ells):
+        val = (2 * ell + 1) * ww * eval_legendre(ell, mu)
+        out[li] = np.bincount(bp[ok], weights=val[ok], minlength=nbins)[:nbins]
+    out = out * alpha * alpha / (np.maximum(npts, 1)[None, :] * h ** 3 * norm)
+    return np.where(npts[None, :] > 0, out, 0.0)

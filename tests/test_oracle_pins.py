@@ -348,3 +348,46 @@ def test_shot_noise_and_normalisation_periodic():
     assert r.shot_plus == pytest.approx(np.sum(g12 ** 2) / r.norm_auto)
     rel = r.p[O.M_INDEX[("plus", 0)]].real / r.shot_plus
     assert np.all(np.abs(rel) < 0.25)
+
+
+# ------------------------------------------------------------------ window multipoles
+def test_window_fft_equals_pair_count_on_nodes():
+    """Randoms on grid nodes, CIC without deconvolution: the FFT window multipoles equal
+    the brute-force endpoint pair sums exactly (Eq. windowQ_ell with d = x)."""
+    n, box = 16, 160.0
+    rng = np.random.default_rng(31)
+    cnt = 150
+    cells = rng.choice(n ** 3, cnt, replace=False)
+    ix, iy, iz = np.unravel_index(cells, (n, n, n))
+    h = box / n
+    pos = np.stack([ix * h, iy * h, iz * h]).astype(np.float64)
+    w = rng.uniform(0.5, 1.5, cnt)
+    nbar = rng.uniform(0.5, 2.0, cnt)
+    obs = (box / 2, box / 2, -400.0)
+    edges = np.linspace(0.0, 6.5 * h, 7)
+    fft = O.window_multipoles(n, box, (0, 0, 0), obs, pos, w, nbar, 0.7, edges, scheme=2, compensate=False)
+    brute = O.window_pair_count(n, box, obs, pos, w, nbar, 0.7, edges)
+    np.testing.assert_allclose(fft.q, brute, rtol=1e-10, atol=1e-12 * np.abs(brute).max())
+
+
+def test_window_uniform_periodic_is_isotropic():
+    """A uniform periodic window seen from far away (x ~ z for every random): Q_0 = 1 and
+    Q_l(b) = (2l+1) <L_l(s_z)> over the lattice separations of shell b (a finite-sum identity;
+    it tends to 0 for l > 0 in wide shells)."""
+    from scipy.special import eval_legendre
+    n, box = 24, 240.0
+    rng = np.random.default_rng(32)
+    cnt = 60000
+    pos = rng.uniform(0, box, (3, cnt))
+    nbar = np.full(cnt, cnt / box ** 3)
+    edges = np.linspace(10.0, 80.0, 6)
+    r = O.window_multipoles(n, box, (0, 0, 0), (box / 2, box / 2, -1e7), pos, None, nbar, 1.0, edges,
+                            scheme=3, compensate=True)
+    sx, sy, sz, h = O._separations(n, box)
+    q2 = sx * sx + sy * sy + sz * sz
+    b = np.searchsorted(edges, h * np.sqrt(q2), side="right") - 1
+    mu = sz / np.sqrt(np.maximum(q2, 1e-300))
+    for li, ell in enumerate((0, 2, 4, 6, 8)):
+        want = np.array([(2 * ell + 1) * eval_legendre(ell, mu[(b == i) & (q2 > 0)]).mean() for i in range(5)])
+        np.testing.assert_allclose(r.q[li], want, atol=0.03)
+    np.testing.assert_allclose(r.q[0], 1.0, atol=0.02)
