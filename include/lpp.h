@@ -151,6 +151,19 @@ lpp_status lpp_clear(lpp_plan_t plan, int role);
  * the box, at the observer, or on the frame pole. */
 lpp_status lpp_multipoles(lpp_plan_t plan, lpp_result* result);
 
+/* Window multipoles Q_l(s), l = 0,2,4,6,8 (Eq. windowQ_ell, endpoint line of sight d = x):
+ * Q_l(s) = (2l+1) < int_x W(x) W(x+s) L_l(s.x) >_shell / I, with W = alpha times the
+ * assigned randoms (LPP_RANDOMS, required), alpha = sum w_density / sum w_randoms when a
+ * density or shape catalogue is assigned (else 1), and I = alpha sum_r nbar w^2, the
+ * estimator's normalisation.  Computed by FFT cross-correlations of W Y_{l,n}(x) with W on
+ * the plan's grid (CIC/TSC, deconvolved when the plan compensates, never interlaced); the
+ * box must exceed the survey extent plus the largest separation, or pairs wrap around.
+ * Separation shells are [s_edges[b], s_edges[b+1]) over the grid separations (s = 0
+ * excluded).  Outputs: q [5][n_s]; s_mean [n_s] and n_points [n_s] (optional); *norm = I
+ * (optional).  Synchronises the plan's stream. */
+lpp_status lpp_window_Q(lpp_plan_t plan, int n_s, const double* s_edges, double* q, double* s_mean,
+                        long long* n_points, double* norm);
+
 /* Legendre multipoles of P_gE (l = 0,2), P_EE and P_BB (l = 0,2,4) from normalised
  * native moments p[LPP_N_MOMENTS][n_bins][2] (real parts), by the completeness of
  * {Lm_L/(1-mu^2)^(m/2)} (Sec. 2.4) and P_EE/BB = (P_+ +- P_-)/2 (Eq. relation_pm_EB).

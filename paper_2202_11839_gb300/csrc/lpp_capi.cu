@@ -14,6 +14,7 @@ using namespace lpp;
 namespace {
 
 const double kPi = 3.14159265358979323846;
+constexpr int kWindowChannels = 45;   // real harmonics of l = 0, 2, 4, 6, 8
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -64,6 +65,7 @@ struct lpp_plan_s {
     // pencil-sorted catalogues: key, cell coordinates, weights, key offsets; shapes permutation
     size_t off_key[3] = {0, 0, 0}, off_su[3] = {0, 0, 0}, off_sw[3] = {0, 0, 0}, off_koff[3] = {0, 0, 0};
     size_t off_perm = 0, off_counts = 0, off_cursor = 0;
+    size_t off_wout = 0, off_wthr = 0;   // window multipoles: per-channel shell sums, thresholds
     int fty = 4, ftz = 4;
     int n_partner = 0;
     int out_rows = 0;
@@ -97,6 +99,26 @@ static double norm_factor(int m, int L) {
 }
 
 static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// Integer thresholds on q = |f|^2: a lattice vector f lies in shell b iff
+// thr[b] <= q < thr[b+1], the same decision as unit * sqrt(q) in [edge_b, edge_b+1) in FP64.
+static void shell_thresholds(int n, double unit, const double* edges, int nb, std::vector<int>& thr) {
+    const long long qmax = 3LL * (n / 2) * (n / 2);
+    thr.resize(nb + 1);
+    for (int b = 0; b <= nb; ++b) {
+        const double e = edges[b];
+        long long q;
+        if (e <= 0) q = 0;
+        else {
+            const double t = e / unit;
+            q = (long long)floor(t * t);
+            if (q > qmax + 1) q = qmax + 1;
+            while (q > 0 && unit * sqrt((double)(q - 1)) >= e) --q;
+            while (q <= qmax && unit * sqrt((double)q) < e) ++q;
+        }
+        thr[b] = (int)q;
+    }
+}
 
 // ------------------------------------------------------------------ plan create
 extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out) {
@@ -139,21 +161,7 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
     // thresholds on the integer |f|^2: mode in shell b iff thr[b] <= q < thr[b+1],
     // the same decision as kf*sqrt(q) in [edge_b, edge_b+1) in FP64
     const double kf = 2.0 * kPi / d.box;
-    const long long qmax = 3LL * (n / 2) * (n / 2);
-    plan->thr.resize(nb + 1);
-    for (int b = 0; b <= nb; ++b) {
-        const double e = d.k_edges[b];
-        long long q;
-        if (e <= 0) q = 0;
-        else {
-            const double t = e / kf;
-            q = (long long)floor(t * t);
-            if (q > qmax + 1) q = qmax + 1;
-            while (q > 0 && kf * sqrt((double)(q - 1)) >= e) --q;
-            while (q <= qmax && kf * sqrt((double)q) < e) ++q;
-        }
-        plan->thr[b] = (int)q;
-    }
+    shell_thresholds(n, kf, d.k_edges, nb, plan->thr);
     const int tmax = plan->thr[nb];
     int nk = 0;
     while ((long long)(nk + 1) * (nk + 1) < tmax && nk < n / 2) ++nk;
@@ -280,7 +288,9 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
     plan->off_perm = take((size_t)caps[0] * sizeof(int));
     plan->off_counts = take((size_t)n * n * sizeof(int));
     plan->off_cursor = take((size_t)n * n * sizeof(int));
-    plan->off_partner = take((size_t)plan->n_partner * n3 * cs);
+    plan->off_wout = take((size_t)kWindowChannels * 256 * 2 * sizeof(double));
+    plan->off_wthr = take(257 * sizeof(int));
+    plan->off_partner = take((size_t)std::max(1, plan->n_partner) * n3 * cs);
     plan->off_grids = take((size_t)plan->batch * n3 * cs);
     if (d.host_inputs) {
         plan->off_stage[LPP_SHAPES] = take((size_t)(3 + 1 + 6) * d.max_shapes * es);
@@ -779,6 +789,183 @@ extern "C" lpp_status lpp_multipoles(lpp_plan_t plan, lpp_result* res) {
     if (!plan->cat[LPP_SHAPES].set) return fail(plan, LPP_ERR_NOT_READY, "no shape catalogue assigned");
     plan->err.clear();
     return plan->fp64 ? run<double>(plan, res) : run<float>(plan, res);
+}
+
+// ------------------------------------------------------------------ window multipoles
+template <typename T>
+static lpp_status run_window(lpp_plan_t plan, int nb, const double* s_edges, double* q, double* s_mean,
+                             long long* n_points, double* norm_out) {
+    const int n = plan->n;
+    const size_t n3 = (size_t)n * n * n;
+    const double h = plan->box / n;
+    cudaStream_t st = plan->stream;
+    std::vector<int> thr;
+    shell_thresholds(n, h, s_edges, nb, thr);
+    const int tmax = thr[nb];
+    int ns = 0;
+    while ((long long)(ns + 1) * (ns + 1) < tmax && ns < n / 2) ++ns;
+    const int ns_pos = std::min(ns, n / 2 - 1), ns_neg = std::min(ns, n / 2);
+    const int nks = ns_pos + 1 + ns_neg;
+    // separation points per shell and their mean |s|
+    std::vector<long long> npts(nb, 0);
+    std::vector<double> ssum(nb, 0.0);
+    for (int fx = -ns_neg; fx <= ns_pos; ++fx)
+        for (int fy = -ns_neg; fy <= ns_pos; ++fy)
+            for (int fz = -ns_neg; fz <= ns_pos; ++fz) {
+                const long long qq = (long long)fx * fx + (long long)fy * fy + (long long)fz * fz;
+                if (qq == 0 || qq < thr[0] || qq >= tmax) continue;
+                int lo = 0, hi = nb;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) / 2;
+                    if (qq >= thr[mid]) lo = mid; else hi = mid;
+                }
+                ++npts[lo];
+                ssum[lo] += h * sqrt((double)qq);
+            }
+    double* sums = (double*)(plan->ws + plan->off_sums);
+    int* err = (int*)(plan->ws + plan->off_err);
+    double* wout = (double*)(plan->ws + plan->off_wout);
+    c2<T>* grids = (c2<T>*)(plan->ws + plan->off_grids);
+    c2<T>* pW = (c2<T>*)(plan->ws + plan->off_partner);
+    const c2<T>* tw = (const c2<T>*)(plan->ws + plan->off_tw);
+    const T* iw = (const T*)(plan->ws + plan->off_iw);
+    const Catalogue& ra = plan->cat[LPP_RANDOMS];
+    const Catalogue& de = plan->cat[LPP_DENSITY].set ? plan->cat[LPP_DENSITY] : plan->cat[LPP_SHAPES];
+    LPP_CUDA(cudaMemsetAsync(sums, 0, SUM_COUNT * sizeof(double), st));
+    LPP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    LPP_CUDA(cudaMemsetAsync(wout, 0, (size_t)kWindowChannels * nb * 2 * sizeof(double), st));
+    LPP_CUDA(cudaMemcpyAsync(plan->ws + plan->off_wthr, thr.data(), (nb + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (de.set) LPP_CUDA(launch_sums<T>((const T*)de.w, nullptr, de.count, sums, SUM_W_DENS, -1, -1, st));
+    LPP_CUDA(launch_sums<T>((const T*)ra.w, (const T*)ra.nbar, ra.count, sums, SUM_W_RAND, SUM_W2_RAND, SUM_NW2_RAND, st));
+    const long long cap = std::max<long long>(1, plan->d.max_randoms);
+    LPP_CUDA(launch_pencil_sort<T>((const T*)ra.pos, (const T*)ra.w, ra.count, cap, n, plan->box, plan->d.origin,
+                                   (int*)(plan->ws + plan->off_key[LPP_RANDOMS]), (int*)(plan->ws + plan->off_counts),
+                                   (int*)(plan->ws + plan->off_koff[LPP_RANDOMS]),
+                                   (int*)(plan->ws + plan->off_cursor), (T*)(plan->ws + plan->off_su[LPP_RANDOMS]),
+                                   (T*)(plan->ws + plan->off_sw[LPP_RANDOMS]), nullptr, err, st));
+    // forward transforms keep every frequency; the inverse keeps the separations of the shells
+    const FftGeom gfull = fft_geometry(n, n / 2 - 1, n / 2);
+    const FftGeom gs = fft_geometry(n, ns_pos, ns_neg);
+    FusedArgs<T> fa;
+    memset(&fa, 0, sizeof(fa));
+    fa.cat[LPP_RANDOMS].su = plan->ws + plan->off_su[LPP_RANDOMS];
+    fa.cat[LPP_RANDOMS].sw = plan->ws + plan->off_sw[LPP_RANDOMS];
+    fa.cat[LPP_RANDOMS].off = (const int*)(plan->ws + plan->off_koff[LPP_RANDOMS]);
+    fa.cat[LPP_RANDOMS].cap = cap;
+    fa.grids = grids;
+    fa.grid_stride = (long long)n3;
+    fa.n = n;
+    fa.ty = plan->fty;
+    fa.tz = plan->ftz;
+    fa.scheme = plan->d.scheme;
+    fa.interlace = 0;
+    fa.nk_pos = n / 2 - 1;
+    fa.nk_neg = n / 2;
+    fa.tw = tw;
+    fa.sums = sums;
+    for (int a = 0; a < 3; ++a) { fa.observer[a] = plan->d.observer[a]; fa.origin[a] = plan->d.origin[a]; }
+    fa.h = h;
+    // the window field W itself: transformed and deconvolved into the partner array
+    fa.n_slots = 1;
+    FusedSlot ws{};
+    ws.n_src = 1;
+    ws.src[0] = FusedSrc{LPP_RANDOMS, nullptr, 0};
+    ws.grid = 0;
+    ws.yl_a = ws.yl_b = -1;
+    fa.slots[0] = ws;
+    LPP_CUDA(launch_assign_xfft<T>(fa, st));
+    LPP_CUDA(fft_yz<T>(grids, 1, n, tw, gfull, false, st, nullptr));
+    LPP_CUDA(launch_window_partner<T>(grids, pW, iw, n, st));
+    // channels (l, m), two per grid
+    int chl[kWindowChannels], chm[kWindowChannels], nchan = 0;
+    for (int l = 0; l <= 8; l += 2)
+        for (int m = -l; m <= l; ++m) { chl[nchan] = l; chm[nchan] = m; ++nchan; }
+    const int per_batch = std::min(2 * plan->batch, kMaxBatchCh);
+    SbinArgs<T> sb;
+    memset(&sb, 0, sizeof(sb));
+    sb.grids = grids;
+    sb.grid_stride = (long long)n3;
+    sb.n = n;
+    sb.thr = (const int*)(plan->ws + plan->off_wthr);
+    sb.nb = nb;
+    sb.ns_pos = ns_pos;
+    sb.ns_neg = ns_neg;
+    sb.nks = nks;
+    sb.scale = 1.0 / (double)n3;
+    sb.out = wout;
+    for (int c0 = 0; c0 < nchan; c0 += per_batch) {
+        const int c1 = std::min(nchan, c0 + per_batch);
+        const int ngr = (c1 - c0 + 1) / 2;
+        fa.n_slots = 0;
+        sb.n_ch = 0;
+        for (int gi = 0; gi < ngr; ++gi) {
+            const int a0 = c0 + 2 * gi, a1 = a0 + 1;
+            FusedSlot fs{};
+            fs.n_src = 1;
+            fs.src[0] = FusedSrc{LPP_RANDOMS, nullptr, 0};
+            fs.grid = gi;
+            fs.use_ylm = 1;
+            fs.yl_a = chl[a0];
+            fs.yn_a = chm[a0];
+            fs.ynorm_a = ylm_norm(chl[a0], chm[a0]);
+            fs.yl_b = a1 < c1 ? chl[a1] : -1;
+            fs.yn_b = a1 < c1 ? chm[a1] : 0;
+            fs.ynorm_b = a1 < c1 ? ylm_norm(chl[a1], chm[a1]) : 0.0;
+            fa.slots[fa.n_slots++] = fs;
+            for (int sub = 0; sub < 2; ++sub) {
+                const int ci = sub ? a1 : a0;
+                if (ci >= c1) continue;
+                SbinChan& sc = sb.ch[sb.n_ch++];
+                sc.grid = gi;
+                sc.sub = sub;
+                sc.l = chl[ci];
+                sc.m = chm[ci];
+                sc.out_row = ci;
+                sc.ynorm = ylm_norm(chl[ci], chm[ci]);
+            }
+        }
+        LPP_CUDA(launch_assign_xfft<T>(fa, st));
+        LPP_CUDA(fft_yz<T>(grids, ngr, n, tw, gfull, false, st, nullptr));
+        LPP_CUDA(launch_window_mult<T>(grids, (long long)n3, ngr, pW, iw, n, st));
+        LPP_CUDA(fft3d<T>(grids, ngr, n, tw, gs, true, st, nullptr));
+        LPP_CUDA(launch_sbin<T>(sb, plan->n_sm, st));
+    }
+    std::vector<double> h_out((size_t)kWindowChannels * nb * 2);
+    double h_sums[SUM_COUNT];
+    int h_err = 0;
+    LPP_CUDA(cudaMemcpyAsync(h_out.data(), wout, h_out.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LPP_CUDA(cudaMemcpyAsync(h_sums, sums, sizeof(h_sums), cudaMemcpyDeviceToHost, st));
+    LPP_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LPP_CUDA(cudaStreamSynchronize(st));
+    if (h_err) return fail(plan, LPP_ERR_DOMAIN, "random outside the box");
+    const double alpha = (de.set && h_sums[SUM_W_RAND] != 0.0) ? h_sums[SUM_W_DENS] / h_sums[SUM_W_RAND] : 1.0;
+    const double I = alpha * h_sums[SUM_NW2_RAND];
+    const double fac = (I != 0.0) ? 4.0 * kPi * alpha * alpha / (h * h * h * I) : 0.0;
+    for (int li = 0; li < 5; ++li)
+        for (int b = 0; b < nb; ++b) {
+            double v = 0.0;
+            for (int ci = 0; ci < nchan; ++ci)
+                if (chl[ci] == 2 * li) v += h_out[((size_t)ci * nb + b) * 2];
+            q[li * nb + b] = npts[b] > 0 ? fac * v / (double)npts[b] : 0.0;
+        }
+    for (int b = 0; b < nb; ++b) {
+        if (s_mean) s_mean[b] = npts[b] > 0 ? ssum[b] / npts[b] : 0.0;
+        if (n_points) n_points[b] = npts[b];
+    }
+    if (norm_out) *norm_out = I;
+    return LPP_OK;
+}
+
+extern "C" lpp_status lpp_window_Q(lpp_plan_t plan, int n_s, const double* s_edges, double* q, double* s_mean,
+                                   long long* n_points, double* norm) {
+    if (!plan || !s_edges || !q || n_s < 1 || n_s > 256) return LPP_ERR_INVALID_ARG;
+    for (int i = 0; i < n_s; ++i)
+        if (!(s_edges[i] < s_edges[i + 1])) return LPP_ERR_INVALID_ARG;
+    if (!plan->ws || !plan->tables_ready) return fail(plan, LPP_ERR_NOT_READY, "workspace not set");
+    if (!plan->cat[LPP_RANDOMS].set) return fail(plan, LPP_ERR_NOT_READY, "no randoms assigned");
+    plan->err.clear();
+    return plan->fp64 ? run_window<double>(plan, n_s, s_edges, q, s_mean, n_points, norm)
+                      : run_window<float>(plan, n_s, s_edges, q, s_mean, n_points, norm);
 }
 
 extern "C" const char* lpp_status_string(lpp_status s) {

@@ -16,56 +16,9 @@
 // global FP64 shell sums once at the end.
 #include "lpp_internal.h"
 #include "lpp_kernels.h"
+#include "lpp_reduce.cuh"
 
 namespace lpp {
-
-template <typename T> struct Owned;
-template <> struct Owned<float> {
-    // compensated sum (Knuth two-sum) in two floats
-    static __device__ __forceinline__ void add(float* hi, float* lo, float v) {
-        const float s = *hi + v;
-        const float bp = s - *hi;
-        const float err = (*hi - (s - bp)) + (v - bp);
-        *hi = s;
-        *lo += err;
-    }
-    static __device__ __forceinline__ double value(const float* hi, const float* lo) {
-        return (double)*hi + (double)*lo;
-    }
-    static constexpr int words = 2;
-};
-template <> struct Owned<double> {
-    static __device__ __forceinline__ void add(double* hi, double*, double v) { *hi += v; }
-    static __device__ __forceinline__ double value(const double* hi, const double*) { return *hi; }
-    static constexpr int words = 1;
-};
-
-template <typename T>
-__device__ __forceinline__ int freq_of(int i, int n) { return i < n / 2 ? i : i - n; }
-
-// segmented inclusive scan of (re, im) over lanes with equal, monotone shell labels;
-// the last lane of each run adds the run total to acc[bin][2].
-template <typename T>
-__device__ __forceinline__ void warp_bin_add(T re, T im, int bin, T* acc) {
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int ob = __shfl_up_sync(full, bin, d);
-        const T ore = __shfl_up_sync(full, re, d);
-        const T oim = __shfl_up_sync(full, im, d);
-        if (lane >= d && ob == bin) {
-            re += ore;
-            im += oim;
-        }
-    }
-    const int nb = __shfl_down_sync(full, bin, 1);
-    const bool last = (lane == 31) || (nb != bin);
-    if (last && bin >= 0) {
-        atomicAdd(acc + 2 * bin, re);
-        atomicAdd(acc + 2 * bin + 1, im);
-    }
-}
 
 template <typename T>
 struct ModeCtx {

@@ -171,6 +171,12 @@ struct FusedSlot {
     FusedSrc src[2];
     const void* vals_b;  // non-interlaced: second field (same catalogue as src[0]) in the imaginary part
     int grid;
+    // optional real-harmonic weights Y_{l,n}(xhat) of the line of sight for the real-part
+    // field and (yl_b >= 0) a second field from the same values (window multipoles);
+    // use_ylm = 0 (the value-initialised default) disables both
+    int use_ylm;
+    int yl_a, yn_a, yl_b, yn_b;
+    double ynorm_a, ynorm_b;
 };
 template <typename T>
 struct FusedArgs {
@@ -183,6 +189,7 @@ struct FusedArgs {
     int nk_pos, nk_neg;
     const c2<T>* tw;
     const double* sums;
+    double observer[3], origin[3], h;   // for the harmonic weights
 };
 
 void fused_geometry(int n, size_t elem_bytes, int* ty, int* tz, int* ipt, int* threads, size_t* smem);
@@ -229,5 +236,32 @@ struct CombineArgs {
 
 template <typename T>
 cudaError_t launch_combine(const CombineArgs<T>& a, int n_sm, cudaStream_t st);
+
+// ------------------------------------------------------------------ window multipoles
+// pD[m] = Z[m] / W(m) over every mode of grid 0 (the window field alone in the real part)
+template <typename T>
+cudaError_t launch_window_partner(const c2<T>* grid, c2<T>* pD, const T* inv_w, int n, cudaStream_t st);
+// per mode pair, Z <- conj(A/W) pD + i conj(B/W) pD for the two packed fields of every grid
+template <typename T>
+cudaError_t launch_window_mult(c2<T>* grids, long long grid_stride, int n_grids, const c2<T>* pD, const T* inv_w,
+                               int n, cudaStream_t st);
+struct SbinChan {
+    int grid, sub, l, m, out_row;
+    double ynorm;
+};
+template <typename T>
+struct SbinArgs {
+    const c2<T>* grids;
+    long long grid_stride;
+    int n, n_ch;
+    SbinChan ch[kMaxBatchCh];
+    const int* thr;   // [nb+1] thresholds on the integer |s|^2 / h^2
+    int nb;
+    int ns_pos, ns_neg, nks;
+    double scale;     // 1 / n^3 of the unnormalised inverse FFT
+    double* out;      // [rows][nb][2]
+};
+template <typename T>
+cudaError_t launch_sbin(const SbinArgs<T>& a, int n_sm, cudaStream_t st);
 
 }  // namespace lpp

@@ -230,13 +230,16 @@ k_assign_xfft(FusedArgs<T> a) {
     __syncthreads();
     const int nr = n_ranges;
     const int total = r_pref[nr];
+    // kept x frequencies of a pencil: indices 0..nk_pos and n-nk_neg..n-1; LPL consecutive
+    // threads write one pencil (coalesced along x)
+    const int nkept = a.nk_pos + 1 + a.nk_neg;
+    constexpr int LPL = S::THREADS / W;
+    const int cw = tid / LPL;
     if (total == 0) {
         // no particle reaches these pencils: their transform is zero
-#pragma unroll 4
-        for (int idx = tid; idx < N * W; idx += S::THREADS) {
-            const int e = idx & (N - 1), c = idx >> LOGN;
-            if (kept(e, N, a.nk_pos, a.nk_neg))
-                out[((c / TY) * N + (c & (TY - 1))) * N + e] = mk<T>((T)0, (T)0);
+        for (int k = tid & (LPL - 1); k < nkept; k += LPL) {
+            const int e = k <= a.nk_pos ? k : N - nkept + k;
+            out[((cw / TY) * N + (cw & (TY - 1))) * N + e] = mk<T>((T)0, (T)0);
         }
         return;
     }
@@ -256,20 +259,32 @@ k_assign_xfft(FusedArgs<T> a) {
         const T* vals = src.vals ? static_cast<const T*>(src.vals) : static_cast<const T*>(cat.sw);
         const long long cap = cat.cap;
         const T ux = su[j], uy = su[cap + j], uz = su[2 * cap + j];
-        T va = vals[j];
+        const T base = vals[j];
+        T va = base;
         if (src.neg_alpha) va *= -alpha;
-        const bool two = vb_ptr != nullptr && r_src[r] == 0;
-        const T vb = two ? vb_ptr[j] : (T)0;
+        bool two = vb_ptr != nullptr && r_src[r] == 0;
+        T vb = two ? vb_ptr[j] : (T)0;
+        if (sl.use_ylm) {
+            // line of sight of the particle from its cell coordinates
+            const T px = (T)a.origin[0] + ux * (T)a.h - (T)a.observer[0];
+            const T py = (T)a.origin[1] + uy * (T)a.h - (T)a.observer[1];
+            const T pz = (T)a.origin[2] + uz * (T)a.h - (T)a.observer[2];
+            const T inv = (T)1 / sqrt(px * px + py * py + pz * pz);
+            va *= (T)sl.ynorm_a * ylm_poly<T>(sl.yl_a, sl.yn_a, px * inv, py * inv, pz * inv);
+            if (sl.yl_b >= 0) {
+                vb = base * (T)sl.ynorm_b * ylm_poly<T>(sl.yl_b, sl.yn_b, px * inv, py * inv, pz * inv);
+                two = true;
+            }
+        }
         scatter_one<T>(tilef, LD, N, P, ux, uy, uz, (T)0, y0, z0, TY, TZ, va, vb, two, 0);
         if (a.interlace) scatter_one<T>(tilef, LD, N, P, ux, uy, uz, (T)0.5, y0, z0, TY, TZ, va, (T)0, false, 1);
     }
     __syncthreads();
     constexpr int WC = W / S::IPT;
     fft_columns<T, LOGN, false, S::IPT>(tile, LD, tid & (WC - 1), WC, tid >> ilog2(WC), tw);
-#pragma unroll 4
-    for (int idx = tid; idx < N * W; idx += S::THREADS) {
-        const int e = idx & (N - 1), c = idx >> LOGN;
-        if (kept(e, N, a.nk_pos, a.nk_neg)) out[((c / TY) * N + (c & (TY - 1))) * N + e] = tile[e * LD + c];
+    for (int k = tid & (LPL - 1); k < nkept; k += LPL) {
+        const int e = k <= a.nk_pos ? k : N - nkept + k;
+        out[((cw / TY) * N + (cw & (TY - 1))) * N + e] = tile[e * LD + cw];
     }
 }
 

@@ -70,6 +70,8 @@ EXPORTS = {
     "lpp_assign": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Particles)]),
     "lpp_clear": (C.c_int, [C.c_void_p, C.c_int]),
     "lpp_multipoles": (C.c_int, [C.c_void_p, C.POINTER(Result)]),
+    "lpp_window_Q": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                               C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_double)]),
     "lpp_derive_eb": (C.c_int, [C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                 C.POINTER(C.c_double)]),
     "lpp_plan_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
@@ -242,6 +244,19 @@ class Plan:
         _check(self.lib, self.lib.lpp_multipoles(self.h, C.byref(r)), self.h)
         return Estimate(p[..., 0] + 1j * p[..., 1], raw[..., 0] + 1j * raw[..., 1], km, nm, r.norm_auto,
                         r.norm_cross, r.norm_dd, r.shot_plus, r.shot_dd, r.alpha)
+
+    def window_q(self, s_edges):
+        """Window multipoles Q_l(s), l = 0..8 even, from the assigned randoms: (q[5, nb], s_mean, n_points, I)."""
+        e = np.ascontiguousarray(s_edges, dtype=np.float64)
+        nb = len(e) - 1
+        q = np.zeros((5, nb))
+        sm = np.zeros(nb)
+        npt = np.zeros(nb, dtype=np.int64)
+        norm = C.c_double()
+        dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        _check(self.lib, self.lib.lpp_window_Q(self.h, nb, dp(e), dp(q), dp(sm),
+                                               npt.ctypes.data_as(C.POINTER(C.c_longlong)), C.byref(norm)), self.h)
+        return q, sm, npt, norm.value
 
     def close(self):
         if getattr(self, "h", None):

@@ -23,7 +23,7 @@ def _lib():
 def header_functions():
     src = open(os.path.join(ROOT, "include", "lpp.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lpp_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(lpp_[A-Za-z_]+)\s*\(", src)))
 
 
 def test_every_declared_symbol_is_exported():
