@@ -1,0 +1,98 @@
+"""Pins for the window-convolution template oracle (Sec. 3.2, Appendix D)."""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import sympy as sp
+from scipy.integrate import quad
+from scipy.special import spherical_jn
+
+from oracle import template_oracle as T
+
+F = Fraction
+
+
+def _coeffs(kind, L, Lp):
+    return [sp.Rational(c) for c in T.mixing_coefficients(kind, L, Lp)]
+
+
+# The paper prints these mixtures in Eq. all_convolutions and in the leakage terms of
+# Sec. 4.3 (coefficients of Q_0, Q_2, Q_4, Q_6, Q_8).
+PRINTED = {
+    ("cross", 2, 2): [1, F(-2, 7), F(1, 21), 0, 0],
+    ("cross", 4, 2): [0, F(3, 35), F(-6, 77), F(3, 143), 0],
+    ("minus", 4, 4): [1, F(-4, 11), F(18, 143), F(-4, 143), F(7, 2431)],
+    ("plus", 0, 0): [1, 0, 0, 0, 0],
+    ("plus", 0, 2): [0, F(1, 5), 0, 0, 0],
+    ("plus", 0, 4): [0, 0, F(1, 9), 0, 0],
+    ("plus", 2, 0): [0, 1, 0, 0, 0],
+    ("plus", 2, 2): [1, F(2, 7), F(2, 7), 0, 0],
+    ("plus", 2, 4): [0, F(2, 7), F(100, 693), F(25, 143), 0],
+    ("plus", 4, 0): [0, 0, 1, 0, 0],
+    ("plus", 4, 2): [0, F(18, 35), F(20, 77), F(45, 143), 0],
+    ("plus", 4, 4): [1, F(20, 77), F(162, 1001), F(20, 143), F(490, 2431)],
+    ("dd", 2, 0): [0, 1, 0, 0, 0],
+    ("dd", 0, 0): [1, 0, 0, 0, 0],
+}
+
+
+@pytest.mark.parametrize("key", sorted(PRINTED))
+def test_mixing_coefficients_match_paper(key):
+    got = _coeffs(*key)
+    want = [sp.Rational(f.numerator, f.denominator) for f in map(F, PRINTED[key])]
+    assert got == want, (key, got)
+
+
+@pytest.mark.parametrize("ell", [0, 2, 4])
+def test_fftlog_gaussian_pair(ell):
+    """int k^(l+2) e^{-a k^2} j_l(kr) dk = sqrt(pi) r^l e^{-r^2/4a} / (2^(l+2) a^(l+3/2))."""
+    k, r, delta = T.log_grid()
+    a = 25.0
+    pk = np.where(np.arange(T.N_FFT) < T.N_IN, k ** ell * np.exp(-a * k * k), 0.0)
+    xi = T.hankel_inverse(pk, ell)
+    want = (1j ** ell).real / (2 * math.pi ** 2) * math.sqrt(math.pi) * r ** ell * np.exp(-r * r / (4 * a)) / (
+        2 ** (ell + 2) * a ** (ell + 1.5))
+    sel = (r > 0.5) & (r < 60.0)
+    scale = np.abs(want[sel]).max()
+    assert np.max(np.abs(xi[sel] - want[sel])) < 1e-7 * scale
+
+
+def test_fftlog_matches_direct_quadrature():
+    """H^-1_l of the (tapered) BBKS spectrum against adaptive quadrature of the same integrand."""
+    from scipy.interpolate import interp1d
+    k, r, delta = T.log_grid()
+    params = (1.0, 1.5, 0.8, 0.0, 0.2, 1.0)
+    pk = T.linear_pk(params)
+    norm = pk[100] / T.bbks_shape(k[100], 0.2, 0.0)
+    tp = interp1d(np.log(k[:T.N_IN]), T.taper(), kind="cubic")
+    for ell in (0, 2):
+        xi = T.hankel_inverse(pk, ell)
+        sel = (r > 5.0) & (r < 200.0)
+        scale = np.abs(xi[sel]).max()
+        for rr in (5.0, 20.0, 80.0, 150.0):
+            m = int(np.argmin(np.abs(r - rr)))
+            f = lambda kk: (kk * kk * norm * T.bbks_shape(kk, 0.2, 0.0) * float(tp(np.log(kk)))
+                            * spherical_jn(ell, kk * r[m]) / (2 * math.pi ** 2))
+            val, _ = quad(f, T.K_MIN, T.K_MAX, limit=8000, epsabs=1e-14, epsrel=1e-11)
+            val *= (1j ** ell).real
+            assert abs(xi[m] - val) < 1e-6 * scale, (ell, rr, xi[m], val)
+
+
+def test_round_trip_and_unit_window():
+    """A window with Q_0 = exp(-(r/R)^2), Q_l>0 = 0 and R large smooths by ~1/R only, so
+    Pt^(L)_X tends to the model multipole P^(L)_X at k >> 1/R (the window convolution is the
+    identity in that limit, Eq. window_convolution_X_hankel)."""
+    k, r, delta = T.log_grid()
+    params = (1.2, 1.7, 0.8, 0.05, 0.21, 1.0)
+    s = np.geomspace(0.01, 9000.0, 400)
+    qt = np.zeros((5, s.size))
+    qt[0] = np.exp(-(s / 3000.0) ** 2)
+    edges = np.linspace(0.03, 0.2, 10)
+    tmpl = T.template(params, qt, s, edges)
+    pk = T.linear_pk(params)
+    model = T.model_multipoles(params)
+    for i, (kind, L) in enumerate(T.SLOTS):
+        want = T.bin_average(model[kind].get(L, 0.0) * pk, edges)
+        scale = np.abs(T.bin_average(model[kind][min(model[kind])] * pk, edges))
+        assert np.max(np.abs(tmpl[i] - want) / scale) < 2e-3, (kind, L, np.max(np.abs(tmpl[i] - want) / scale))
