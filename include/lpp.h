@@ -164,6 +164,33 @@ lpp_status lpp_multipoles(lpp_plan_t plan, lpp_result* result);
 lpp_status lpp_window_Q(lpp_plan_t plan, int n_s, const double* s_edges, double* q, double* s_mean,
                         long long* n_points, double* norm);
 
+/* ------------------------------------------------------------------ templates
+ * Window-convolved theory templates (Sec. 3.2, Eqs. window_convolution_X_hankel and
+ * def_of_Q_llp; Appendix D): for every parameter set (A, b_g, sigma_8, tilt, Gamma,
+ * shot-noise scale) the ten native moment slots (the estimator's order)
+ *   Pt^(L)_X(k) = H_L[ sum_L' Q^X_LL'(r) xi^(L')_X(r) ](k),  xi^(L')_X = H^-1_L'[P^(L')_X],
+ * of the tidal-alignment model (shapes e = -A T_ij, galaxies b_g delta; Eq.
+ * power_for_validation scaled): P_dd^(0) = b^2 P, P_gd^(2) = -A b P / 6,
+ * P_+^(0,2,4) = A^2 (2/15, -4/21, 2/35) P, P_-^(4) = A^2 P / 420, with a BBKS P(k) of
+ * shape Gamma and slope 1 + tilt normalised to sigma_8; the plus monopole also gets the
+ * shot-noise scale times shot_plus.  FFTLog Hankel transforms (Hamilton 2000) in FP64 on
+ * 2048 log-spaced k in [1e-4, 10] padded to 4096, the input tapered over the outer 10% of
+ * ln k; outputs are k^3-weighted averages over the grid k in each shell [e_b, e_b+1). */
+typedef struct lpp_template_s* lpp_template_t;
+
+/* Host tables from a window table q[5][n_s] (Q_l at increasing separations s[n_s], l = 0..8
+ * even, e.g. from lpp_window_Q; held below s[0], zero beyond s[n_s-1]) and shells. */
+lpp_status lpp_template_create(const double* q, const double* s, int n_s, const double* k_edges, int n_bins,
+                               double shot_plus, lpp_template_t* tmpl);
+void lpp_template_destroy(lpp_template_t tmpl);
+lpp_status lpp_template_workspace_size(lpp_template_t tmpl, size_t* bytes);
+/* Device buffer (256-byte aligned, caller-owned); uploads the tables on `stream` and synchronises it. */
+lpp_status lpp_template_set_workspace(lpp_template_t tmpl, void* device_ptr, size_t bytes, void* stream);
+/* params: device [n_templates][6]; out: device [n_templates][LPP_N_MOMENTS][n_bins].
+ * Asynchronous on `stream`. */
+lpp_status lpp_convolve_template(lpp_template_t tmpl, const double* params, int n_templates, double* out,
+                                 void* stream);
+
 /* Legendre multipoles of P_gE (l = 0,2), P_EE and P_BB (l = 0,2,4) from normalised
  * native moments p[LPP_N_MOMENTS][n_bins][2] (real parts), by the completeness of
  * {Lm_L/(1-mu^2)^(m/2)} (Sec. 2.4) and P_EE/BB = (P_+ +- P_-)/2 (Eq. relation_pm_EB).

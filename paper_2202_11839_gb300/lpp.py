@@ -72,6 +72,12 @@ EXPORTS = {
     "lpp_multipoles": (C.c_int, [C.c_void_p, C.POINTER(Result)]),
     "lpp_window_Q": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_double)]),
+    "lpp_template_create": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double),
+                                      C.c_int, C.c_double, C.POINTER(C.c_void_p)]),
+    "lpp_template_destroy": (None, [C.c_void_p]),
+    "lpp_template_workspace_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "lpp_template_set_workspace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "lpp_convolve_template": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "lpp_derive_eb": (C.c_int, [C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                 C.POINTER(C.c_double)]),
     "lpp_plan_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
@@ -261,6 +267,53 @@ class Plan:
     def close(self):
         if getattr(self, "h", None):
             self.lib.lpp_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Template:
+    """Window-convolved template evaluator (lpp_template_*): tables built once, many parameter sets."""
+
+    def __init__(self, q_table, s, k_edges, shot_plus: float = 0.0, stream=None, device=None):
+        import torch
+        self.lib = load_library()
+        q = np.ascontiguousarray(q_table, dtype=np.float64)
+        sv = np.ascontiguousarray(s, dtype=np.float64)
+        e = np.ascontiguousarray(k_edges, dtype=np.float64)
+        self.nb = len(e) - 1
+        dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        h = C.c_void_p()
+        _check(self.lib, self.lib.lpp_template_create(dp(q), dp(sv), sv.size, dp(e), self.nb, shot_plus, C.byref(h)))
+        self.h = h
+        sz = C.c_size_t()
+        _check(self.lib, self.lib.lpp_template_workspace_size(h, C.byref(sz)))
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.workspace = torch.empty(sz.value + 256, dtype=torch.uint8, device=self.device)
+        addr = self.workspace.data_ptr()
+        off = (-addr) % 256
+        _check(self.lib, self.lib.lpp_template_set_workspace(h, C.c_void_p(addr + off), C.c_size_t(sz.value),
+                                                             C.c_void_p(self.stream.cuda_stream)))
+
+    def __call__(self, params, out=None):
+        """params: torch float64 CUDA tensor [n, 6]; returns a [n, 10, nb] float64 CUDA tensor."""
+        import torch
+        n = int(params.shape[0])
+        if out is None:
+            out = torch.empty((n, LPP_N_MOMENTS, self.nb), dtype=torch.float64, device=params.device)
+        _check(self.lib, self.lib.lpp_convolve_template(self.h, C.c_void_p(params.data_ptr()), n,
+                                                        C.c_void_p(out.data_ptr()),
+                                                        C.c_void_p(self.stream.cuda_stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lpp_template_destroy(self.h)
             self.h = None
 
     def __del__(self):

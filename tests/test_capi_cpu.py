@@ -104,3 +104,22 @@ def test_derive_eb_matches_oracle():
     np.testing.assert_allclose(ge, oge, rtol=1e-13, atol=1e-13)
     np.testing.assert_allclose(ee, oee, rtol=1e-13, atol=1e-13)
     np.testing.assert_allclose(bb, obb, rtol=1e-13, atol=1e-13)
+
+
+def test_template_tables_build_on_host():
+    """lpp_template_create builds every host table without touching a GPU; bad inputs are refused."""
+    L, lib = _lib()
+    s = np.linspace(5.0, 3000.0, 50)
+    q = np.zeros((5, s.size))
+    q[0] = 1.0
+    e = np.linspace(0, 0.2, 11)
+    dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    h = C.c_void_p()
+    assert lib.lpp_template_create(dp(q), dp(s), s.size, dp(e), 10, 0.0, C.byref(h)) == L.LPP_OK
+    sz = C.c_size_t()
+    assert lib.lpp_template_workspace_size(h, C.byref(sz)) == L.LPP_OK
+    assert sz.value > 16 * 4096 * 8
+    assert lib.lpp_convolve_template(h, None, 1, None, None) == L.LPP_ERR_INVALID_ARG
+    lib.lpp_template_destroy(h)
+    bad = s[::-1].copy()
+    assert lib.lpp_template_create(dp(q), dp(bad), s.size, dp(e), 10, 0.0, C.byref(h)) == L.LPP_ERR_INVALID_ARG
