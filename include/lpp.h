@@ -191,6 +191,36 @@ lpp_status lpp_template_set_workspace(lpp_template_t tmpl, void* device_ptr, siz
 lpp_status lpp_convolve_template(lpp_template_t tmpl, const double* params, int n_templates, double* out,
                                  void* stream);
 
+/* ------------------------------------------------------------------ surrogate
+ * Template surrogate network (no counterpart in the paper; it emulates the output of
+ * lpp_convolve_template): x (6 parameters) -> [Linear 256, GELU] x 4 -> Linear 320, with
+ * GELU(z) = z (1 + erf(z/sqrt2)) / 2.  Every matrix product takes BF16 operands (weights,
+ * layer inputs, back-propagated gradients) and accumulates in FP32 on the tensor cores;
+ * Adam (beta 0.9, 0.999, eps 1e-8, bias-corrected) updates FP32 master weights.
+ * Parameters travel as one FP32 host array: for each layer W [out][in] then b [out]
+ * (in/out = 6/256, 256/256, 256/256, 256/256, 256/320). */
+typedef struct lpp_surrogate_s* lpp_surrogate_t;
+
+/* batch: training minibatch and inference chunk (multiple of 32). */
+lpp_status lpp_surrogate_create(int batch, lpp_surrogate_t* net);
+void lpp_surrogate_destroy(lpp_surrogate_t net);
+lpp_status lpp_surrogate_workspace_size(lpp_surrogate_t net, size_t* bytes);
+/* Device workspace (256-byte aligned, caller-owned) and initial host parameters; resets Adam. */
+lpp_status lpp_surrogate_set_workspace(lpp_surrogate_t net, void* device_ptr, size_t bytes, const float* params,
+                                       void* stream);
+lpp_status lpp_surrogate_get_params(lpp_surrogate_t net, float* params, void* stream);
+/* n_steps Adam steps; step i uses rows schedule[i*batch .. (i+1)*batch) of the device arrays
+ * x [n][6] and y [n][320]; losses (device, optional) [n_steps] receive each minibatch's mean
+ * squared error before its update.  Asynchronous on `stream`. */
+lpp_status lpp_surrogate_train(lpp_surrogate_t net, const float* x, const float* y, const int* schedule,
+                               int n_steps, float lr, double* losses, void* stream);
+/* Gradients of the mean squared error of one minibatch (rows idx[0..batch) of device x, y)
+ * without changing the network: host grads in the parameter layout, host *loss.  Synchronous. */
+lpp_status lpp_surrogate_gradients(lpp_surrogate_t net, const float* x, const float* y, const int* idx,
+                                   float* grads, double* loss, void* stream);
+/* Forward pass: device x [n][6] -> device y [n][320], in chunks of `batch` rows. */
+lpp_status lpp_surrogate_infer(lpp_surrogate_t net, const float* x, int n, float* y, void* stream);
+
 /* Legendre multipoles of P_gE (l = 0,2), P_EE and P_BB (l = 0,2,4) from normalised
  * native moments p[LPP_N_MOMENTS][n_bins][2] (real parts), by the completeness of
  * {Lm_L/(1-mu^2)^(m/2)} (Sec. 2.4) and P_EE/BB = (P_+ +- P_-)/2 (Eq. relation_pm_EB).

@@ -1,0 +1,548 @@
+// Template surrogate network: 6 -> [256, GELU] x 4 -> 320, BF16 operands, FP32 accumulation.
+//
+// Every matrix product C = A B^T (A [M x K], B [N x K], both BF16 with K contiguous) runs on
+// the tensor cores (mma.m16n8k16, BF16 in, FP32 accumulate) in 64 x 64 CTA tiles with fused
+// epilogues: bias + GELU for hidden layers (the BF16 activation and, when training, its
+// transpose), bias for the output, plain FP32 for weight gradients, and the GELU derivative
+// for back-propagated gradients.  Adam keeps FP32 master weights and refreshes their BF16
+// copies (and transposes) after every step.  The training loop is native: one call runs all
+// steps of a schedule of minibatch indices.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "lpp_internal.h"
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+constexpr int kLayers = 5;
+constexpr int kIn[kLayers] = {6, 256, 256, 256, 256};
+constexpr int kInPad[kLayers] = {16, 256, 256, 256, 256};
+constexpr int kOut[kLayers] = {256, 256, 256, 256, 320};
+constexpr int kNout = 320;
+constexpr int kNin = 6;
+
+enum Epi { EPI_HIDDEN = 0, EPI_OUT = 1, EPI_DW = 2, EPI_DA_GELU = 3 };
+
+struct GemmArgs {
+    const bf16* A;
+    int lda;
+    const bf16* B;
+    int ldb;
+    int M, N, K;
+    int epi;
+    const float* bias;
+    float* z;          // hidden: pre-activation; out: output; dW: gradient
+    int ldz;
+    bf16* a16;         // hidden: BF16 GELU(z); da: BF16 gradient
+    int ld16;
+    bf16* a16t;        // transposed BF16 copy (optional)
+    int ld16t;
+    const float* zprev;   // da: pre-activation of the layer below
+    int ldzp;
+    float* g32;           // da: FP32 gradient
+    int ldg;
+};
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+constexpr int BM = 64, BN = 64, BK = 32, LDS = BK + 8;
+
+__global__ void __launch_bounds__(128) k_gemm(GemmArgs a) {
+    __shared__ __align__(16) bf16 As[BM][LDS];
+    __shared__ __align__(16) bf16 Bs[BN][LDS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp >> 1, wn = warp & 1;
+    const int g = lane >> 2, t = lane & 3;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+    for (int k0 = 0; k0 < a.K; k0 += BK) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int c = tid + i * 128;   // 256 chunks of 8 BF16 per tile
+            const int row = c >> 2, col = (c & 3) * 8;
+            uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
+            if (m0 + row < a.M && k0 + col < a.K)
+                va = *reinterpret_cast<const uint4*>(a.A + (size_t)(m0 + row) * a.lda + k0 + col);
+            if (n0 + row < a.N && k0 + col < a.K)
+                vb = *reinterpret_cast<const uint4*>(a.B + (size_t)(n0 + row) * a.ldb + k0 + col);
+            *reinterpret_cast<uint4*>(&As[row][col]) = va;
+            *reinterpret_cast<uint4*>(&Bs[row][col]) = vb;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi) {
+                const int r = wm * 32 + mi * 16 + g;
+                af[mi][0] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 2 * t]);
+                af[mi][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 2 * t]);
+                af[mi][2] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 2 * t + 8]);
+                af[mi][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 2 * t + 8]);
+            }
+#pragma unroll
+            for (int ni = 0; ni < 4; ++ni) {
+                const int n = wn * 32 + ni * 8 + g;
+                bfr[ni][0] = *reinterpret_cast<const uint32_t*>(&Bs[n][kk + 2 * t]);
+                bfr[ni][1] = *reinterpret_cast<const uint32_t*>(&Bs[n][kk + 2 * t + 8]);
+            }
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni)
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                        : "+f"(acc[mi][ni][0]), "+f"(acc[mi][ni][1]), "+f"(acc[mi][ni][2]), "+f"(acc[mi][ni][3])
+                        : "r"(af[mi][0]), "r"(af[mi][1]), "r"(af[mi][2]), "r"(af[mi][3]), "r"(bfr[ni][0]),
+                          "r"(bfr[ni][1]));
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int row = m0 + wm * 32 + mi * 16 + g + (r >= 2 ? 8 : 0);
+                const int col = n0 + wn * 32 + ni * 8 + 2 * t + (r & 1);
+                if (row >= a.M || col >= a.N) continue;
+                const float v = acc[mi][ni][r];
+                if (a.epi == EPI_HIDDEN) {
+                    const float z = v + a.bias[col];
+                    a.z[(size_t)row * a.ldz + col] = z;
+                    const bf16 h = __float2bfloat16_rn(gelu(z));
+                    a.a16[(size_t)row * a.ld16 + col] = h;
+                    if (a.a16t) a.a16t[(size_t)col * a.ld16t + row] = h;
+                } else if (a.epi == EPI_OUT) {
+                    a.z[(size_t)row * a.ldz + col] = v + a.bias[col];
+                } else if (a.epi == EPI_DW) {
+                    a.z[(size_t)row * a.ldz + col] = v;
+                } else {
+                    const float gv = v * gelu_grad(a.zprev[(size_t)row * a.ldzp + col]);
+                    a.g32[(size_t)row * a.ldg + col] = gv;
+                    const bf16 h = __float2bfloat16_rn(gv);
+                    a.a16[(size_t)row * a.ld16 + col] = h;
+                    a.a16t[(size_t)col * a.ld16t + row] = h;
+                }
+            }
+}
+
+cudaError_t gemm(const GemmArgs& a, cudaStream_t st) {
+    dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM);
+    k_gemm<<<grid, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// inputs x [m][6] FP32 -> BF16 [m][16] (zero padded) and, when training, its transpose [16][ld]
+__global__ void k_input(const float* __restrict__ x, const int* __restrict__ idx, int m, bf16* a0, bf16* a0t,
+                        int ldt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m * 16; i += gridDim.x * blockDim.x) {
+        const int r = i / 16, c = i % 16;
+        const int src = idx ? idx[r] : r;
+        const float v = c < kNin ? x[(size_t)src * kNin + c] : 0.f;
+        const bf16 h = __float2bfloat16_rn(v);
+        a0[i] = h;
+        if (a0t) a0t[(size_t)c * ldt + r] = h;
+    }
+}
+
+// dL/d out = 2 (out - y) / (m * 320); loss sum of squares into loss (FP64)
+__global__ void k_loss(const float* __restrict__ out, const float* __restrict__ y, const int* __restrict__ idx, int m,
+                       float* g32, bf16* g16, bf16* g16t, int ldt, double* loss) {
+    double part = 0.0;
+    const float sc = 2.0f / (float)(m * kNout);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m * kNout; i += gridDim.x * blockDim.x) {
+        const int r = i / kNout, c = i % kNout;
+        const int src = idx ? idx[r] : r;
+        const float d = out[i] - y[(size_t)src * kNout + c];
+        part += (double)d * d;
+        const float gv = sc * d;
+        g32[i] = gv;
+        const bf16 h = __float2bfloat16_rn(gv);
+        g16[i] = h;
+        g16t[(size_t)c * ldt + r] = h;
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(loss, part / (double)(m * kNout));
+}
+
+// db[n] = sum over rows of g[m][n]
+__global__ void k_bias_grad(const float* __restrict__ g, int m, int n, float* db) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    float s = 0.f;
+    for (int r = 0; r < m; ++r) s += g[(size_t)r * n + c];
+    db[c] = s;
+}
+
+struct AdamLayer {
+    float *w, *b, *mw, *vw, *mb, *vb, *dw, *db;
+    bf16 *w16, *w16t;
+    int out, in, inp;
+};
+struct AdamArgs {
+    AdamLayer L[kLayers];
+    float lr, b1, b2, eps, bc1, bc2;
+};
+
+__global__ void k_adam(AdamArgs a) {
+    const int layer = blockIdx.y;
+    const AdamLayer& L = a.L[layer];
+    const int nw = L.out * L.inp;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nw + L.out; i += gridDim.x * blockDim.x) {
+        float *p, *m, *v;
+        float gr;
+        if (i < nw) {
+            const int c = i % L.inp;
+            if (c >= L.in) continue;   // padded input columns stay zero
+            p = L.w + i;
+            m = L.mw + i;
+            v = L.vw + i;
+            gr = L.dw[i];
+        } else {
+            const int j = i - nw;
+            p = L.b + j;
+            m = L.mb + j;
+            v = L.vb + j;
+            gr = L.db[j];
+        }
+        const float mm = a.b1 * *m + (1.f - a.b1) * gr;
+        const float vv = a.b2 * *v + (1.f - a.b2) * gr * gr;
+        *m = mm;
+        *v = vv;
+        const float upd = a.lr * (mm / a.bc1) / (sqrtf(vv / a.bc2) + a.eps);
+        const float nwv = *p - upd;
+        *p = nwv;
+        if (i < nw) {
+            const int r = i / L.inp, c = i % L.inp;
+            const bf16 h = __float2bfloat16_rn(nwv);
+            L.w16[i] = h;
+            L.w16t[(size_t)c * L.out + r] = h;
+        }
+    }
+}
+
+// BF16 copies of the master weights (after loading parameters)
+__global__ void k_refresh(AdamArgs a) {
+    const int layer = blockIdx.y;
+    const AdamLayer& L = a.L[layer];
+    const int nw = L.out * L.inp;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += gridDim.x * blockDim.x) {
+        const int r = i / L.inp, c = i % L.inp;
+        const bf16 h = __float2bfloat16_rn(L.w[i]);
+        L.w16[i] = h;
+        L.w16t[(size_t)c * L.out + r] = h;
+    }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct lpp_surrogate_s {
+    int batch = 0;
+    long long step = 0;
+    char* ws = nullptr;
+    size_t need = 0;
+    // offsets
+    size_t w[kLayers], b[kLayers], mw[kLayers], vw[kLayers], mb[kLayers], vb[kLayers], dw[kLayers], db[kLayers];
+    size_t w16[kLayers], w16t[kLayers], act[kLayers + 1], actt[kLayers], z[kLayers];
+    size_t g32[2], g16[2], g16t[2], loss;
+};
+
+extern "C" lpp_status lpp_surrogate_create(int batch, lpp_surrogate_t* out) {
+    if (!out || batch < 32 || batch % 32 != 0 || batch > (1 << 20)) return LPP_ERR_INVALID_ARG;
+    lpp_surrogate_t s = new lpp_surrogate_s();
+    s->batch = batch;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+    for (int l = 0; l < kLayers; ++l) {
+        const size_t nw = (size_t)kOut[l] * kInPad[l];
+        s->w[l] = take(nw * 4);
+        s->mw[l] = take(nw * 4);
+        s->vw[l] = take(nw * 4);
+        s->dw[l] = take(nw * 4);
+        s->b[l] = take(kOut[l] * 4);
+        s->mb[l] = take(kOut[l] * 4);
+        s->vb[l] = take(kOut[l] * 4);
+        s->db[l] = take(kOut[l] * 4);
+        s->w16[l] = take(nw * 2);
+        s->w16t[l] = take(nw * 2);
+        s->act[l] = take((size_t)batch * kInPad[l] * 2);
+        s->actt[l] = take((size_t)batch * kInPad[l] * 2);
+        s->z[l] = take((size_t)batch * kOut[l] * 4);
+    }
+    s->act[kLayers] = 0;
+    for (int i = 0; i < 2; ++i) {
+        s->g32[i] = take((size_t)batch * kNout * 4);
+        s->g16[i] = take((size_t)batch * kNout * 2);
+        s->g16t[i] = take((size_t)batch * kNout * 2);
+    }
+    s->loss = take(8);
+    s->need = off;
+    *out = s;
+    return LPP_OK;
+}
+
+extern "C" void lpp_surrogate_destroy(lpp_surrogate_t s) { delete s; }
+
+extern "C" lpp_status lpp_surrogate_workspace_size(lpp_surrogate_t s, size_t* bytes) {
+    if (!s || !bytes) return LPP_ERR_INVALID_ARG;
+    *bytes = s->need;
+    return LPP_OK;
+}
+
+static AdamArgs adam_args(lpp_surrogate_t s) {
+    AdamArgs a;
+    memset(&a, 0, sizeof(a));
+    for (int l = 0; l < kLayers; ++l) {
+        AdamLayer& L = a.L[l];
+        L.w = (float*)(s->ws + s->w[l]);
+        L.b = (float*)(s->ws + s->b[l]);
+        L.mw = (float*)(s->ws + s->mw[l]);
+        L.vw = (float*)(s->ws + s->vw[l]);
+        L.mb = (float*)(s->ws + s->mb[l]);
+        L.vb = (float*)(s->ws + s->vb[l]);
+        L.dw = (float*)(s->ws + s->dw[l]);
+        L.db = (float*)(s->ws + s->db[l]);
+        L.w16 = (bf16*)(s->ws + s->w16[l]);
+        L.w16t = (bf16*)(s->ws + s->w16t[l]);
+        L.out = kOut[l];
+        L.in = kIn[l];
+        L.inp = kInPad[l];
+    }
+    return a;
+}
+
+// Host params: for every layer W [out][in] then b [out], FP32, unpadded.
+extern "C" lpp_status lpp_surrogate_set_workspace(lpp_surrogate_t s, void* dev, size_t bytes, const float* params,
+                                                  void* stream) {
+    if (!s || !dev || !params) return LPP_ERR_INVALID_ARG;
+    if (((uintptr_t)dev & 255) != 0) return LPP_ERR_INVALID_ARG;
+    if (bytes < s->need) return LPP_ERR_WORKSPACE;
+    s->ws = (char*)dev;
+    s->step = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(s->ws, 0, s->need, st) != cudaSuccess) return LPP_ERR_CUDA;
+    std::vector<float> wpad;
+    size_t p = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        wpad.assign((size_t)kOut[l] * kInPad[l], 0.f);
+        for (int r = 0; r < kOut[l]; ++r)
+            for (int c = 0; c < kIn[l]; ++c) wpad[(size_t)r * kInPad[l] + c] = params[p++];
+        if (cudaMemcpyAsync(s->ws + s->w[l], wpad.data(), wpad.size() * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return LPP_ERR_CUDA;
+        if (cudaMemcpyAsync(s->ws + s->b[l], params + p, kOut[l] * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return LPP_ERR_CUDA;
+        p += kOut[l];
+        if (cudaStreamSynchronize(st) != cudaSuccess) return LPP_ERR_CUDA;
+    }
+    AdamArgs a = adam_args(s);
+    k_refresh<<<dim3(64, kLayers), 256, 0, st>>>(a);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return LPP_ERR_CUDA;
+    return LPP_OK;
+}
+
+extern "C" lpp_status lpp_surrogate_get_params(lpp_surrogate_t s, float* params, void* stream) {
+    if (!s || !s->ws || !params) return LPP_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<float> wpad;
+    size_t p = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        wpad.resize((size_t)kOut[l] * kInPad[l]);
+        if (cudaMemcpyAsync(wpad.data(), s->ws + s->w[l], wpad.size() * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return LPP_ERR_CUDA;
+        if (cudaMemcpyAsync(params + p + (size_t)kOut[l] * kIn[l], s->ws + s->b[l], kOut[l] * 4,
+                            cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return LPP_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return LPP_ERR_CUDA;
+        for (int r = 0; r < kOut[l]; ++r)
+            for (int c = 0; c < kIn[l]; ++c) params[p++] = wpad[(size_t)r * kInPad[l] + c];
+        p += kOut[l];
+    }
+    return LPP_OK;
+}
+
+// forward pass of m <= batch rows (inputs gathered through idx when given)
+static cudaError_t forward(lpp_surrogate_t s, const float* x, const int* idx, int m, bool train, float* out_final,
+                           cudaStream_t st) {
+    const int B = s->batch;
+    bf16* a0 = (bf16*)(s->ws + s->act[0]);
+    k_input<<<(m * 16 + 255) / 256, 256, 0, st>>>(x, idx, m, a0, train ? (bf16*)(s->ws + s->actt[0]) : nullptr, B);
+    for (int l = 0; l < kLayers; ++l) {
+        GemmArgs g;
+        memset(&g, 0, sizeof(g));
+        g.A = (const bf16*)(s->ws + s->act[l]);
+        g.lda = kInPad[l];
+        g.B = (const bf16*)(s->ws + s->w16[l]);
+        g.ldb = kInPad[l];
+        g.M = m;
+        g.N = kOut[l];
+        g.K = kInPad[l];
+        g.bias = (const float*)(s->ws + s->b[l]);
+        if (l < kLayers - 1) {
+            g.epi = EPI_HIDDEN;
+            g.z = (float*)(s->ws + s->z[l]);
+            g.ldz = kOut[l];
+            g.a16 = (bf16*)(s->ws + s->act[l + 1]);
+            g.ld16 = kInPad[l + 1];
+            g.a16t = train ? (bf16*)(s->ws + s->actt[l + 1]) : nullptr;
+            g.ld16t = B;
+        } else {
+            g.epi = EPI_OUT;
+            g.z = out_final ? out_final : (float*)(s->ws + s->z[l]);
+            g.ldz = kOut[l];
+        }
+        cudaError_t e = gemm(g, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+extern "C" lpp_status lpp_surrogate_infer(lpp_surrogate_t s, const float* x, int n, float* y, void* stream) {
+    if (!s || !s->ws || n < 0 || (n > 0 && (!x || !y))) return LPP_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int r0 = 0; r0 < n; r0 += s->batch) {
+        const int m = n - r0 < s->batch ? n - r0 : s->batch;
+        if (forward(s, x + (size_t)r0 * kNin, nullptr, m, false, y + (size_t)r0 * kNout, st) != cudaSuccess)
+            return LPP_ERR_CUDA;
+    }
+    return LPP_OK;
+}
+
+// One Adam step on the minibatch rows idx[0..batch) of (x, y); the mean squared error of the
+// minibatch (before the step) is added to *loss_out (device).
+static cudaError_t train_step(lpp_surrogate_t s, const float* x, const float* y, const int* idx, float lr,
+                              double* loss_out, cudaStream_t st) {
+    const int B = s->batch;
+    cudaError_t e = forward(s, x, idx, B, true, nullptr, st);
+    if (e != cudaSuccess) return e;
+    int cur = 0;
+    k_loss<<<(B * kNout + 255) / 256, 256, 0, st>>>((const float*)(s->ws + s->z[kLayers - 1]), y, idx, B,
+                                                    (float*)(s->ws + s->g32[cur]), (bf16*)(s->ws + s->g16[cur]),
+                                                    (bf16*)(s->ws + s->g16t[cur]), B, loss_out);
+    for (int l = kLayers - 1; l >= 0; --l) {
+        // dW_l = g^T a_l : [out x inp] = [out x B] . [inp x B]^T
+        GemmArgs gw;
+        memset(&gw, 0, sizeof(gw));
+        gw.A = (const bf16*)(s->ws + s->g16t[cur]);
+        gw.lda = B;
+        gw.B = (const bf16*)(s->ws + s->actt[l]);
+        gw.ldb = B;
+        gw.M = kOut[l];
+        gw.N = kInPad[l];
+        gw.K = B;
+        gw.epi = EPI_DW;
+        gw.z = (float*)(s->ws + s->dw[l]);
+        gw.ldz = kInPad[l];
+        if ((e = gemm(gw, st)) != cudaSuccess) return e;
+        k_bias_grad<<<(kOut[l] + 127) / 128, 128, 0, st>>>((const float*)(s->ws + s->g32[cur]), B, kOut[l],
+                                                           (float*)(s->ws + s->db[l]));
+        if (l > 0) {
+            // g_{l-1} = (g_l W_l) * GELU'(z_{l-1}) : [B x inp] = [B x out] . [inp x out]^T
+            GemmArgs gd;
+            memset(&gd, 0, sizeof(gd));
+            gd.A = (const bf16*)(s->ws + s->g16[cur]);
+            gd.lda = kOut[l];
+            gd.B = (const bf16*)(s->ws + s->w16t[l]);
+            gd.ldb = kOut[l];
+            gd.M = B;
+            gd.N = kInPad[l];
+            gd.K = kOut[l];
+            gd.epi = EPI_DA_GELU;
+            gd.zprev = (const float*)(s->ws + s->z[l - 1]);
+            gd.ldzp = kOut[l - 1];
+            gd.g32 = (float*)(s->ws + s->g32[1 - cur]);
+            gd.ldg = kInPad[l];
+            gd.a16 = (bf16*)(s->ws + s->g16[1 - cur]);
+            gd.ld16 = kInPad[l];
+            gd.a16t = (bf16*)(s->ws + s->g16t[1 - cur]);
+            gd.ld16t = B;
+            if ((e = gemm(gd, st)) != cudaSuccess) return e;
+            cur = 1 - cur;
+        }
+    }
+    s->step += 1;
+    AdamArgs a = adam_args(s);
+    a.lr = lr;
+    a.b1 = 0.9f;
+    a.b2 = 0.999f;
+    a.eps = 1e-8f;
+    a.bc1 = (float)(1.0 - pow(0.9, (double)s->step));
+    a.bc2 = (float)(1.0 - pow(0.999, (double)s->step));
+    k_adam<<<dim3(128, kLayers), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+extern "C" lpp_status lpp_surrogate_train(lpp_surrogate_t s, const float* x, const float* y, const int* schedule,
+                                          int n_steps, float lr, double* losses, void* stream) {
+    if (!s || !s->ws || !x || !y || !schedule || n_steps < 0) return LPP_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (losses && cudaMemsetAsync(losses, 0, (size_t)n_steps * sizeof(double), st) != cudaSuccess) return LPP_ERR_CUDA;
+    double* scratch = (double*)(s->ws + s->loss);
+    for (int i = 0; i < n_steps; ++i) {
+        double* lo = losses ? losses + i : scratch;
+        if (train_step(s, x, y, schedule + (size_t)i * s->batch, lr, lo, st) != cudaSuccess) return LPP_ERR_CUDA;
+    }
+    return LPP_OK;
+}
+
+// Gradients of the loss of one minibatch without an update (for checks): host dW [out][in], db [out].
+extern "C" lpp_status lpp_surrogate_gradients(lpp_surrogate_t s, const float* x, const float* y, const int* idx,
+                                              float* grads, double* loss, void* stream) {
+    if (!s || !s->ws || !x || !y || !idx || !grads) return LPP_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long saved = s->step;
+    double* lo = (double*)(s->ws + s->loss);
+    if (cudaMemsetAsync(lo, 0, 8, st) != cudaSuccess) return LPP_ERR_CUDA;
+    // run the step with lr = 0 so that only the gradients are formed (Adam moments are restored below)
+    std::vector<char> mom;
+    for (int l = 0; l < kLayers; ++l) {
+        const size_t nw = (size_t)kOut[l] * kInPad[l] * 4;
+        const size_t off0 = mom.size();
+        mom.resize(off0 + 2 * nw + 2 * kOut[l] * 4);
+        cudaMemcpyAsync(mom.data() + off0, s->ws + s->mw[l], nw, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(mom.data() + off0 + nw, s->ws + s->vw[l], nw, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(mom.data() + off0 + 2 * nw, s->ws + s->mb[l], kOut[l] * 4, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(mom.data() + off0 + 2 * nw + kOut[l] * 4, s->ws + s->vb[l], kOut[l] * 4,
+                        cudaMemcpyDeviceToHost, st);
+    }
+    if (train_step(s, x, y, idx, 0.0f, lo, st) != cudaSuccess) return LPP_ERR_CUDA;
+    size_t p = 0, mo = 0;
+    std::vector<float> dw;
+    for (int l = 0; l < kLayers; ++l) {
+        const size_t nw = (size_t)kOut[l] * kInPad[l];
+        dw.resize(nw);
+        cudaMemcpyAsync(dw.data(), s->ws + s->dw[l], nw * 4, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(grads + p + (size_t)kOut[l] * kIn[l], s->ws + s->db[l], kOut[l] * 4, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(s->ws + s->mw[l], mom.data() + mo, nw * 4, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(s->ws + s->vw[l], mom.data() + mo + nw * 4, nw * 4, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(s->ws + s->mb[l], mom.data() + mo + 2 * nw * 4, kOut[l] * 4, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(s->ws + s->vb[l], mom.data() + mo + 2 * nw * 4 + kOut[l] * 4, kOut[l] * 4,
+                        cudaMemcpyHostToDevice, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return LPP_ERR_CUDA;
+        for (int r = 0; r < kOut[l]; ++r)
+            for (int c = 0; c < kIn[l]; ++c) grads[p++] = dw[(size_t)r * kInPad[l] + c];
+        p += kOut[l];
+        mo += 2 * nw * 4 + 2 * kOut[l] * 4;
+    }
+    s->step = saved;
+    if (loss && cudaMemcpyAsync(loss, lo, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return LPP_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return LPP_ERR_CUDA;
+    return LPP_OK;
+}

@@ -78,6 +78,16 @@ EXPORTS = {
     "lpp_template_workspace_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "lpp_template_set_workspace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "lpp_convolve_template": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "lpp_surrogate_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p)]),
+    "lpp_surrogate_destroy": (None, [C.c_void_p]),
+    "lpp_surrogate_workspace_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "lpp_surrogate_set_workspace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_float), C.c_void_p]),
+    "lpp_surrogate_get_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_void_p]),
+    "lpp_surrogate_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_float,
+                                      C.c_void_p, C.c_void_p]),
+    "lpp_surrogate_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_float),
+                                          C.POINTER(C.c_double), C.c_void_p]),
+    "lpp_surrogate_infer": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "lpp_derive_eb": (C.c_int, [C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                 C.POINTER(C.c_double)]),
     "lpp_plan_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
@@ -314,6 +324,94 @@ class Template:
     def close(self):
         if getattr(self, "h", None):
             self.lib.lpp_template_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+SURROGATE_SIZES = (6, 256, 256, 256, 256, 320)
+
+
+def flatten_params(layers) -> np.ndarray:
+    """[(W [out, in], b [out]), ...] -> the FP32 parameter array of the C ABI."""
+    return np.ascontiguousarray(np.concatenate([np.concatenate([w.ravel(), b.ravel()]) for w, b in layers]),
+                                dtype=np.float32)
+
+
+def unflatten_params(flat):
+    out, p = [], 0
+    for fi, fo in zip(SURROGATE_SIZES[:-1], SURROGATE_SIZES[1:]):
+        w = flat[p:p + fo * fi].reshape(fo, fi)
+        p += fo * fi
+        b = flat[p:p + fo]
+        p += fo
+        out.append((w, b))
+    return out
+
+
+class Surrogate:
+    """The template surrogate network (lpp_surrogate_*) on the current CUDA device."""
+
+    def __init__(self, params_flat, batch: int = 256, stream=None, device=None):
+        import torch
+        self.lib = load_library()
+        self.batch = batch
+        h = C.c_void_p()
+        _check(self.lib, self.lib.lpp_surrogate_create(batch, C.byref(h)))
+        self.h = h
+        sz = C.c_size_t()
+        _check(self.lib, self.lib.lpp_surrogate_workspace_size(h, C.byref(sz)))
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.workspace = torch.empty(sz.value + 256, dtype=torch.uint8, device=self.device)
+        addr = self.workspace.data_ptr()
+        off = (-addr) % 256
+        p = np.ascontiguousarray(params_flat, dtype=np.float32)
+        _check(self.lib, self.lib.lpp_surrogate_set_workspace(h, C.c_void_p(addr + off), C.c_size_t(sz.value),
+                                                              p.ctypes.data_as(C.POINTER(C.c_float)),
+                                                              C.c_void_p(self.stream.cuda_stream)))
+
+    def params(self) -> np.ndarray:
+        n = sum(fo * fi + fo for fi, fo in zip(SURROGATE_SIZES[:-1], SURROGATE_SIZES[1:]))
+        out = np.zeros(n, dtype=np.float32)
+        _check(self.lib, self.lib.lpp_surrogate_get_params(self.h, out.ctypes.data_as(C.POINTER(C.c_float)),
+                                                           C.c_void_p(self.stream.cuda_stream)))
+        return out
+
+    def train(self, x, y, schedule, lr: float, losses=None):
+        """x, y: float32 CUDA tensors; schedule: int32 CUDA tensor [n_steps * batch]."""
+        n_steps = int(schedule.numel()) // self.batch
+        _check(self.lib, self.lib.lpp_surrogate_train(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                                      C.c_void_p(schedule.data_ptr()), n_steps, float(lr),
+                                                      C.c_void_p(losses.data_ptr()) if losses is not None else None,
+                                                      C.c_void_p(self.stream.cuda_stream)))
+
+    def gradients(self, x, y, idx):
+        n = sum(fo * fi + fo for fi, fo in zip(SURROGATE_SIZES[:-1], SURROGATE_SIZES[1:]))
+        g = np.zeros(n, dtype=np.float32)
+        loss = C.c_double()
+        _check(self.lib, self.lib.lpp_surrogate_gradients(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                                          C.c_void_p(idx.data_ptr()),
+                                                          g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(loss),
+                                                          C.c_void_p(self.stream.cuda_stream)))
+        return g, loss.value
+
+    def infer(self, x, out=None):
+        import torch
+        n = int(x.shape[0])
+        if out is None:
+            out = torch.empty((n, 320), dtype=torch.float32, device=x.device)
+        _check(self.lib, self.lib.lpp_surrogate_infer(self.h, C.c_void_p(x.data_ptr()), n, C.c_void_p(out.data_ptr()),
+                                                      C.c_void_p(self.stream.cuda_stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lpp_surrogate_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -340,3 +340,26 @@ def workload_survey(n_data: int = 1_500_000, n_rand: int = 15_000_000, n: int = 
     data, rand = survey_mock(n_data, n_rand, n_field, box, pk, 1.0, 0.25, seed, obs)
     return Workload("survey_cap_L4000_N512_tsc_il", n, box, (0.0, 0.0, 0.0), obs, (-1.0, 0.0, 0.0),
                     3, True, data, randoms=rand, k_edges=linear_edges(0.0, 0.2, 40), dtype="f32")
+
+
+# ----------------------------------------------------------------- surrogate inputs
+SURROGATE_RANGES = np.array([[0.0, 3.0], [1.0, 3.0], [0.6, 1.0], [-0.2, 0.2], [0.1, 0.3], [0.5, 2.0]])
+
+
+def latin_hypercube(n: int, ranges=SURROGATE_RANGES, seed: int = 0) -> np.ndarray:
+    """n points of a Latin hypercube over the box `ranges` ([dim, 2]): one point per stratum
+    of every coordinate, strata shuffled independently, uniform within each stratum."""
+    rng = _rng(seed, 11)
+    d = len(ranges)
+    u = (np.stack([rng.permutation(n) for _ in range(d)], axis=1) + rng.random((n, d))) / n
+    return ranges[:, 0] + u * (ranges[:, 1] - ranges[:, 0])
+
+
+def surrogate_init(seed: int = 0, sizes=(6, 256, 256, 256, 256, 320)):
+    """Initial weights W [out, in] ~ U(-1/sqrt(in), 1/sqrt(in)) and zero biases (FP32)."""
+    rng = _rng(seed, 12)
+    layers = []
+    for fi, fo in zip(sizes[:-1], sizes[1:]):
+        lim = 1.0 / math.sqrt(fi)
+        layers.append((rng.uniform(-lim, lim, (fo, fi)).astype(np.float32), np.zeros(fo, dtype=np.float32)))
+    return layers
