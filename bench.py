@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     return ap.parse_args()
 
 
@@ -203,6 +204,49 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------- GPU arm
+def template_leg(plan, est, wl, dev):
+    """Window-convolved templates for the survey: Q_l(s) from its randoms, then templates/s of
+    the FFTLog path and of the trained surrogate (20k Latin-hypercube training templates),
+    and the surrogate's error on 2k held-out parameter sets in Gaussian error bars."""
+    import torch
+
+    from paper_2202_11839_gb300 import lpp as L
+    from paper_2202_11839_gb300 import surrogate as SG
+    from paper_2202_11839_gb300 import synthetic as S
+    s_edges = np.linspace(0.0, 3800.0, 191)
+    q, s_mean, npts, _ = plan.window_q(s_edges)
+    keep = npts > 0
+    tm = L.Template(q[:, keep], s_mean[keep], wl.k_edges, shot_plus=est.shot_plus, stream=plan.stream, device=dev)
+    em = SG.Emulator(tm, SG.survey_volume(), est.shot_dd)
+    em.train()
+    rep = em.evaluate(em.cfg.n_test, seed=77)
+    net = em.inference_net(8192)
+    th = torch.from_numpy(S.latin_hypercube(8192, seed=78)).to(dev)
+    rates = {}
+    for name, fn in (("plain", em.plain), ("surrogate", net.predict)):
+        for _ in range(3):
+            fn(th)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(plan.stream)
+        for _ in range(5):
+            fn(th)
+        e1.record(plan.stream)
+        torch.cuda.synchronize()
+        rates[name] = 5 * 8192 / (e0.elapsed_time(e1) / 1000.0)
+    out = {"unit": "templates/s", "plain": rates["plain"], "surrogate": rates["surrogate"],
+           "speedup": rates["surrogate"] / rates["plain"], "batch": 8192,
+           "error_sigma": {"rms": rep.rms_sigma, "p99": rep.p99_sigma, "max": rep.max_sigma},
+           "baseline_only_sigma": {"rms": rep.baseline_rms_sigma, "max": rep.baseline_max_sigma},
+           "n_train": em.cfg.n_train, "n_test": em.cfg.n_test, "train_s": rep.train_seconds,
+           "data_s": rep.data_seconds, "outputs": "gE_0,2 EE_0,2,4 BB_0,2,4 x 40 shells",
+           "window": "Q_l(s) of the survey randoms on the same grid", "dtype": "bf16 network, f64 FFTLog"}
+    net.close()
+    em.net.close()
+    tm.close()
+    return out
+
+
 def run_lpp(args):
     import torch
 
@@ -269,6 +313,10 @@ def run_lpp(args):
             for k, v in stats.items()}
     launches = sum(v["launches"] for v in stats.values())
 
+    templates = None
+    if rank == 0 and not args.no_surrogate:
+        templates = template_leg(plan, est, wl, dev)
+
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -333,6 +381,7 @@ def run_lpp(args):
         "gpu_launches": launches,
         "clocks": clk,
         "kernels": kern,
+        "templates": templates,
     }
     print(json.dumps(out), flush=True)
     if pg:

@@ -190,6 +190,12 @@ lpp_status lpp_template_set_workspace(lpp_template_t tmpl, void* device_ptr, siz
  * Asynchronous on `stream`. */
 lpp_status lpp_convolve_template(lpp_template_t tmpl, const double* params, int n_templates, double* out,
                                  void* stream);
+/* As lpp_convolve_template, and also the Legendre multipoles of the derived spectra
+ * (gE_0, gE_2, EE_0, EE_2, EE_4, BB_0, BB_2, BB_4; see lpp_derive_eb) standardised as
+ * (value - ref) / sigma into eb (device FP32 [n_templates][8][n_bins]); eb_ref and eb_sigma
+ * are device [8][n_bins] or NULL (0 and 1). */
+lpp_status lpp_convolve_template_eb(lpp_template_t tmpl, const double* params, int n_templates, double* out,
+                                    float* eb, const double* eb_ref, const double* eb_sigma, void* stream);
 
 /* ------------------------------------------------------------------ surrogate
  * Template surrogate network (no counterpart in the paper; it emulates the output of
@@ -220,6 +226,60 @@ lpp_status lpp_surrogate_gradients(lpp_surrogate_t net, const float* x, const fl
                                    float* grads, double* loss, void* stream);
 /* Forward pass: device x [n][6] -> device y [n][320], in chunks of `batch` rows. */
 lpp_status lpp_surrogate_infer(lpp_surrogate_t net, const float* x, int n, float* y, void* stream);
+
+/* Map between template parameters and the network (the emulator of lpp_convolve_template_eb
+ * built on this network).  Parameters theta = (A, b_g, sigma_8, tilt, Gamma, shot scale).
+ * The window-convolved derived curves are exactly
+ *     t_j(theta) = pre_c(theta) u_j(tilt, Gamma) + theta_5 s_j,   j = c * 40 + bin,
+ * with pre_c = A b_g sigma_8^2 for the gE curves (c = 0, 1) and A^2 sigma_8^2 for the EE/BB
+ * curves (c = 2..7): the model multipoles are proportional to b_g^2, A b_g and A^2 times the
+ * sigma_8-normalised linear spectrum (Eq. all_convolutions), and the shot-noise term adds to
+ * P_+^(0) only.  Inputs x_c = feed_c ? 2 (theta_c - lo_c) / (hi_c - lo_c) - 1 : 0.  The
+ * network learns y_j = (u_j - B_j(x)) / sd_j around the baseline
+ *     B_j(x) = mu_j + sum_ab l_a(x_p) l_b(x_q) base[a * nodes + b][j],
+ * l_a the Lagrange polynomials on the Chebyshev-Lobatto nodes -cos(pi a / (nodes - 1)) and
+ * (p, q) = base_in (both fed); base = NULL drops the sum.
+ * mu, sd, shot (= s) are device FP64 [320]; base device FP64 [nodes^2][320]; ref and sigma
+ * device FP64 [320] or NULL (0, 1) standardise the prediction as (t - ref) / sigma, as
+ * lpp_convolve_template_eb does.  The pointers are borrowed and must outlive the surrogate's
+ * use of them.  nodes in 2..8. */
+typedef struct {
+    double lo[6], hi[6];
+    int feed[6];
+    const double* mu;
+    const double* sd;
+    const double* shot;
+    const double* ref;
+    const double* sigma;
+    const double* base;
+    int base_nodes;
+    int base_in[2];
+} lpp_surrogate_map;
+
+lpp_status lpp_surrogate_set_map(lpp_surrogate_t net, const lpp_surrogate_map* map);
+/* Training targets y (device FP32 [n][320]) from device params [n][6] and the native slots
+ * that lpp_convolve_template returned for them at unit amplitude and no shot noise
+ * (device FP64 [n][10][40]). */
+lpp_status lpp_surrogate_targets(lpp_surrogate_t net, const double* params, const double* native, int n, float* y,
+                                 void* stream);
+/* Network inputs for device params [n][6] (FP64) -> device x [n][6] (FP32). */
+lpp_status lpp_surrogate_encode(lpp_surrogate_t net, const double* params, int n, float* x, void* stream);
+/* Emulated, standardised derived curves: device params [n][6] -> device out [n][320] FP32
+ * (the layout of lpp_convolve_template_eb's eb for n_bins = 40).  Requires a map. */
+lpp_status lpp_surrogate_predict(lpp_surrogate_t net, const double* params, int n, float* out, void* stream);
+
+/* Gaussian (disconnected, mode-counting) error bars of the derived multipoles, the unit in
+ * which the template emulator is trained and judged.  The paper gives no covariance; this
+ * is the standard isotropic-Gaussian reading: a shell with N_k = V (k_hi^3 - k_lo^3) / (6 pi^2)
+ * Fourier modes (both k and -k counted) and multipole l has
+ *   sigma^2(gE_l)    = (2l+1) [(P_gg + N_g)(P_EE + N_e) + P_gE^2] / N_k,
+ *   sigma^2(EE/BB_l) = 2 (2l+1) (P_EE/BB + N_e)^2 / N_k,
+ * with the monopoles p0 (host [4][n_bins]: P_gg, P_gE, P_EE, P_BB, without shot noise),
+ * the galaxy shot noise noise_g and the shot noise of each of E and B, noise_e (half that of
+ * P_+).  sigma: host [8][n_bins] in the order gE_0,2, EE_0,2,4, BB_0,2,4.
+ * LPP_ERR_INVALID_ARG for an empty or inverted shell, volume <= 0 or negative noise. */
+lpp_status lpp_gaussian_sigma(const double* p0, const double* k_edges, int n_bins, double volume, double noise_g,
+                              double noise_e, double* sigma);
 
 /* Legendre multipoles of P_gE (l = 0,2), P_EE and P_BB (l = 0,2,4) from normalised
  * native moments p[LPP_N_MOMENTS][n_bins][2] (real parts), by the completeness of

@@ -218,3 +218,29 @@ def mixing_table():
         for lp in model_multipoles((1.0, 1.0, 0.8, 0.0, 0.2, 1.0))[kind]:
             tab[(kind, L, lp)] = [float(c) for c in mixing_coefficients(kind, L, lp)]
     return tab
+
+
+def gaussian_sigma(p0, k_edges, volume, noise_g, noise_e):
+    """Gaussian error bars of the derived multipoles (gE_0,2, EE_0,2,4, BB_0,2,4).
+
+    The paper states no covariance; the reading used is the disconnected Gaussian one with
+    isotropic power: a shell holding N_k = V * (4 pi / 3) (k_hi^3 - k_lo^3) / (2 pi)^3 modes
+    (k and -k both counted, so N_k / 2 independent complex amplitudes at fixed mu) and the
+    Legendre-weighted estimator of multipole l give var(P_ab^(l)) = (2l+1) (P_aa P_bb + P_ab^2) / N_k,
+    which for an auto spectrum is 2 (2l+1) P^2 / N_k.  p0 = [P_gg, P_gE, P_EE, P_BB] monopoles
+    without shot noise; noise_g is added to P_gg and noise_e to P_EE and P_BB."""
+    p0 = np.asarray(p0, dtype=np.float64).reshape(4, -1)
+    e = np.asarray(k_edges, dtype=np.float64)
+    nk = volume * (4.0 * math.pi / 3.0) * (e[1:] ** 3 - e[:-1] ** 3) / (2.0 * math.pi) ** 3
+    gg, ge, ee, bb = p0[0] + noise_g, p0[1], p0[2] + noise_e, p0[3] + noise_e
+    out = np.zeros((8, p0.shape[1]))
+    for c, ell in enumerate([0, 2, 0, 2, 4, 0, 2, 4]):
+        f = 2 * ell + 1
+        if c < 2:
+            var = f * (gg * ee + ge * ge) / nk
+        elif c < 5:
+            var = 2 * f * ee * ee / nk
+        else:
+            var = 2 * f * bb * bb / nk
+        out[c] = np.sqrt(var)
+    return out

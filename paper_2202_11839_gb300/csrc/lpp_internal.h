@@ -106,6 +106,7 @@ void build_quadrature(int L, Quadrature& q);
 void build_kernel_polys(KernelPolys& kp);
 void legendre_poly(int l, double* c);  // power-series coefficients, c[0..l]
 void gauss_legendre(int n, double* x, double* w);
+void eb_matrices(double N[2][3], double M[3][3]);
 
 // --------------------------------------------------------------------- device params
 struct DevTables;  // opaque pointer bundle filled by the C API

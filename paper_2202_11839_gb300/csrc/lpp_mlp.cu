@@ -250,6 +250,88 @@ __global__ void k_refresh(AdamArgs a) {
     }
 }
 
+// parameters -> network inputs and network outputs -> curves (see lpp_surrogate_map)
+constexpr int kMaxNodes = 8;
+struct MapArgs {
+    float scale[kNin], shift[kNin];   // x_c = theta_c * scale_c + shift_c (0, 0 when not fed)
+    double dscale[kNin], dshift[kNin];
+    const double* mu;
+    const double* sd;
+    const double* shot;
+    const double* ref;
+    const double* sigma;
+    const double* base;               // [nodes^2][320] or null
+    int nodes, base_in[2];
+    double N[2][3], M[3][3];          // native moments -> derived multipoles
+};
+
+__global__ void k_encode(const double* __restrict__ theta, int n, float* __restrict__ x, MapArgs m) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * kNin; i += gridDim.x * blockDim.x) {
+        const int c = i % kNin;
+        x[i] = (float)(theta[i] * (double)m.scale[c] + (double)m.shift[c]);
+    }
+}
+
+// Lagrange basis at the Chebyshev-Lobatto nodes x_i = -cos(pi i / (n - 1)), evaluated at x
+__device__ void lobatto_basis(double x, int n, double* l) {
+    double xs[kMaxNodes];
+    for (int i = 0; i < n; ++i) xs[i] = -cospi((double)i / (double)(n - 1));
+    for (int i = 0; i < n; ++i) {
+        double v = 1.0;
+        for (int j = 0; j < n; ++j)
+            if (j != i) v *= (x - xs[j]) / (xs[i] - xs[j]);
+        l[i] = v;
+    }
+}
+
+// baseline mu_j + sum_ab l_a(x_p) l_b(x_q) base[a n + b][j] for one parameter row
+__device__ double baseline(const MapArgs& a, const double* t, int j) {
+    double u = a.mu[j];
+    if (a.base) {
+        double la[kMaxNodes], lb[kMaxNodes];
+        lobatto_basis(t[a.base_in[0]] * a.dscale[a.base_in[0]] + a.dshift[a.base_in[0]], a.nodes, la);
+        lobatto_basis(t[a.base_in[1]] * a.dscale[a.base_in[1]] + a.dshift[a.base_in[1]], a.nodes, lb);
+        for (int p = 0; p < a.nodes; ++p)
+            for (int q = 0; q < a.nodes; ++q) u += la[p] * lb[q] * a.base[(size_t)(p * a.nodes + q) * kNout + j];
+    }
+    return u;
+}
+
+// network outputs y [m][320] -> standardised curves (pre_c (baseline + sd y) + theta_5 s - ref) / sigma
+__global__ void k_decode(const double* __restrict__ theta, int m, const float* __restrict__ y, float* __restrict__ out,
+                         MapArgs a) {
+    constexpr int nb = kNout / 8;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m * kNout; i += gridDim.x * blockDim.x) {
+        const int r = i / kNout, j = i % kNout;
+        const double* t = theta + (size_t)r * kNin;
+        const double amp = t[2] * t[2] * ((j / nb) < 2 ? t[0] * t[1] : t[0] * t[0]);
+        double v = amp * (baseline(a, t, j) + a.sd[j] * (double)y[i]) + t[5] * a.shot[j];
+        if (a.ref) v -= a.ref[j];
+        if (a.sigma) v /= a.sigma[j];
+        out[i] = (float)v;
+    }
+}
+
+// training targets: derived curves u of native template slots [n][10][40] (FP64, unit
+// amplitude, no shot noise), y = (u - baseline) / sd
+__global__ void k_targets(const double* __restrict__ theta, const double* __restrict__ native, int n,
+                          float* __restrict__ y, MapArgs a) {
+    constexpr int nb = kNout / 8;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * kNout; i += gridDim.x * blockDim.x) {
+        const int r = i / kNout, j = i % kNout, c = j / nb, b = j % nb;
+        const double* o = native + (size_t)r * 10 * nb;
+        double u;
+        if (c < 2) {
+            u = a.N[c][0] * o[1 * nb + b] + a.N[c][1] * o[2 * nb + b] + a.N[c][2] * o[3 * nb + b];
+        } else {
+            const int li = (c - 2) % 3;
+            const double mm = a.M[li][0] * o[7 * nb + b] + a.M[li][1] * o[8 * nb + b] + a.M[li][2] * o[9 * nb + b];
+            u = 0.5 * (o[(4 + li) * nb + b] + (c < 5 ? mm : -mm));
+        }
+        y[i] = (float)((u - baseline(a, theta + (size_t)r * kNin, j)) / a.sd[j]);
+    }
+}
+
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
@@ -262,7 +344,9 @@ struct lpp_surrogate_s {
     // offsets
     size_t w[kLayers], b[kLayers], mw[kLayers], vw[kLayers], mb[kLayers], vb[kLayers], dw[kLayers], db[kLayers];
     size_t w16[kLayers], w16t[kLayers], act[kLayers + 1], actt[kLayers], z[kLayers];
-    size_t g32[2], g16[2], g16t[2], loss;
+    size_t g32[2], g16[2], g16t[2], loss, xin;
+    bool has_map = false;
+    MapArgs map;
 };
 
 extern "C" lpp_status lpp_surrogate_create(int batch, lpp_surrogate_t* out) {
@@ -294,6 +378,7 @@ extern "C" lpp_status lpp_surrogate_create(int batch, lpp_surrogate_t* out) {
         s->g16t[i] = take((size_t)batch * kNout * 2);
     }
     s->loss = take(8);
+    s->xin = take((size_t)batch * kNin * 4);
     s->need = off;
     *out = s;
     return LPP_OK;
@@ -423,6 +508,71 @@ extern "C" lpp_status lpp_surrogate_infer(lpp_surrogate_t s, const float* x, int
             return LPP_ERR_CUDA;
     }
     return LPP_OK;
+}
+
+extern "C" lpp_status lpp_surrogate_set_map(lpp_surrogate_t s, const lpp_surrogate_map* m) {
+    if (!s || !m || !m->mu || !m->sd || !m->shot) return LPP_ERR_INVALID_ARG;
+    MapArgs a;
+    memset(&a, 0, sizeof(a));
+    for (int c = 0; c < kNin; ++c) {
+        if (!m->feed[c]) continue;
+        if (!(m->hi[c] > m->lo[c])) return LPP_ERR_INVALID_ARG;
+        const double sc = 2.0 / (m->hi[c] - m->lo[c]);
+        a.dscale[c] = sc;
+        a.dshift[c] = -1.0 - m->lo[c] * sc;
+        a.scale[c] = (float)a.dscale[c];
+        a.shift[c] = (float)a.dshift[c];
+    }
+    if (m->base) {
+        if (m->base_nodes < 2 || m->base_nodes > kMaxNodes) return LPP_ERR_INVALID_ARG;
+        for (int d = 0; d < 2; ++d)
+            if (m->base_in[d] < 0 || m->base_in[d] >= kNin || !m->feed[m->base_in[d]]) return LPP_ERR_INVALID_ARG;
+        a.base = m->base;
+        a.nodes = m->base_nodes;
+        a.base_in[0] = m->base_in[0];
+        a.base_in[1] = m->base_in[1];
+    }
+    a.mu = m->mu;
+    a.sd = m->sd;
+    a.shot = m->shot;
+    a.ref = m->ref;
+    a.sigma = m->sigma;
+    lpp::eb_matrices(a.N, a.M);
+    s->map = a;
+    s->has_map = true;
+    return LPP_OK;
+}
+
+extern "C" lpp_status lpp_surrogate_targets(lpp_surrogate_t s, const double* theta, const double* native, int n,
+                                            float* y, void* stream) {
+    if (!s || !s->has_map || n < 0 || (n > 0 && (!theta || !native || !y))) return LPP_ERR_INVALID_ARG;
+    if (n == 0) return LPP_OK;
+    const long long total = (long long)n * kNout;
+    const int blocks = (int)((total + 255) / 256 < 65535 * 8 ? (total + 255) / 256 : 65535 * 8);
+    k_targets<<<blocks, 256, 0, (cudaStream_t)stream>>>(theta, native, n, y, s->map);
+    return cudaGetLastError() == cudaSuccess ? LPP_OK : LPP_ERR_CUDA;
+}
+
+extern "C" lpp_status lpp_surrogate_encode(lpp_surrogate_t s, const double* theta, int n, float* x, void* stream) {
+    if (!s || !s->has_map || n < 0 || (n > 0 && (!theta || !x))) return LPP_ERR_INVALID_ARG;
+    if (n == 0) return LPP_OK;
+    k_encode<<<(n * kNin + 255) / 256, 256, 0, (cudaStream_t)stream>>>(theta, n, x, s->map);
+    return cudaGetLastError() == cudaSuccess ? LPP_OK : LPP_ERR_CUDA;
+}
+
+extern "C" lpp_status lpp_surrogate_predict(lpp_surrogate_t s, const double* theta, int n, float* out, void* stream) {
+    if (!s || !s->ws || !s->has_map || n < 0 || (n > 0 && (!theta || !out))) return LPP_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    float* x = (float*)(s->ws + s->xin);
+    for (int r0 = 0; r0 < n; r0 += s->batch) {
+        const int m = n - r0 < s->batch ? n - r0 : s->batch;
+        const double* th = theta + (size_t)r0 * kNin;
+        k_encode<<<(m * kNin + 255) / 256, 256, 0, st>>>(th, m, x, s->map);
+        float* y = out + (size_t)r0 * kNout;
+        if (forward(s, x, nullptr, m, false, y, st) != cudaSuccess) return LPP_ERR_CUDA;
+        k_decode<<<(m * kNout + 255) / 256, 256, 0, st>>>(th, m, y, y, s->map);
+    }
+    return cudaGetLastError() == cudaSuccess ? LPP_OK : LPP_ERR_CUDA;
 }
 
 // One Adam step on the minibatch rows idx[0..batch) of (x, y); the mean squared error of the

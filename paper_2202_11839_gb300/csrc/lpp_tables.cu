@@ -139,6 +139,17 @@ static double legendre_overlap(int m, int L, int l) {
     return 0.5 * (2 * l + 1) * s;
 }
 
+namespace lpp {
+// N[l][L] = (2l+1)/2 int Lm2_L L_l (l = 0, 2; L = 2, 4, 6), M[l][L] = (2l+1)/2 int Lm4_L L_l
+// (l = 0, 2, 4; L = 4, 6, 8): native associated-Legendre moments -> Legendre multipoles.
+void eb_matrices(double N[2][3], double M[3][3]) {
+    for (int li = 0; li < 2; ++li)
+        for (int j = 0; j < 3; ++j) N[li][j] = legendre_overlap(2, 2 + 2 * j, 2 * li);
+    for (int li = 0; li < 3; ++li)
+        for (int j = 0; j < 3; ++j) M[li][j] = legendre_overlap(4, 4 + 2 * j, 2 * li);
+}
+}  // namespace lpp
+
 extern "C" lpp_status lpp_derive_eb(const double* p, int n_bins, double* ge, double* ee, double* bb) {
     if (!p || n_bins <= 0 || !ge || !ee || !bb) return LPP_ERR_INVALID_ARG;
     const int crossL[3] = {2, 4, 6}, minusL[3] = {4, 6, 8};
@@ -157,6 +168,30 @@ extern "C" lpp_status lpp_derive_eb(const double* p, int n_bins, double* ge, dou
             const double pl = p[(plusSlot[li] * n_bins + b) * 2];
             ee[li * n_bins + b] = 0.5 * (pl + mm);
             bb[li * n_bins + b] = 0.5 * (pl - mm);
+        }
+    }
+    return LPP_OK;
+}
+
+extern "C" lpp_status lpp_gaussian_sigma(const double* p0, const double* k_edges, int n_bins, double volume,
+                                         double noise_g, double noise_e, double* sigma) {
+    if (!p0 || !k_edges || !sigma || n_bins < 1 || !(volume > 0.0) || noise_g < 0.0 || noise_e < 0.0)
+        return LPP_ERR_INVALID_ARG;
+    const double pi = 3.14159265358979323846;
+    const int ell[8] = {0, 2, 0, 2, 4, 0, 2, 4};
+    for (int b = 0; b < n_bins; ++b) {
+        const double k0 = k_edges[b], k1 = k_edges[b + 1];
+        if (!(k1 > k0) || k0 < 0.0) return LPP_ERR_INVALID_ARG;
+        const double nk = volume * (k1 * k1 * k1 - k0 * k0 * k0) / (6.0 * pi * pi);
+        const double gg = p0[b] + noise_g, ge = p0[n_bins + b];
+        const double ee = p0[2 * n_bins + b] + noise_e, bb = p0[3 * n_bins + b] + noise_e;
+        for (int c = 0; c < 8; ++c) {
+            const double f = 2 * ell[c] + 1;
+            double v;
+            if (c < 2) v = f * (gg * ee + ge * ge) / nk;
+            else if (c < 5) v = 2.0 * f * ee * ee / nk;
+            else v = 2.0 * f * bb * bb / nk;
+            sigma[c * n_bins + b] = sqrt(v);
         }
     }
     return LPP_OK;

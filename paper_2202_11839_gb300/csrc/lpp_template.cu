@@ -62,6 +62,12 @@ struct TemplateArgs {
     int nb;
     double shot_plus;
     SlotDesc slots[kSlots];
+    // optional derived curves gE_0,2, EE_0,2,4, BB_0,2,4 per shell, standardised as
+    // (value - ref) / sigma and stored FP32 [n][8][nb]
+    float* eb;
+    const double* eb_ref;
+    const double* eb_sigma;
+    double N[2][3], M[3][3];
 };
 
 __device__ __forceinline__ double bbks_shape(double k, double gam, double tilt) {
@@ -170,6 +176,28 @@ __global__ void __launch_bounds__(512, 1) k_template(TemplateArgs a) {
             if (lane == 0) a.out[((size_t)t * kSlots + s) * a.nb + bb] = den > 0.0 ? num / den + add : 0.0;
         }
         __syncthreads();
+    }
+    if (a.eb) {
+        // Legendre multipoles of P_gE = Re P_gd and P_EE/BB = (P_+ +- P_-)/2 (Sec. 2.4, Eq. relation_pm_EB)
+        const double* o = a.out + (size_t)t * kSlots * a.nb;
+        for (int bb = tid; bb < a.nb; bb += nthr) {
+            double v[8];
+            for (int li = 0; li < 2; ++li)
+                v[li] = a.N[li][0] * o[1 * a.nb + bb] + a.N[li][1] * o[2 * a.nb + bb] + a.N[li][2] * o[3 * a.nb + bb];
+            for (int li = 0; li < 3; ++li) {
+                const double mm = a.M[li][0] * o[7 * a.nb + bb] + a.M[li][1] * o[8 * a.nb + bb] +
+                                  a.M[li][2] * o[9 * a.nb + bb];
+                const double pl = o[(4 + li) * a.nb + bb];
+                v[2 + li] = 0.5 * (pl + mm);
+                v[5 + li] = 0.5 * (pl - mm);
+            }
+            for (int c = 0; c < 8; ++c) {
+                const int i = c * a.nb + bb;
+                const double ref = a.eb_ref ? a.eb_ref[i] : 0.0;
+                const double sg = a.eb_sigma ? a.eb_sigma[i] : 1.0;
+                a.eb[(size_t)t * 8 * a.nb + i] = (float)((v[c] - ref) / sg);
+            }
+        }
     }
 }
 
@@ -425,8 +453,22 @@ extern "C" lpp_status lpp_template_set_workspace(lpp_template_t t, void* dev, si
     return LPP_OK;
 }
 
+static lpp_status convolve(lpp_template_t t, const double* params, int n_templates, double* out, float* eb,
+                           const double* eb_ref, const double* eb_sigma, void* stream);
+
 extern "C" lpp_status lpp_convolve_template(lpp_template_t t, const double* params, int n_templates, double* out,
                                             void* stream) {
+    return convolve(t, params, n_templates, out, nullptr, nullptr, nullptr, stream);
+}
+
+extern "C" lpp_status lpp_convolve_template_eb(lpp_template_t t, const double* params, int n_templates, double* out,
+                                               float* eb, const double* eb_ref, const double* eb_sigma, void* stream) {
+    if (n_templates > 0 && !eb) return LPP_ERR_INVALID_ARG;
+    return convolve(t, params, n_templates, out, eb, eb_ref, eb_sigma, stream);
+}
+
+static lpp_status convolve(lpp_template_t t, const double* params, int n_templates, double* out, float* eb,
+                           const double* eb_ref, const double* eb_sigma, void* stream) {
     if (!t || (n_templates > 0 && (!params || !out)) || n_templates < 0) return LPP_ERR_INVALID_ARG;
     if (!t->ready) return LPP_ERR_NOT_READY;
     if (n_templates == 0) return LPP_OK;
@@ -451,6 +493,10 @@ extern "C" lpp_status lpp_convolve_template(lpp_template_t t, const double* para
     a.nb = t->nb;
     a.shot_plus = t->shot_plus;
     for (int s = 0; s < kSlots; ++s) a.slots[s] = t->slots[s];
+    a.eb = eb;
+    a.eb_ref = eb_ref;
+    a.eb_sigma = eb_sigma;
+    lpp::eb_matrices(a.N, a.M);
     const size_t smem = (size_t)kNfft * 16 + (size_t)3 * kNfft * 8 + (size_t)kNin * 8;
     cudaFuncSetAttribute(k_template, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_template<<<n_templates, 512, smem, (cudaStream_t)stream>>>(a);

@@ -78,6 +78,8 @@ EXPORTS = {
     "lpp_template_workspace_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "lpp_template_set_workspace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "lpp_convolve_template": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "lpp_convolve_template_eb": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.c_void_p, C.c_void_p]),
     "lpp_surrogate_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p)]),
     "lpp_surrogate_destroy": (None, [C.c_void_p]),
     "lpp_surrogate_workspace_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
@@ -88,6 +90,12 @@ EXPORTS = {
     "lpp_surrogate_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_float),
                                           C.POINTER(C.c_double), C.c_void_p]),
     "lpp_surrogate_infer": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "lpp_gaussian_sigma": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double,
+                                     C.c_void_p]),
+    "lpp_surrogate_set_map": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lpp_surrogate_targets": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "lpp_surrogate_encode": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "lpp_surrogate_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "lpp_derive_eb": (C.c_int, [C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                 C.POINTER(C.c_double)]),
     "lpp_plan_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
@@ -295,6 +303,8 @@ class Template:
         q = np.ascontiguousarray(q_table, dtype=np.float64)
         sv = np.ascontiguousarray(s, dtype=np.float64)
         e = np.ascontiguousarray(k_edges, dtype=np.float64)
+        self.k_edges = e
+        self.shot_plus = float(shot_plus)
         self.nb = len(e) - 1
         dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
         h = C.c_void_p()
@@ -320,6 +330,18 @@ class Template:
                                                         C.c_void_p(out.data_ptr()),
                                                         C.c_void_p(self.stream.cuda_stream)))
         return out
+
+    def derived(self, params, ref=None, sigma=None, out=None):
+        """Native slots [n, 10, nb] (float64) and standardised derived curves [n, 8 * nb] (float32)."""
+        import torch
+        n = int(params.shape[0])
+        if out is None:
+            out = torch.empty((n, LPP_N_MOMENTS, self.nb), dtype=torch.float64, device=params.device)
+        eb = torch.empty((n, 8 * self.nb), dtype=torch.float32, device=params.device)
+        ptr = lambda a: C.c_void_p(a.data_ptr()) if a is not None else None
+        _check(self.lib, self.lib.lpp_convolve_template_eb(self.h, ptr(params), n, ptr(out), ptr(eb), ptr(ref),
+                                                           ptr(sigma), C.c_void_p(self.stream.cuda_stream)))
+        return out, eb
 
     def close(self):
         if getattr(self, "h", None):
@@ -351,6 +373,12 @@ def unflatten_params(flat):
         p += fo
         out.append((w, b))
     return out
+
+
+class SurrogateMap(C.Structure):
+    _fields_ = [("lo", C.c_double * 6), ("hi", C.c_double * 6), ("feed", C.c_int * 6), ("mu", C.c_void_p),
+                ("sd", C.c_void_p), ("shot", C.c_void_p), ("ref", C.c_void_p), ("sigma", C.c_void_p),
+                ("base", C.c_void_p), ("base_nodes", C.c_int), ("base_in", C.c_int * 2)]
 
 
 class Surrogate:
@@ -409,6 +437,49 @@ class Surrogate:
                                                       C.c_void_p(self.stream.cuda_stream)))
         return out
 
+    def set_map(self, lo, hi, feed, mu, sd, shot, ref=None, sigma=None, base=None, base_nodes=0, base_in=(3, 4)):
+        """Parameter box, fed inputs and the output map (mu, sd, shot, ref, sigma, base: FP64
+        CUDA tensors, kept alive by this object)."""
+        m = SurrogateMap()
+        for c in range(6):
+            m.lo[c], m.hi[c], m.feed[c] = float(lo[c]), float(hi[c]), int(feed[c])
+        ptr = lambda a: a.data_ptr() if a is not None else None
+        m.mu, m.sd, m.shot, m.ref, m.sigma = ptr(mu), ptr(sd), ptr(shot), ptr(ref), ptr(sigma)
+        m.base, m.base_nodes = ptr(base), int(base_nodes)
+        m.base_in[0], m.base_in[1] = int(base_in[0]), int(base_in[1])
+        self._map_refs = (mu, sd, shot, ref, sigma, base)
+        _check(self.lib, self.lib.lpp_surrogate_set_map(self.h, C.byref(m)))
+
+    def targets(self, params, native, out=None):
+        import torch
+        n = int(params.shape[0])
+        if out is None:
+            out = torch.empty((n, 320), dtype=torch.float32, device=params.device)
+        _check(self.lib, self.lib.lpp_surrogate_targets(self.h, C.c_void_p(params.data_ptr()),
+                                                        C.c_void_p(native.data_ptr()), n, C.c_void_p(out.data_ptr()),
+                                                        C.c_void_p(self.stream.cuda_stream)))
+        return out
+
+    def encode(self, params, out=None):
+        import torch
+        n = int(params.shape[0])
+        if out is None:
+            out = torch.empty((n, 6), dtype=torch.float32, device=params.device)
+        _check(self.lib, self.lib.lpp_surrogate_encode(self.h, C.c_void_p(params.data_ptr()), n,
+                                                       C.c_void_p(out.data_ptr()), C.c_void_p(self.stream.cuda_stream)))
+        return out
+
+    def predict(self, params, out=None):
+        """Emulated standardised derived curves [n, 320] (FP32) for FP64 params [n, 6]."""
+        import torch
+        n = int(params.shape[0])
+        if out is None:
+            out = torch.empty((n, 320), dtype=torch.float32, device=params.device)
+        _check(self.lib, self.lib.lpp_surrogate_predict(self.h, C.c_void_p(params.data_ptr()), n,
+                                                        C.c_void_p(out.data_ptr()),
+                                                        C.c_void_p(self.stream.cuda_stream)))
+        return out
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.lpp_surrogate_destroy(self.h)
@@ -432,3 +503,16 @@ def derive_eb(p: np.ndarray):
     dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
     _check(lib, lib.lpp_derive_eb(dp(pr), nb, dp(ge), dp(ee), dp(bb)))
     return ge, ee, bb
+
+
+def gaussian_sigma(p0: np.ndarray, k_edges, volume: float, noise_g: float, noise_e: float) -> np.ndarray:
+    """Gaussian error bars [8, nb] of the derived multipoles from the monopoles p0 [4, nb]
+    (P_gg, P_gE, P_EE, P_BB without shot noise) (lpp_gaussian_sigma)."""
+    lib = load_library()
+    p = np.ascontiguousarray(p0, dtype=np.float64).reshape(4, -1)
+    nb = p.shape[1]
+    k = np.ascontiguousarray(k_edges, dtype=np.float64)
+    out = np.zeros((8, nb))
+    dp = lambda a: a.ctypes.data_as(C.c_void_p)
+    _check(lib, lib.lpp_gaussian_sigma(dp(p), dp(k), nb, float(volume), float(noise_g), float(noise_e), dp(out)))
+    return out

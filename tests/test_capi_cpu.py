@@ -123,3 +123,17 @@ def test_template_tables_build_on_host():
     lib.lpp_template_destroy(h)
     bad = s[::-1].copy()
     assert lib.lpp_template_create(dp(q), dp(bad), s.size, dp(e), 10, 0.0, C.byref(h)) == L.LPP_ERR_INVALID_ARG
+
+
+def test_gaussian_sigma_matches_oracle():
+    from oracle import template_oracle as T
+    L, _ = _lib()
+    rng = np.random.default_rng(3)
+    nb = 12
+    edges = np.linspace(0.01, 0.2, nb + 1)
+    p0 = rng.uniform(100.0, 20000.0, (4, nb))
+    got = L.gaussian_sigma(p0, edges, 5.1e9, 3373.0, 210.0)
+    want = T.gaussian_sigma(p0, edges, 5.1e9, 3373.0, 210.0)
+    np.testing.assert_allclose(got, want, rtol=1e-13)
+    with pytest.raises(L.LppError):
+        L.gaussian_sigma(p0, edges[::-1], 5.1e9, 3373.0, 210.0)

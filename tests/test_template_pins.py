@@ -96,3 +96,31 @@ def test_round_trip_and_unit_window():
         want = T.bin_average(model[kind].get(L, 0.0) * pk, edges)
         scale = np.abs(T.bin_average(model[kind][min(model[kind])] * pk, edges))
         assert np.max(np.abs(tmpl[i] - want) / scale) < 2e-3, (kind, L, np.max(np.abs(tmpl[i] - want) / scale))
+
+
+def test_gaussian_sigma_against_monte_carlo():
+    """The Gaussian error bars against the scatter of the multipole estimator over Gaussian
+    realisations: N_k / 2 independent complex modes per shell, uniform in mu (isotropic
+    power; the mu of the modes are fixed by the grid, the same in every realisation),
+    P_ab^(l) = (2l+1) <Re(d_a d_b*) L_l(mu)>."""
+    from scipy.special import eval_legendre
+    rng = np.random.default_rng(12)
+    n_k, reals = 400, 20000
+    k1 = 0.05
+    volume = n_k * 6.0 * math.pi ** 2 / k1 ** 3
+    pgg, pee, pbb, pge = 3.0, 2.0, 0.7, 0.9
+    chol = np.linalg.cholesky(np.array([[pgg, pge], [pge, pee]]))
+    m = n_k // 2
+    z = (rng.standard_normal((reals, m, 3)) + 1j * rng.standard_normal((reals, m, 3))) / math.sqrt(2.0)
+    dg = chol[0, 0] * z[..., 0]
+    de = chol[1, 0] * z[..., 0] + chol[1, 1] * z[..., 1]
+    db = math.sqrt(pbb) * z[..., 2]
+    mu = -1.0 + (np.arange(m) + 0.5) * (2.0 / m)
+    noise_e = 0.5
+    p0 = np.array([[pgg], [pge], [pee - noise_e], [pbb - noise_e]])
+    want = T.gaussian_sigma(p0, np.array([0.0, k1]), volume, 0.0, noise_e)[:, 0]
+    pairs = [(dg, de), (dg, de), (de, de), (de, de), (de, de), (db, db), (db, db), (db, db)]
+    for c, (ell, (a, b)) in enumerate(zip([0, 2, 0, 2, 4, 0, 2, 4], pairs)):
+        est = (2 * ell + 1) * np.mean((a * np.conj(b)).real * eval_legendre(ell, mu), axis=1)
+        got = est.std()
+        assert abs(got / want[c] - 1.0) < 0.04, (c, got, want[c])
