@@ -164,6 +164,33 @@ lpp_status lpp_multipoles(lpp_plan_t plan, lpp_result* result);
 lpp_status lpp_window_Q(lpp_plan_t plan, int n_s, const double* s_edges, double* q, double* s_mean,
                         long long* n_points, double* norm);
 
+/* ------------------------------------------------------------------ batches of catalogues
+ * Many catalogues (mocks) through a set of plans in one launch.  plans[0..n_plans) are
+ * distinct plans with their workspaces set (they may differ in grid size and bins); mock j
+ * runs on plans[plan_of[j]] with the device catalogues shapes[j] (shape kind GAMMA12 or
+ * TENSOR6) and randoms[j] (randoms == NULL or randoms[j].count == 0: periodic box).  Mocks
+ * of one plan run in order on a stream of the batch, different plans concurrently.  With
+ * use_graph != 0 the whole batch is captured once into a CUDA graph at creation and every
+ * lpp_batch_launch is one graph launch; otherwise each launch enqueues the kernels anew.
+ * The catalogue buffers are borrowed: they must stay valid, with the same addresses and
+ * counts, for the batch's lifetime (their contents may change between launches).  Host
+ * memory for the per-mock sums is pinned and owned by the batch.  While a batch is in
+ * flight its plans must not be used otherwise.  Errors: LPP_ERR_INVALID_ARG (bad indices,
+ * counts above a plan's capacity, host catalogues, a plan listed twice), LPP_ERR_NOT_READY
+ * (a plan without workspace), LPP_ERR_CUDA (stream, event, pinned memory or capture). */
+typedef struct lpp_batch_s* lpp_batch_t;
+
+lpp_status lpp_batch_create(lpp_plan_t* plans, int n_plans, const int* plan_of, const lpp_particles* shapes,
+                            const lpp_particles* randoms, int n_mocks, int use_graph, lpp_batch_t* batch);
+void lpp_batch_destroy(lpp_batch_t batch);
+/* Runs every mock, ordered after the work already on `stream` and before later work on it;
+ * asynchronous. */
+lpp_status lpp_batch_launch(lpp_batch_t batch, void* stream);
+/* Waits for the last launch and fills results[n_mocks] (caller-owned arrays as for
+ * lpp_multipoles); returns the first failing mock's status (e.g. LPP_ERR_DOMAIN). */
+lpp_status lpp_batch_results(lpp_batch_t batch, lpp_result* results);
+const char* lpp_batch_last_error(lpp_batch_t batch);
+
 /* ------------------------------------------------------------------ templates
  * Window-convolved theory templates (Sec. 3.2, Eqs. window_convolution_X_hankel and
  * def_of_Q_llp; Appendix D): for every parameter set (A, b_g, sigma_8, tilt, Gamma,

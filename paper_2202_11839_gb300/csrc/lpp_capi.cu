@@ -465,13 +465,16 @@ extern "C" lpp_status lpp_clear(lpp_plan_t plan, int role) {
 }
 
 // ------------------------------------------------------------------ estimate
+// Steps 0-3 of an estimate on the plan's stream, then asynchronous copies of the shell sums,
+// the scalar sums and the error flag to host_out [out_rows][nb][2], host_sums [SUM_COUNT] and
+// *host_err (pinned memory for a copy that overlaps; the caller synchronises).  No host
+// synchronisation, so the whole sequence can be captured into a CUDA graph.
 template <typename T>
-static lpp_status run(lpp_plan_t plan, lpp_result* res) {
+static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, int* host_err) {
     const int n = plan->n, nb = plan->nb;
     const size_t n3 = (size_t)n * n * n;
     cudaStream_t st = plan->stream;
     Timer* tm = plan->timer.enabled ? &plan->timer : nullptr;
-    if (tm) tm->reset();
     double* sums = (double*)(plan->ws + plan->off_sums);
     int* err = (int*)(plan->ws + plan->off_err);
     double* out = (double*)(plan->ws + plan->off_out);
@@ -706,14 +709,18 @@ static lpp_status run(lpp_plan_t plan, lpp_result* res) {
     }
 
     // 4. results to the host
-    std::vector<double> h_out((size_t)plan->out_rows * nb * 2);
-    double h_sums[SUM_COUNT];
-    int h_err = 0;
-    LPP_CUDA(cudaMemcpyAsync(h_out.data(), out, h_out.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-    LPP_CUDA(cudaMemcpyAsync(h_sums, sums, sizeof(h_sums), cudaMemcpyDeviceToHost, st));
-    LPP_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    LPP_CUDA(cudaStreamSynchronize(st));
-    if (tm) tm->collect();
+    LPP_CUDA(cudaMemcpyAsync(host_out, out, (size_t)plan->out_rows * nb * 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                             st));
+    LPP_CUDA(cudaMemcpyAsync(host_sums, sums, SUM_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LPP_CUDA(cudaMemcpyAsync(host_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    return LPP_OK;
+}
+
+// Step 5 on the host from the copied sums (FP64): normalisation, shot noise, moment slots.
+static lpp_status finish(lpp_plan_t plan, const double* h_out, const double* h_sums, int h_err, bool has_rand,
+                         lpp_result* res) {
+    const int nb = plan->nb;
+    const int n_ch = (int)plan->channels.size();
     if (h_err) {
         std::string msg = "particle outside the domain:";
         if (h_err & ERRF_DOMAIN) msg += " outside the box";
@@ -783,12 +790,26 @@ static lpp_status run(lpp_plan_t plan, lpp_result* res) {
     return LPP_OK;
 }
 
+static lpp_status enqueue_any(lpp_plan_t plan, double* host_out, double* host_sums, int* host_err) {
+    return plan->fp64 ? enqueue<double>(plan, host_out, host_sums, host_err)
+                      : enqueue<float>(plan, host_out, host_sums, host_err);
+}
+
 extern "C" lpp_status lpp_multipoles(lpp_plan_t plan, lpp_result* res) {
     if (!plan || !res) return LPP_ERR_INVALID_ARG;
     if (!plan->ws || !plan->tables_ready) return fail(plan, LPP_ERR_NOT_READY, "workspace not set");
     if (!plan->cat[LPP_SHAPES].set) return fail(plan, LPP_ERR_NOT_READY, "no shape catalogue assigned");
     plan->err.clear();
-    return plan->fp64 ? run<double>(plan, res) : run<float>(plan, res);
+    Timer* tm = plan->timer.enabled ? &plan->timer : nullptr;
+    if (tm) tm->reset();
+    std::vector<double> h_out((size_t)plan->out_rows * plan->nb * 2);
+    double h_sums[SUM_COUNT];
+    int h_err = 0;
+    lpp_status s = enqueue_any(plan, h_out.data(), h_sums, &h_err);
+    if (s != LPP_OK) return s;
+    LPP_CUDA(cudaStreamSynchronize(plan->stream));
+    if (tm) tm->collect();
+    return finish(plan, h_out.data(), h_sums, h_err, plan->cat[LPP_RANDOMS].set, res);
 }
 
 // ------------------------------------------------------------------ window multipoles
@@ -982,3 +1003,195 @@ extern "C" const char* lpp_status_string(lpp_status s) {
 }
 
 extern "C" const char* lpp_plan_last_error(lpp_plan_t plan) { return plan ? plan->err.c_str() : ""; }
+
+// ------------------------------------------------------------------ batches of catalogues
+struct lpp_batch_s {
+    std::vector<lpp_plan_t> plans;
+    std::vector<int> plan_of;
+    std::vector<Catalogue> shapes, randoms;
+    std::vector<cudaStream_t> streams;       // one per plan (the batch's own)
+    std::vector<cudaEvent_t> done;           // one per plan
+    cudaEvent_t start = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;   // ordering against the caller's stream
+    cudaStream_t root = nullptr;
+    double* h_out = nullptr;                 // pinned: per mock [out_rows][nb][2]
+    double* h_sums = nullptr;                // pinned: per mock [SUM_COUNT]
+    int* h_err = nullptr;                    // pinned: per mock
+    std::vector<size_t> out_off;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool launched = false;
+    std::string err;
+};
+
+static lpp_status batch_fail(lpp_batch_t b, lpp_status s, const std::string& m) {
+    if (b) b->err = m;
+    return s;
+}
+
+#define LPP_BCUDA(call)                                                                   \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) return batch_fail(b, LPP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// All mocks, each on its plan's batch stream (mocks of one plan in order, plans concurrently).
+static lpp_status batch_enqueue(lpp_batch_t b, cudaStream_t root) {
+    LPP_BCUDA(cudaEventRecord(b->start, root));
+    for (size_t p = 0; p < b->plans.size(); ++p) LPP_BCUDA(cudaStreamWaitEvent(b->streams[p], b->start, 0));
+    for (size_t j = 0; j < b->plan_of.size(); ++j) {
+        const int pi = b->plan_of[j];
+        lpp_plan_t plan = b->plans[pi];
+        const cudaStream_t keep = plan->stream;
+        const bool timing = plan->timer.enabled;
+        plan->stream = b->streams[pi];
+        plan->timer.enabled = false;
+        plan->cat[LPP_SHAPES] = b->shapes[j];
+        plan->cat[LPP_DENSITY] = Catalogue();
+        plan->cat[LPP_RANDOMS] = b->randoms[j];
+        const lpp_status s = enqueue_any(plan, b->h_out + b->out_off[j], b->h_sums + j * SUM_COUNT, b->h_err + j);
+        plan->stream = keep;
+        plan->timer.enabled = timing;
+        if (s != LPP_OK) return batch_fail(b, s, "mock " + std::to_string(j) + ": " + plan->err);
+    }
+    for (size_t p = 0; p < b->plans.size(); ++p) {
+        LPP_BCUDA(cudaEventRecord(b->done[p], b->streams[p]));
+        LPP_BCUDA(cudaStreamWaitEvent(root, b->done[p], 0));
+    }
+    return LPP_OK;
+}
+
+extern "C" void lpp_batch_destroy(lpp_batch_t b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaStream_t s : b->streams) if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->done) if (e) cudaEventDestroy(e);
+    if (b->start) cudaEventDestroy(b->start);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->root) cudaStreamDestroy(b->root);
+    if (b->h_out) cudaFreeHost(b->h_out);
+    if (b->h_sums) cudaFreeHost(b->h_sums);
+    if (b->h_err) cudaFreeHost(b->h_err);
+    delete b;
+}
+
+static bool catalogue_of(lpp_plan_t plan, int role, const lpp_particles* p, Catalogue* c) {
+    const long long cap = role == LPP_SHAPES ? plan->d.max_shapes : plan->d.max_randoms;
+    if (p->count < 0 || p->count > cap || p->on_host) return false;
+    if (p->count > 0 && !p->pos) return false;
+    const int sk = role == LPP_SHAPES ? p->shape_kind : LPP_SHAPE_NONE;
+    if (role == LPP_SHAPES && (sk != LPP_SHAPE_GAMMA12 && sk != LPP_SHAPE_TENSOR6)) return false;
+    if (sk != LPP_SHAPE_NONE && p->count > 0 && !p->shape) return false;
+    c->set = true;
+    c->count = p->count;
+    c->shape_kind = sk;
+    c->pos = p->pos;
+    c->w = p->w;
+    c->nbar = role == LPP_RANDOMS ? p->nbar : nullptr;
+    c->shape = sk != LPP_SHAPE_NONE ? p->shape : nullptr;
+    return true;
+}
+
+extern "C" lpp_status lpp_batch_create(lpp_plan_t* plans, int n_plans, const int* plan_of, const lpp_particles* shapes,
+                                       const lpp_particles* randoms, int n_mocks, int use_graph, lpp_batch_t* out) {
+    if (!out || !plans || n_plans < 1 || !plan_of || !shapes || n_mocks < 1) return LPP_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int p = 0; p < n_plans; ++p) {
+        if (!plans[p]) return LPP_ERR_INVALID_ARG;
+        if (!plans[p]->ws || !plans[p]->tables_ready) return LPP_ERR_NOT_READY;
+        for (int q = 0; q < p; ++q) if (plans[q] == plans[p]) return LPP_ERR_INVALID_ARG;
+    }
+    lpp_batch_t b = new lpp_batch_s();
+    b->plans.assign(plans, plans + n_plans);
+    size_t total = 0;
+    for (int j = 0; j < n_mocks; ++j) {
+        const int pi = plan_of[j];
+        if (pi < 0 || pi >= n_plans) { lpp_batch_destroy(b); return LPP_ERR_INVALID_ARG; }
+        Catalogue cs, cr;
+        if (!catalogue_of(plans[pi], LPP_SHAPES, &shapes[j], &cs) ||
+            (randoms && randoms[j].count > 0 && !catalogue_of(plans[pi], LPP_RANDOMS, &randoms[j], &cr))) {
+            lpp_batch_destroy(b);
+            return LPP_ERR_INVALID_ARG;
+        }
+        b->plan_of.push_back(pi);
+        b->shapes.push_back(cs);
+        b->randoms.push_back(cr);
+        b->out_off.push_back(total);
+        total += (size_t)plans[pi]->out_rows * plans[pi]->nb * 2;
+    }
+    const lpp_status bad = LPP_ERR_CUDA;
+    if (cudaHostAlloc((void**)&b->h_out, total * sizeof(double), cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void**)&b->h_sums, (size_t)n_mocks * SUM_COUNT * sizeof(double), cudaHostAllocDefault) !=
+            cudaSuccess ||
+        cudaHostAlloc((void**)&b->h_err, (size_t)n_mocks * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+        lpp_batch_destroy(b);
+        return bad;
+    }
+    b->streams.resize(n_plans, nullptr);
+    b->done.resize(n_plans, nullptr);
+    bool ok = cudaStreamCreateWithFlags(&b->root, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->start, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) == cudaSuccess;
+    for (int p = 0; ok && p < n_plans; ++p)
+        ok = cudaStreamCreateWithFlags(&b->streams[p], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->done[p], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) { lpp_batch_destroy(b); return bad; }
+    if (use_graph) {
+        if (cudaStreamBeginCapture(b->root, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            lpp_batch_destroy(b);
+            return bad;
+        }
+        const lpp_status s = batch_enqueue(b, b->root);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(b->root, &g);
+        if (s != LPP_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            lpp_batch_destroy(b);
+            return s != LPP_OK ? s : bad;
+        }
+        b->graph = g;
+        if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) { lpp_batch_destroy(b); return bad; }
+    }
+    *out = b;
+    return LPP_OK;
+}
+
+extern "C" lpp_status lpp_batch_launch(lpp_batch_t b, void* stream) {
+    if (!b) return LPP_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    // order after the caller's stream, run on the batch's root stream
+    LPP_BCUDA(cudaEventRecord(b->ev_in, st));
+    LPP_BCUDA(cudaStreamWaitEvent(b->root, b->ev_in, 0));
+    if (b->exec) {
+        LPP_BCUDA(cudaGraphLaunch(b->exec, b->root));
+    } else {
+        const lpp_status s = batch_enqueue(b, b->root);
+        if (s != LPP_OK) return s;
+    }
+    LPP_BCUDA(cudaEventRecord(b->ev_out, b->root));
+    LPP_BCUDA(cudaStreamWaitEvent(st, b->ev_out, 0));
+    b->launched = true;
+    return LPP_OK;
+}
+
+extern "C" lpp_status lpp_batch_results(lpp_batch_t b, lpp_result* results) {
+    if (!b || !results) return LPP_ERR_INVALID_ARG;
+    if (!b->launched) return batch_fail(b, LPP_ERR_NOT_READY, "batch not launched");
+    LPP_BCUDA(cudaStreamSynchronize(b->root));
+    lpp_status first = LPP_OK;
+    for (size_t j = 0; j < b->plan_of.size(); ++j) {
+        lpp_plan_t plan = b->plans[b->plan_of[j]];
+        const lpp_status s = finish(plan, b->h_out + b->out_off[j], b->h_sums + j * SUM_COUNT, b->h_err[j],
+                                    b->randoms[j].set, &results[j]);
+        if (s != LPP_OK && first == LPP_OK) {
+            first = s;
+            b->err = "mock " + std::to_string(j) + ": " + plan->err;
+        }
+    }
+    return first;
+}
+
+extern "C" const char* lpp_batch_last_error(lpp_batch_t b) { return b ? b->err.c_str() : "null batch"; }

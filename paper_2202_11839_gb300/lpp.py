@@ -62,6 +62,12 @@ class Result(C.Structure):
 
 EXPORTS = {
     "lpp_plan_create": (C.c_int, [C.POINTER(PlanDesc), C.POINTER(C.c_void_p)]),
+    "lpp_batch_create": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                                   C.POINTER(C.c_void_p)]),
+    "lpp_batch_destroy": (None, [C.c_void_p]),
+    "lpp_batch_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lpp_batch_results": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lpp_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "lpp_plan_destroy": (None, [C.c_void_p]),
     "lpp_plan_workspace_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "lpp_plan_set_workspace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
@@ -268,6 +274,15 @@ class Plan:
         _check(self.lib, self.lib.lpp_multipoles(self.h, C.byref(r)), self.h)
         return Estimate(p[..., 0] + 1j * p[..., 1], raw[..., 0] + 1j * raw[..., 1], km, nm, r.norm_auto,
                         r.norm_cross, r.norm_dd, r.shot_plus, r.shot_dd, r.alpha)
+
+    def particles(self, role: int, pos, w=None, nbar=None, shape=None, shape_kind: int = LPP_SHAPE_NONE):
+        """A device catalogue descriptor for lpp_batch_create (tensors are not copied)."""
+        for a in (pos, w, nbar, shape):
+            if a is not None and (not hasattr(a, "data_ptr") or not a.is_cuda or a.dtype != self.tdtype
+                                  or not a.is_contiguous()):
+                raise ValueError("batch catalogues must be contiguous CUDA tensors of the plan precision")
+        count = int(pos.shape[-1]) if pos is not None else 0
+        return Particles(_ptr(pos), _ptr(w), _ptr(nbar), _ptr(shape), count, shape_kind, 0)
 
     def window_q(self, s_edges):
         """Window multipoles Q_l(s), l = 0..8 even, from the assigned randoms: (q[5, nb], s_mean, n_points, I)."""
@@ -516,3 +531,67 @@ def gaussian_sigma(p0: np.ndarray, k_edges, volume: float, noise_g: float, noise
     dp = lambda a: a.ctypes.data_as(C.c_void_p)
     _check(lib, lib.lpp_gaussian_sigma(dp(p), dp(k), nb, float(volume), float(noise_g), float(noise_e), dp(out)))
     return out
+
+
+class Batch:
+    """Many catalogues through a set of plans in one launch (lpp_batch_*), optionally one CUDA graph."""
+
+    def __init__(self, plans, plan_of, shapes, randoms=None, use_graph: bool = True, keep=None):
+        self.lib = load_library()
+        self.plans = list(plans)
+        self.plan_of = list(plan_of)
+        self._keep = keep                 # the tensors behind the descriptors
+        n = len(self.plan_of)
+        ph = (C.c_void_p * len(self.plans))(*[p.h.value for p in self.plans])
+        po = (C.c_int * n)(*self.plan_of)
+        sh = (Particles * n)(*shapes)
+        rd = (Particles * n)(*randoms) if randoms is not None else None
+        h = C.c_void_p()
+        st = self.lib.lpp_batch_create(ph, len(self.plans), po, sh, rd, n, int(use_graph), C.byref(h))
+        if st != LPP_OK:
+            raise LppError(st, self.lib.lpp_status_string(st).decode())
+        self.h = h
+
+    def _check(self, st):
+        if st != LPP_OK:
+            raise LppError(st, self.lib.lpp_status_string(st).decode() + ": " +
+                           self.lib.lpp_batch_last_error(self.h).decode())
+
+    def launch(self, stream=None):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self._check(self.lib.lpp_batch_launch(self.h, C.c_void_p(s.cuda_stream)))
+
+    def results(self):
+        n = len(self.plan_of)
+        bufs = []
+        rs = (Result * n)()
+        for j in range(n):
+            nb = self.plans[self.plan_of[j]].nb
+            p = np.zeros((LPP_N_MOMENTS, nb, 2))
+            raw = np.zeros((LPP_N_MOMENTS, nb, 2))
+            km = np.zeros(nb)
+            nm = np.zeros(nb, dtype=np.int64)
+            rs[j].p = p.ctypes.data_as(C.POINTER(C.c_double))
+            rs[j].raw = raw.ctypes.data_as(C.POINTER(C.c_double))
+            rs[j].k_mean = km.ctypes.data_as(C.POINTER(C.c_double))
+            rs[j].n_modes = nm.ctypes.data_as(C.POINTER(C.c_longlong))
+            bufs.append((p, raw, km, nm))
+        self._check(self.lib.lpp_batch_results(self.h, rs))
+        out = []
+        for j, (p, raw, km, nm) in enumerate(bufs):
+            r = rs[j]
+            out.append(Estimate(p[..., 0] + 1j * p[..., 1], raw[..., 0] + 1j * raw[..., 1], km, nm, r.norm_auto,
+                                r.norm_cross, r.norm_dd, r.shot_plus, r.shot_dd, r.alpha))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lpp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
