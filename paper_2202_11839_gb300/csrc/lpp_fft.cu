@@ -55,24 +55,41 @@ __global__ void __launch_bounds__(PassShape<LOGN>::THREADS, sizeof(T) == 4 ? 2 :
         cs = 1;
     }
     for (int i = tid; i < N; i += S::THREADS) tw[i] = twg[i];
-#pragma unroll
-    for (int k = 0; k < S::PER; ++k) {
-        const int idx = tid + k * S::THREADS;
-        int e, c;
-        if (MODE == 0) { e = idx & (N - 1); c = idx >> LOGN; }
-        else { c = idx & (W - 1); e = idx >> S::LOGW; }
-        tile[e * LD + c] = base[e * es + c * cs];
-    }
-    __syncthreads();
     constexpr int WC = W / S::IPT;
-    fft_columns<T, LOGN, INV, S::IPT>(tile, LD, tid & (WC - 1), WC, tid >> ilog2(WC), tw);
+    if constexpr (MODE == 0) {
 #pragma unroll
-    for (int k = 0; k < S::PER; ++k) {
-        const int idx = tid + k * S::THREADS;
-        int e, c;
-        if (MODE == 0) { e = idx & (N - 1); c = idx >> LOGN; }
-        else { c = idx & (W - 1); e = idx >> S::LOGW; }
-        if (kept(e, N, g.nk_pos, g.nk_neg)) base[e * es + c * cs] = tile[e * LD + c];
+        for (int k = 0; k < S::PER; ++k) {
+            const int idx = tid + k * S::THREADS;
+            const int e = idx & (N - 1), c = idx >> LOGN;
+            tile[e * LD + c] = base[e * es + c * cs];
+        }
+        __syncthreads();
+        fft_columns<T, LOGN, INV, S::IPT, LD, WC>(tile, tid & (WC - 1), tid >> ilog2(WC), tw);
+#pragma unroll
+        for (int k = 0; k < S::PER; ++k) {
+            const int idx = tid + k * S::THREADS;
+            const int e = idx & (N - 1), c = idx >> LOGN;
+            if (kept(e, N, g.nk_pos, g.nk_neg)) base[e * es + c * cs] = tile[e * LD + c];
+        }
+    } else {
+        // rows e0 + k ROWS of W consecutive x values: one base pointer, compile-time strides
+        constexpr int ROWS = S::THREADS / W;
+        constexpr unsigned ES = MODE == 1 ? (unsigned)N : (unsigned)N * N;
+        const int c = tid & (W - 1), e0 = tid >> S::LOGW;
+        c2<T>* gp = base + (size_t)e0 * ES + c;
+        c2<T>* sp = tile + e0 * LD + c;
+        // z pencils: 64-bit strides; two batches of loads keep the live registers under the cap
+        constexpr int KB = (MODE == 2 && S::PER > 8) ? 8 : S::PER;
+#pragma unroll 1
+        for (int k0 = 0; k0 < S::PER; k0 += KB) {
+#pragma unroll
+            for (int k = k0; k < k0 + KB; ++k) sp[k * ROWS * LD] = gp[(size_t)k * ROWS * ES];
+        }
+        __syncthreads();
+        fft_columns<T, LOGN, INV, S::IPT, LD, WC>(tile, tid & (WC - 1), tid >> ilog2(WC), tw);
+#pragma unroll
+        for (int k = 0; k < S::PER; ++k)
+            if (kept(e0 + k * ROWS, N, g.nk_pos, g.nk_neg)) gp[(size_t)k * ROWS * ES] = sp[k * ROWS * LD];
     }
 }
 

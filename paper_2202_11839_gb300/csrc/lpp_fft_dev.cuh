@@ -57,60 +57,84 @@ __device__ __forceinline__ void dft8(c2<T>* v) {
 }
 
 // One Stockham stage of radix R on every pencil of the tile.  The thread owns pencils
-// c + k wc (k < IPT) and butterflies j = u + q N/8 (q < 8/R) of each.
-template <typename T, int N, int R, bool INV, int IPT>
-__device__ __forceinline__ void stockham_stage(c2<T>* tile, int ld, int c, int wc, int u, int Ns, const c2<T>* tw) {
+// c + k WC (k < IPT) and butterflies j = u + q N/8 (q < 8/R) of each.  The tile's row
+// pitch LD, the pencil stride WC and the stage's sub-transform length NS are compile-time,
+// so every shared-memory address is a per-thread base plus an immediate offset; the
+// twiddles of the thread's butterflies are loaded once and reused for all its pencils
+// (and skipped in the first stage, where they are all 1).
+template <typename T, int N, int R, bool INV, int IPT, int LD, int WC, int NS>
+__device__ __forceinline__ void stockham_stage(c2<T>* tile, int c, int u, const c2<T>* tw) {
     constexpr int Q = 8 / R;
+    c2<T> w[Q][R];
+    int dsto[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int j = u + q * (N / 8);
+        const int jm = j & (NS - 1);
+        if (NS > 1) {
+            const int step = jm * (N / (NS * R));
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                c2<T> t = tw[step * r];
+                if (INV) t.y = -t.y;
+                w[q][r] = t;
+            }
+        }
+        dsto[q] = ((j - jm) * R + jm) * LD + c;
+    }
     c2<T> v[IPT][8];
+    const c2<T>* src = tile + u * LD + c;
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
-        const int col = c + k * wc;
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            const int j = u + q * (N / 8);
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[k][q * R + r] = tile[(j + r * (N / R)) * ld + col];
+            for (int r = 0; r < R; ++r) v[k][q * R + r] = src[(q * (N / 8) + r * (N / R)) * LD + k * WC];
         }
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
-        const int col = c + k * wc;
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            const int j = u + q * (N / 8);
-            const int jm = j & (Ns - 1);
-            const int step = jm * (N / (Ns * R));
+            if (NS > 1) {
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                c2<T> w = tw[step * r];
-                if (INV) w.y = -w.y;
-                v[k][q * R + r] = cmul<T>(v[k][q * R + r], w);
+                for (int r = 1; r < R; ++r) v[k][q * R + r] = cmul<T>(v[k][q * R + r], w[q][r]);
             }
             if (R == 8) dft8<T, INV>(v[k] + q * R);
             else if (R == 4) dft4<T, INV>(v[k] + q * R);
             else dft2<T, INV>(v[k] + q * R);
-            const int idxD = (j - jm) * R + jm;
+            c2<T>* dst = tile + dsto[q] + k * WC;
 #pragma unroll
-            for (int r = 0; r < R; ++r) tile[(idxD + r * Ns) * ld + col] = v[k][q * R + r];
+            for (int r = 0; r < R; ++r) dst[r * NS * LD] = v[k][q * R + r];
         }
     }
     __syncthreads();
 }
 
-// Forward (or inverse, unnormalised) FFT of length N = 2^LOGN along every pencil.
-template <typename T, int LOGN, bool INV, int IPT>
-__device__ __forceinline__ void fft_columns(c2<T>* tile, int ld, int c, int wc, int u, const c2<T>* tw) {
-    // c = thread's first pencil, wc = W / IPT, u = butterfly slot (0 .. N/8 - 1)
+template <typename T, int N, bool INV, int IPT, int LD, int WC, int NS>
+__device__ __forceinline__ void radix8_stages(c2<T>* tile, int c, int u, const c2<T>* tw) {
+    if constexpr (NS < N) {
+        stockham_stage<T, N, 8, INV, IPT, LD, WC, NS>(tile, c, u, tw);
+        radix8_stages<T, N, INV, IPT, LD, WC, NS * 8>(tile, c, u, tw);
+    }
+}
+
+// Forward (or inverse, unnormalised) FFT of length N = 2^LOGN along every pencil: one
+// radix-2 or radix-4 stage when LOGN is not a multiple of 3, then radix-8 stages.
+template <typename T, int LOGN, bool INV, int IPT, int LD, int WC>
+__device__ __forceinline__ void fft_columns(c2<T>* tile, int c, int u, const c2<T>* tw) {
+    // c = thread's first pencil, WC = W / IPT, u = butterfly slot (0 .. N/8 - 1)
     constexpr int N = 1 << LOGN;
     constexpr int rem = LOGN % 3;
-    int Ns = 1;
-    if (rem == 1) { stockham_stage<T, N, 2, INV, IPT>(tile, ld, c, wc, u, Ns, tw); Ns = 2; }
-    if (rem == 2) { stockham_stage<T, N, 4, INV, IPT>(tile, ld, c, wc, u, Ns, tw); Ns = 4; }
-#pragma unroll
-    for (int s = 0; s < LOGN / 3; ++s) {
-        stockham_stage<T, N, 8, INV, IPT>(tile, ld, c, wc, u, Ns, tw);
-        Ns *= 8;
+    if constexpr (rem == 1) {
+        stockham_stage<T, N, 2, INV, IPT, LD, WC, 1>(tile, c, u, tw);
+        radix8_stages<T, N, INV, IPT, LD, WC, 2>(tile, c, u, tw);
+    } else if constexpr (rem == 2) {
+        stockham_stage<T, N, 4, INV, IPT, LD, WC, 1>(tile, c, u, tw);
+        radix8_stages<T, N, INV, IPT, LD, WC, 4>(tile, c, u, tw);
+    } else {
+        radix8_stages<T, N, INV, IPT, LD, WC, 1>(tile, c, u, tw);
     }
 }
 

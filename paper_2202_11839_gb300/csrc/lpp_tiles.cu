@@ -281,7 +281,7 @@ k_assign_xfft(FusedArgs<T> a) {
     }
     __syncthreads();
     constexpr int WC = W / S::IPT;
-    fft_columns<T, LOGN, false, S::IPT>(tile, LD, tid & (WC - 1), WC, tid >> ilog2(WC), tw);
+    fft_columns<T, LOGN, false, S::IPT, LD, WC>(tile, tid & (WC - 1), tid >> ilog2(WC), tw);
     for (int k = tid & (LPL - 1); k < nkept; k += LPL) {
         const int e = k <= a.nk_pos ? k : N - nkept + k;
         out[((cw / TY) * N + (cw & (TY - 1))) * N + e] = tile[e * LD + cw];
