@@ -568,6 +568,7 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
     cb.grid_stride = (long long)n3;
     cb.n = n;
     cb.interlace = plan->d.interlace;
+    cb.per_grid = plan->d.interlace ? 1 : 2;
     c2<T>* pG1 = partner;
     c2<T>* pG2 = plan->need_g ? partner + n3 : nullptr;
     c2<T>* pD = plan->need_d ? partner + (plan->need_g ? 2 : 0) * n3 : nullptr;
@@ -698,7 +699,7 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
             cc.n = ch.n;
             cc.part = ch.part;
             cc.out_row = c0 + ci;
-            cc.ynorm = ylm_norm(ch.L, ch.n);
+            cc.ynorm = ylm_norm_scaled(ch.L, ch.n);
             if (ch.kind == KIND_CROSS) cb.has_d = 1; else cb.has_g = 1;
         }
         { lpp_status s0 = assign_fused(sh.count); if (s0 != LPP_OK) return s0; }

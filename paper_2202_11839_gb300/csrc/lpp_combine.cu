@@ -40,14 +40,14 @@ __device__ __forceinline__ void unpack(const c2<T>* g, const ModeCtx<T>& c, c2<T
     B = mk<T>(h * di, -h * dr);
 }
 
-// k-space field at m and -m for sub-field `sub` of a slot.
+// k-space field at m and -m for sub-field `sub` of a slot, from its packed values.
 template <typename T>
-__device__ __forceinline__ void field_at(const c2<T>* g, int sub, int interlace, const ModeCtx<T>& c, c2<T>& Fm,
+__device__ __forceinline__ void field_of(c2<T> zm, c2<T> zp, int sub, int interlace, const ModeCtx<T>& c, c2<T>& Fm,
                                          c2<T>& Fp) {
-    c2<T> A, B;
-    unpack<T>(g, c, A, B);
+    const T h = (T)0.5;
+    const c2<T> A = mk<T>(h * (zm.x + zp.x), h * (zm.y - zp.y));
+    const c2<T> B = mk<T>(h * (zm.y + zp.y), -h * (zm.x - zp.x));   // -i (zm - conj zp) / 2
     if (interlace) {
-        const T h = (T)0.5;
         Fm = cscale<T>(cadd<T>(A, cmul<T>(c.ph_m, B)), h * c.iw_m);
         Fp = cscale<T>(cadd<T>(cconj<T>(A), cmul<T>(c.ph_p, cconj<T>(B))), h * c.iw_p);
     } else {
@@ -55,6 +55,13 @@ __device__ __forceinline__ void field_at(const c2<T>* g, int sub, int interlace,
         Fm = cscale<T>(X, c.iw_m);
         Fp = cscale<T>(cconj<T>(X), c.iw_p);
     }
+}
+
+// k-space field at m and -m for sub-field `sub` of a slot.
+template <typename T>
+__device__ __forceinline__ void field_at(const c2<T>* g, int sub, int interlace, const ModeCtx<T>& c, c2<T>& Fm,
+                                         c2<T>& Fp) {
+    field_of<T>(g[c.im], g[c.ip], sub, interlace, c, Fm, Fp);
 }
 
 template <typename T>
@@ -178,39 +185,64 @@ __global__ void __launch_bounds__(1024) k_combine(CombineArgs<T> a) {
                 if (a.has_d) { Dm = a.pD[c.im]; Dp = a.pD[c.ip]; }
                 if (a.has_g) { G1m = a.pG1[c.im]; G1p = a.pG1[c.ip]; G2m = a.pG2[c.im]; G2p = a.pG2[c.ip]; }
             }
-            for (int ci = 0; ci < a.n_ch; ++ci) {
-                const CombineChan& ch = a.ch[ci];
-                T tre = 0, tim = 0;
-                if (own_pair) {
-                    c2<T> Fm, Fp;
-                    field_at<T>(a.grids + ch.slot * a.grid_stride, ch.sub, a.interlace, c, Fm, Fp);
-                    if (ch.part == PART_IM) {
-                        Fm = mk<T>(-Fm.y, Fm.x);
-                        Fp = mk<T>(-Fp.y, Fp.x);
+            // the mirror is exactly -k unless an index sits at the Nyquist frequency; then an
+            // even-degree harmonic takes the same value at both members of the pair
+            const bool mirror_neg = (fxp == -fx) && (fyp == -fy) && (fzp == -fz);
+            const int n_slots = (a.n_ch + a.per_grid - 1) / a.per_grid;
+            // four slots at a time: their packed values at m and -m are loaded together
+            for (int s0 = 0; s0 < n_slots; s0 += 4) {
+                c2<T> zm[4], zp[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    zm[k] = zp[k] = mk<T>(0, 0);
+                    if (own_pair && s0 + k < n_slots) {
+                        const c2<T>* g = a.grids + (long long)(s0 + k) * a.grid_stride;
+                        zm[k] = g[c.im];
+                        zp[k] = g[c.ip];
                     }
-                    // partner: delta(-k) = conj D; gamma*(-k) = conj G1 - i conj G2;
-                    // gamma(-k) = conj G1 + i conj G2
-                    c2<T> Pm, Pp;
-                    if (ch.kind == KIND_CROSS) {
-                        Pm = cconj<T>(Dm);
-                        Pp = cconj<T>(Dp);
-                    } else {
-                        const T s = ch.kind == KIND_PLUS ? (T)-1 : (T)1;
-                        // conj(G1) + s i conj(G2)
-                        Pm = mk<T>(G1m.x + s * G2m.y, -G1m.y + s * G2m.x);
-                        Pp = mk<T>(G1p.x + s * G2p.y, -G1p.y + s * G2p.x);
-                    }
-                    const T yn = (T)ch.ynorm;
-                    const T ym = yn * ylm_poly<T>(ch.L, ch.n, kx, ky, kz);
-                    c2<T> t = cscale<T>(cmul<T>(Fm, Pm), ym);
-                    if (!c.self) {
-                        const T yp2 = yn * ylm_poly<T>(ch.L, ch.n, kxp, kyp, kzp);
-                        t = cadd<T>(t, cscale<T>(cmul<T>(Fp, Pp), yp2));
-                    }
-                    tre = t.x;
-                    tim = t.y;
                 }
-                warp_bin_add<T>(tre, tim, bin, acc + ci * 2 * nb);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (s0 + k >= n_slots) break;
+                    for (int sub = 0; sub < a.per_grid; ++sub) {
+                        const int ci = (s0 + k) * a.per_grid + sub;
+                        if (ci >= a.n_ch) break;
+                        const CombineChan& ch = a.ch[ci];
+                        T tre = 0, tim = 0;
+                        if (own_pair) {
+                            c2<T> Fm, Fp;
+                            field_of<T>(zm[k], zp[k], ch.sub, a.interlace, c, Fm, Fp);
+                            if (ch.part == PART_IM) {
+                                Fm = mk<T>(-Fm.y, Fm.x);
+                                Fp = mk<T>(-Fp.y, Fp.x);
+                            }
+                            // partner: delta(-k) = conj D; gamma*(-k) = conj G1 - i conj G2;
+                            // gamma(-k) = conj G1 + i conj G2
+                            c2<T> Pm, Pp;
+                            if (ch.kind == KIND_CROSS) {
+                                Pm = cconj<T>(Dm);
+                                Pp = cconj<T>(Dp);
+                            } else {
+                                const T s = ch.kind == KIND_PLUS ? (T)-1 : (T)1;
+                                // conj(G1) + s i conj(G2)
+                                Pm = mk<T>(G1m.x + s * G2m.y, -G1m.y + s * G2m.x);
+                                Pp = mk<T>(G1p.x + s * G2p.y, -G1p.y + s * G2p.x);
+                            }
+                            const T yn = (T)ch.ynorm;
+                            const T ym = yn * ylm_poly_scaled<T>(ch.L, ch.n, kx, ky, kz);
+                            c2<T> t = cscale<T>(cmul<T>(Fm, Pm), ym);
+                            if (!c.self) {
+                                const T yp2 = (mirror_neg && (ch.L & 1) == 0)
+                                                  ? ym
+                                                  : yn * ylm_poly_scaled<T>(ch.L, ch.n, kxp, kyp, kzp);
+                                t = cadd<T>(t, cscale<T>(cmul<T>(Fp, Pp), yp2));
+                            }
+                            tre = t.x;
+                            tim = t.y;
+                        }
+                        warp_bin_add<T>(tre, tim, bin, acc + ci * 2 * nb);
+                    }
+                }
             }
         }
         __syncthreads();

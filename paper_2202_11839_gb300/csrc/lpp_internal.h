@@ -71,6 +71,42 @@ __host__ __device__ __forceinline__ T ylm_poly(int L, int n, T x, T y, T z) {
     return q * (n > 0 ? re : im);
 }
 
+// (L - |n|)! * ylm_poly(L, n, x, y, z) without divisions: with q~_l = (l - m)! Q_l^m the
+// recurrence (l - m) Q_l = (2l - 1) z Q_{l-1} - (l + m - 1) Q_{l-2} becomes
+// q~_l = (2l - 1) z q~_{l-1} - (l + m - 1)(l - m - 1) q~_{l-2}, integer coefficients only.
+template <typename T>
+__host__ __device__ __forceinline__ T ylm_poly_scaled(int L, int n, T x, T y, T z) {
+    int m = n < 0 ? -n : n;
+    T qmm = (T)1;
+    for (int i = 1; i <= m; ++i) qmm *= (T)(2 * i - 1);
+    T q = qmm;
+    if (L > m) {
+        T q0 = qmm, q1 = (T)(2 * m + 1) * z * qmm;
+        for (int l = m + 2; l <= L; ++l) {
+            T q2 = (T)(2 * l - 1) * z * q1 - (T)((l + m - 1) * (l - m - 1)) * q0;
+            q0 = q1;
+            q1 = q2;
+        }
+        q = q1;
+    }
+    if (m == 0) return q;
+    T re = (T)1, im = (T)0;
+    for (int i = 0; i < m; ++i) {
+        T t = re * x - im * y;
+        im = re * y + im * x;
+        re = t;
+    }
+    return q * (n > 0 ? re : im);
+}
+
+// ylm_norm(L, n) / (L - |n|)!: the constant that goes with ylm_poly_scaled.
+__host__ __device__ inline double ylm_norm_scaled(int L, int n) {
+    int m = n < 0 ? -n : n;
+    double f = 1.0;
+    for (int j = 2; j <= L - m; ++j) f *= (double)j;
+    return ylm_norm(L, n) / f;
+}
+
 // ------------------------------------------------------------------ channel tables
 enum Kind { KIND_CROSS = 0, KIND_PLUS = 1, KIND_MINUS = 2 };
 enum Part { PART_RE = 0, PART_IM = 1 };

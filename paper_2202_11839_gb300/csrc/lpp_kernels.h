@@ -208,7 +208,7 @@ struct CombineChan {
     int L, n;      // harmonic
     int part;      // Part: multiply the field by 1 or by i
     int out_row;   // row of the FP64 output [row][bin][2]
-    double ynorm;  // normalisation of Y_{L,n}
+    double ynorm;  // normalisation of Y_{L,n} divided by (L - |n|)! (goes with ylm_poly_scaled)
 };
 
 template <typename T>
@@ -218,6 +218,7 @@ struct CombineArgs {
     int n;
     int interlace;
     int n_ch;
+    int per_grid;          // channels per batch grid: 1 (interlaced) or 2 (two packed fields)
     CombineChan ch[kMaxBatchCh];
     // partner spectra (full n^3 arrays, valid on kept modes)
     c2<T>* pD;
