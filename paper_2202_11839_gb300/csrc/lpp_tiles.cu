@@ -201,31 +201,78 @@ k_assign_xfft(FusedArgs<T> a) {
     c2<T>* out = a.grids + (size_t)sl.grid * a.grid_stride + ((size_t)z0 * N + y0) * N;
 
     // the particles touching the tile: TZ+3 z rows of keys y0-2 .. y0+TY per source,
-    // one or two contiguous ranges each (the y window may wrap)
-    if (tid == 0) {
-        int nr = 0, acc = 0;
-        for (int s = 0; s < sl.n_src; ++s) {
-            const int* off = a.cat[sl.src[s].cat].off;
-            for (int dz = 0; dz < TZ + 3; ++dz) {
-                const int zr = (z0 - 2 + dz) & (N - 1);
-                const int ylo = y0 - 2, yhi = y0 + TY;   // inclusive
-                int bb[2], ee[2], m = 0;
-                bb[m] = off[zr * N + (ylo < 0 ? 0 : ylo)];
-                ee[m++] = off[zr * N + (yhi >= N ? N - 1 : yhi) + 1];
-                if (ylo < 0) { bb[m] = off[zr * N + N + ylo]; ee[m++] = off[zr * N + N]; }
-                if (yhi >= N) { bb[m] = off[zr * N]; ee[m++] = off[zr * N + (yhi - N) + 1]; }
-                for (int q = 0; q < m; ++q) {
-                    if (ee[q] <= bb[q]) continue;
-                    r_begin[nr] = bb[q];
-                    r_src[nr] = s;
-                    r_pref[nr] = acc;
-                    acc += ee[q] - bb[q];
-                    ++nr;
+    // one or two contiguous ranges each (the y window may wrap).  Lane l of warp 0 takes
+    // row l (source l / (TZ+3)); a warp scan places the ranges.  Meanwhile the other warps
+    // clear the tile and load the twiddles.
+    if (S::THREADS < 64) {
+        // tiny tiles (n <= 16): one thread finds the ranges, everybody clears the tile
+        if (tid == 0) {
+            int nr = 0, acc = 0;
+            for (int sidx = 0; sidx < sl.n_src; ++sidx) {
+                const int* off = a.cat[sl.src[sidx].cat].off;
+                for (int dz = 0; dz < TZ + 3; ++dz) {
+                    const int zr = (z0 - 2 + dz) & (N - 1);
+                    const int ylo = y0 - 2, yhi = y0 + TY;
+                    int bb[2], ee[2], m = 0;
+                    bb[m] = off[zr * N + (ylo < 0 ? 0 : ylo)];
+                    ee[m++] = off[zr * N + (yhi >= N ? N - 1 : yhi) + 1];
+                    if (ylo < 0) { bb[m] = off[zr * N + N + ylo]; ee[m++] = off[zr * N + N]; }
+                    if (yhi >= N) { bb[m] = off[zr * N]; ee[m++] = off[zr * N + (yhi - N) + 1]; }
+                    for (int q = 0; q < m; ++q) {
+                        if (ee[q] <= bb[q]) continue;
+                        r_begin[nr] = bb[q];
+                        r_src[nr] = sidx;
+                        r_pref[nr] = acc;
+                        acc += ee[q] - bb[q];
+                        ++nr;
+                    }
                 }
             }
+            r_pref[nr] = acc;
+            n_ranges = nr;
         }
-        r_pref[nr] = acc;
-        n_ranges = nr;
+        for (int i = tid; i < N; i += S::THREADS) tw[i] = a.tw[i];
+        for (int i = tid; i < N * LD; i += S::THREADS) tile[i] = mk<T>((T)0, (T)0);
+    } else if (tid < 32) {
+        const int lane = tid;
+        int bb[2] = {0, 0}, ee[2] = {0, 0}, m = 0, s_idx = 0;
+        if (lane < sl.n_src * (TZ + 3)) {
+            s_idx = lane / (TZ + 3);
+            const int dz = lane - s_idx * (TZ + 3);
+            const int* off = a.cat[sl.src[s_idx].cat].off;
+            const int zr = (z0 - 2 + dz) & (N - 1);
+            const int ylo = y0 - 2, yhi = y0 + TY;   // inclusive
+            bb[m] = off[zr * N + (ylo < 0 ? 0 : ylo)];
+            ee[m++] = off[zr * N + (yhi >= N ? N - 1 : yhi) + 1];
+            if (ylo < 0) { bb[m] = off[zr * N + N + ylo]; ee[m++] = off[zr * N + N]; }
+            if (yhi >= N) { bb[m] = off[zr * N]; ee[m++] = off[zr * N + (yhi - N) + 1]; }
+        }
+        int nr_l = 0, cnt_l = 0;
+        for (int q = 0; q < m; ++q)
+            if (ee[q] > bb[q]) { ++nr_l; cnt_l += ee[q] - bb[q]; }
+        int nr_inc = nr_l, cnt_inc = cnt_l;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int a1 = __shfl_up_sync(0xffffffffu, nr_inc, d);
+            const int a2 = __shfl_up_sync(0xffffffffu, cnt_inc, d);
+            if (lane >= d) { nr_inc += a1; cnt_inc += a2; }
+        }
+        int nr = nr_inc - nr_l, acc = cnt_inc - cnt_l;
+        for (int q = 0; q < m; ++q) {
+            if (ee[q] <= bb[q]) continue;
+            r_begin[nr] = bb[q];
+            r_src[nr] = s_idx;
+            r_pref[nr] = acc;
+            acc += ee[q] - bb[q];
+            ++nr;
+        }
+        if (lane == 31) {
+            r_pref[nr_inc] = cnt_inc;
+            n_ranges = nr_inc;
+        }
+    } else {
+        for (int i = tid - 32; i < N; i += S::THREADS - 32) tw[i] = a.tw[i];
+        for (int i = tid - 32; i < N * LD; i += S::THREADS - 32) tile[i] = mk<T>((T)0, (T)0);
     }
     __syncthreads();
     const int nr = n_ranges;
@@ -243,9 +290,6 @@ k_assign_xfft(FusedArgs<T> a) {
         }
         return;
     }
-    for (int i = tid; i < N; i += S::THREADS) tw[i] = a.tw[i];
-    for (int i = tid; i < N * LD; i += S::THREADS) tile[i] = mk<T>((T)0, (T)0);
-    __syncthreads();
     const T alpha = (T)a.sums[SUM_ALPHA];
     const int P = a.scheme;
     const T* vb_ptr = (!a.interlace && sl.vals_b) ? static_cast<const T*>(sl.vals_b) : nullptr;
