@@ -181,10 +181,13 @@ struct FusedShape {
     static constexpr int IPT = (W * N / 8) <= 512 ? 1 : ((W * N / 8) <= 1024 ? 2 : 4);
     static constexpr int THREADS = W * N / (8 * IPT);
     static constexpr int MAXR = 2 * 2 * (TZ + 3);   // key ranges: sources x z rows x (1 or 2)
+    // resident CTAs per SM the register budget is sized for (shared memory allows 3 at
+    // n = 512 in FP32)
+    static constexpr int MINB = (sizeof(T) == 4 && LOGN == 9) ? 3 : 1;
 };
 
 template <typename T, int LOGN>
-__global__ void __launch_bounds__(FusedShape<T, LOGN>::THREADS)
+__global__ void __launch_bounds__(FusedShape<T, LOGN>::THREADS, FusedShape<T, LOGN>::MINB)
 k_assign_xfft(FusedArgs<T> a) {
     using S = FusedShape<T, LOGN>;
     constexpr int N = S::N, TY = S::TY, TZ = S::TZ, W = S::W, LD = S::LD;
