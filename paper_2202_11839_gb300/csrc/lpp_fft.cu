@@ -55,7 +55,6 @@ __global__ void __launch_bounds__(PassShape<LOGN>::THREADS, sizeof(T) == 4 ? 2 :
         cs = 1;
     }
     for (int i = tid; i < N; i += S::THREADS) tw[i] = twg[i];
-    constexpr int WC = W / S::IPT;
     if constexpr (MODE == 0) {
 #pragma unroll
         for (int k = 0; k < S::PER; ++k) {
@@ -64,7 +63,7 @@ __global__ void __launch_bounds__(PassShape<LOGN>::THREADS, sizeof(T) == 4 ? 2 :
             tile[e * LD + c] = base[e * es + c * cs];
         }
         __syncthreads();
-        fft_columns<T, LOGN, INV, S::IPT, LD, WC>(tile, tid & (WC - 1), tid >> ilog2(WC), tw);
+        fft_columns<T, LOGN, INV, S::IPT, LD>(tile, tid & (W - 1), tid >> S::LOGW, tw);
 #pragma unroll
         for (int k = 0; k < S::PER; ++k) {
             const int idx = tid + k * S::THREADS;
@@ -86,7 +85,7 @@ __global__ void __launch_bounds__(PassShape<LOGN>::THREADS, sizeof(T) == 4 ? 2 :
             for (int k = k0; k < k0 + KB; ++k) sp[k * ROWS * LD] = gp[(size_t)k * ROWS * ES];
         }
         __syncthreads();
-        fft_columns<T, LOGN, INV, S::IPT, LD, WC>(tile, tid & (WC - 1), tid >> ilog2(WC), tw);
+        fft_columns<T, LOGN, INV, S::IPT, LD>(tile, tid & (W - 1), tid >> S::LOGW, tw);
 #pragma unroll
         for (int k = 0; k < S::PER; ++k)
             if (kept(e0 + k * ROWS, N, g.nk_pos, g.nk_neg)) gp[(size_t)k * ROWS * ES] = sp[k * ROWS * LD];

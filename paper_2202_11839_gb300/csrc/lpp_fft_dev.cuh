@@ -56,85 +56,77 @@ __device__ __forceinline__ void dft8(c2<T>* v) {
     v[7] = csub<T>(e[3], t3);
 }
 
-// One Stockham stage of radix R on every pencil of the tile.  The thread owns pencils
-// c + k WC (k < IPT) and butterflies j = u + q N/8 (q < 8/R) of each.  The tile's row
-// pitch LD, the pencil stride WC and the stage's sub-transform length NS are compile-time,
-// so every shared-memory address is a per-thread base plus an immediate offset; the
-// twiddles of the thread's butterflies are loaded once and reused for all its pencils
-// (and skipped in the first stage, where they are all 1).
-template <typename T, int N, int R, bool INV, int IPT, int LD, int WC, int NS>
+// One Stockham stage of radix R on every pencil of the tile.  The thread owns pencil c
+// and the butterfly slots u + s US (s < IPT, US = N / (8 IPT)), each slot being one
+// radix-8 butterfly or 8/R radix-R ones (j = slot + q N/8).  Consecutive threads own
+// consecutive pencils at the same slot, so with an odd LD the 16 threads of a half warp
+// touch 16 different banks pairs (no conflicts) and read the same twiddle (a broadcast).
+// LD and the stage's sub-transform length NS are compile-time, so every address is a
+// per-thread base plus an immediate offset; the first stage (NS = 1) has no twiddles.
+template <typename T, int N, int R, bool INV, int IPT, int LD, int NS>
 __device__ __forceinline__ void stockham_stage(c2<T>* tile, int c, int u, const c2<T>* tw) {
     constexpr int Q = 8 / R;
-    c2<T> w[Q][R];
-    int dsto[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const int j = u + q * (N / 8);
-        const int jm = j & (NS - 1);
-        if (NS > 1) {
-            const int step = jm * (N / (NS * R));
-#pragma unroll
-            for (int r = 1; r < R; ++r) {
-                c2<T> t = tw[step * r];
-                if (INV) t.y = -t.y;
-                w[q][r] = t;
-            }
-        }
-        dsto[q] = ((j - jm) * R + jm) * LD + c;
-    }
+    constexpr int US = N / (8 * IPT);
     c2<T> v[IPT][8];
     const c2<T>* src = tile + u * LD + c;
 #pragma unroll
-    for (int k = 0; k < IPT; ++k) {
+    for (int s = 0; s < IPT; ++s) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[k][q * R + r] = src[(q * (N / 8) + r * (N / R)) * LD + k * WC];
+            for (int r = 0; r < R; ++r) v[s][q * R + r] = src[(s * US + q * (N / 8) + r * (N / R)) * LD];
         }
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < IPT; ++k) {
+    for (int s = 0; s < IPT; ++s) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
+            const int j = u + s * US + q * (N / 8);
+            const int jm = j & (NS - 1);
             if (NS > 1) {
+                const int step = jm * (N / (NS * R));
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[k][q * R + r] = cmul<T>(v[k][q * R + r], w[q][r]);
+                for (int r = 1; r < R; ++r) {
+                    c2<T> w = tw[step * r];
+                    if (INV) w.y = -w.y;
+                    v[s][q * R + r] = cmul<T>(v[s][q * R + r], w);
+                }
             }
-            if (R == 8) dft8<T, INV>(v[k] + q * R);
-            else if (R == 4) dft4<T, INV>(v[k] + q * R);
-            else dft2<T, INV>(v[k] + q * R);
-            c2<T>* dst = tile + dsto[q] + k * WC;
+            if (R == 8) dft8<T, INV>(v[s] + q * R);
+            else if (R == 4) dft4<T, INV>(v[s] + q * R);
+            else dft2<T, INV>(v[s] + q * R);
+            c2<T>* dst = tile + ((j - jm) * R + jm) * LD + c;
 #pragma unroll
-            for (int r = 0; r < R; ++r) dst[r * NS * LD] = v[k][q * R + r];
+            for (int r = 0; r < R; ++r) dst[r * NS * LD] = v[s][q * R + r];
         }
     }
     __syncthreads();
 }
 
-template <typename T, int N, bool INV, int IPT, int LD, int WC, int NS>
+template <typename T, int N, bool INV, int IPT, int LD, int NS>
 __device__ __forceinline__ void radix8_stages(c2<T>* tile, int c, int u, const c2<T>* tw) {
     if constexpr (NS < N) {
-        stockham_stage<T, N, 8, INV, IPT, LD, WC, NS>(tile, c, u, tw);
-        radix8_stages<T, N, INV, IPT, LD, WC, NS * 8>(tile, c, u, tw);
+        stockham_stage<T, N, 8, INV, IPT, LD, NS>(tile, c, u, tw);
+        radix8_stages<T, N, INV, IPT, LD, NS * 8>(tile, c, u, tw);
     }
 }
 
 // Forward (or inverse, unnormalised) FFT of length N = 2^LOGN along every pencil: one
 // radix-2 or radix-4 stage when LOGN is not a multiple of 3, then radix-8 stages.
-template <typename T, int LOGN, bool INV, int IPT, int LD, int WC>
+// c = the thread's pencil, u = its first butterfly slot (0 .. N / (8 IPT) - 1).
+template <typename T, int LOGN, bool INV, int IPT, int LD>
 __device__ __forceinline__ void fft_columns(c2<T>* tile, int c, int u, const c2<T>* tw) {
-    // c = thread's first pencil, WC = W / IPT, u = butterfly slot (0 .. N/8 - 1)
     constexpr int N = 1 << LOGN;
     constexpr int rem = LOGN % 3;
     if constexpr (rem == 1) {
-        stockham_stage<T, N, 2, INV, IPT, LD, WC, 1>(tile, c, u, tw);
-        radix8_stages<T, N, INV, IPT, LD, WC, 2>(tile, c, u, tw);
+        stockham_stage<T, N, 2, INV, IPT, LD, 1>(tile, c, u, tw);
+        radix8_stages<T, N, INV, IPT, LD, 2>(tile, c, u, tw);
     } else if constexpr (rem == 2) {
-        stockham_stage<T, N, 4, INV, IPT, LD, WC, 1>(tile, c, u, tw);
-        radix8_stages<T, N, INV, IPT, LD, WC, 4>(tile, c, u, tw);
+        stockham_stage<T, N, 4, INV, IPT, LD, 1>(tile, c, u, tw);
+        radix8_stages<T, N, INV, IPT, LD, 4>(tile, c, u, tw);
     } else {
-        radix8_stages<T, N, INV, IPT, LD, WC, 1>(tile, c, u, tw);
+        radix8_stages<T, N, INV, IPT, LD, 1>(tile, c, u, tw);
     }
 }
 

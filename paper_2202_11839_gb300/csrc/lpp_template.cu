@@ -105,10 +105,10 @@ __device__ double block_sum(double v, double* red) {
 // wk <- FFT(wk) * u ; FFT again (the log-Fourier transform between the two grids)
 __device__ void log_fourier(double2* wk, const double2* __restrict__ u, const double2* __restrict__ tw) {
     const int tid = threadIdx.x;
-    lpp::fft_columns<double, kLogN, false, 1, 1, 1>(wk, 0, tid, tw);
+    lpp::fft_columns<double, kLogN, false, 1, 1>(wk, 0, tid, tw);
     for (int i = tid; i < kNfft; i += blockDim.x) wk[i] = lpp::cmul<double>(wk[i], u[i]);
     __syncthreads();
-    lpp::fft_columns<double, kLogN, false, 1, 1, 1>(wk, 0, tid, tw);
+    lpp::fft_columns<double, kLogN, false, 1, 1>(wk, 0, tid, tw);
 }
 
 __global__ void __launch_bounds__(512, 1) k_template(TemplateArgs a) {

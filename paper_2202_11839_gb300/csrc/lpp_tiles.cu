@@ -327,8 +327,7 @@ k_assign_xfft(FusedArgs<T> a) {
         if (a.interlace) scatter_one<T>(tilef, LD, N, P, ux, uy, uz, (T)0.5, y0, z0, TY, TZ, va, (T)0, false, 1);
     }
     __syncthreads();
-    constexpr int WC = W / S::IPT;
-    fft_columns<T, LOGN, false, S::IPT, LD, WC>(tile, tid & (WC - 1), tid >> ilog2(WC), tw);
+    fft_columns<T, LOGN, false, S::IPT, LD>(tile, tid & (W - 1), tid >> ilog2(W), tw);
     for (int k = tid & (LPL - 1); k < nkept; k += LPL) {
         const int e = k <= a.nk_pos ? k : N - nkept + k;
         out[((cw / TY) * N + (cw & (TY - 1))) * N + e] = tile[e * LD + cw];
