@@ -66,6 +66,7 @@ struct lpp_plan_s {
     size_t off_key[3] = {0, 0, 0}, off_su[3] = {0, 0, 0}, off_sw[3] = {0, 0, 0}, off_koff[3] = {0, 0, 0};
     size_t off_perm = 0, off_counts = 0, off_cursor = 0;
     size_t off_wout = 0, off_wthr = 0;   // window multipoles: per-channel shell sums, thresholds
+    size_t off_pmask = 0;                // [3][n] z planes reached per catalogue role
     int fty = 4, ftz = 4;
     int n_partner = 0;
     int out_rows = 0;
@@ -288,6 +289,7 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
     plan->off_perm = take((size_t)caps[0] * sizeof(int));
     plan->off_counts = take((size_t)n * n * sizeof(int));
     plan->off_cursor = take((size_t)n * n * sizeof(int));
+    plan->off_pmask = take((size_t)3 * n * sizeof(int));
     plan->off_wout = take((size_t)kWindowChannels * 256 * 2 * sizeof(double));
     plan->off_wthr = take(257 * sizeof(int));
     plan->off_partner = take((size_t)std::max(1, plan->n_partner) * n3 * cs);
@@ -509,6 +511,29 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
     { lpp_status s0 = sort_cat(LPP_SHAPES, sh); if (s0 != LPP_OK) return s0; }
     if (plan->cat[LPP_DENSITY].set) { lpp_status s0 = sort_cat(LPP_DENSITY, de); if (s0 != LPP_OK) return s0; }
     if (has_rand) { lpp_status s0 = sort_cat(LPP_RANDOMS, ra); if (s0 != LPP_OK) return s0; }
+    int* pmask = (int*)(plan->ws + plan->off_pmask);
+    LPP_CUDA(launch_plane_mask((const int*)(plan->ws + plan->off_koff[0]), (const int*)(plan->ws + plan->off_koff[1]),
+                               (const int*)(plan->ws + plan->off_koff[2]), 1, plan->cat[LPP_DENSITY].set ? 1 : 0,
+                               has_rand ? 1 : 0, n, pmask, st));
+    // timing only: which planes are reached, for the byte counts of the skipping kernels
+    // (one small synchronisation per estimate)
+    std::vector<int> hmask;
+    if (tm) {
+        hmask.resize((size_t)3 * n);
+        LPP_CUDA(cudaMemcpyAsync(hmask.data(), pmask, hmask.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+        LPP_CUDA(cudaStreamSynchronize(st));
+    }
+    auto plane_frac = [&](int bits) -> double {
+        if (hmask.empty() || bits == 0) return 1.0;
+        long long c = 0;
+        for (int z = 0; z < n; ++z) {
+            int hit = 0;
+            for (int r = 0; r < 3; ++r)
+                if (bits & (1 << r)) hit |= hmask[(size_t)r * n + z];
+            c += hit != 0;
+        }
+        return (double)c / n;
+    };
 
     // 1. sky frames, shears and harmonic weights of the shape catalogue (in sorted order)
     CoeffArgs<T> ca;
@@ -608,11 +633,22 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
     fa.nk_neg = plan->nk_neg;
     fa.tw = tw;
     fa.sums = sums;
+    fa.pmask = pmask;
     const double xbytes = (double)n * n * plan->nky * sizeof(c2<T>);   // kept x pencils of one grid
+    auto slot_bits = [&](const FusedSlot& f) {
+        int bits = 0;
+        for (int q = 0; q < f.n_src; ++q) bits |= 1 << f.src[q].cat;
+        return bits;
+    };
     auto assign_fused = [&](long long particles) -> lpp_status {
         if (tm) tm->begin(KK_ASSIGN, st);
         LPP_CUDA(launch_assign_xfft<T>(fa, st));
-        if (tm) tm->end(KK_ASSIGN, st, fa.n_slots * (xbytes + (double)particles * 4 * plan->es));
+        if (tm) {
+            // kept x pencils are stored on the planes the slot's particles reach
+            double wb = 0.0;
+            for (int i = 0; i < fa.n_slots; ++i) wb += xbytes * plane_frac(slot_bits(fa.slots[i]));
+            tm->end(KK_ASSIGN, st, wb + fa.n_slots * (double)particles * 4 * plan->es);
+        }
         return LPP_OK;
     };
 
@@ -659,7 +695,15 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
             parts += de.count + (has_rand ? ra.count : 0);
         }
         { lpp_status s0 = assign_fused(parts); if (s0 != LPP_OK) return s0; }
-        LPP_CUDA(fft_yz<T>(grids, pgrids, n, tw, geom, false, st, tm));
+        FftGeom gp = geom;
+        gp.pmask = pmask;
+        double fr = 0.0;
+        for (int i = 0; i < fa.n_slots; ++i) {
+            gp.gmask[fa.slots[i].grid] = slot_bits(fa.slots[i]);
+            fr += plane_frac(gp.gmask[fa.slots[i].grid]);
+        }
+        gp.yread_frac = fa.n_slots ? (float)(fr / fa.n_slots) : 1.0f;
+        LPP_CUDA(fft_yz<T>(grids, pgrids, n, tw, gp, false, st, tm));
         cb.partner_mode = 1;
         cb.has_d = plan->need_d;
         cb.has_g = plan->need_g;
@@ -703,7 +747,11 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
             if (ch.kind == KIND_CROSS) cb.has_d = 1; else cb.has_g = 1;
         }
         { lpp_status s0 = assign_fused(sh.count); if (s0 != LPP_OK) return s0; }
-        LPP_CUDA(fft_yz<T>(grids, ngr, n, tw, geom, false, st, tm));
+        FftGeom gc = geom;
+        gc.pmask = pmask;
+        for (int i = 0; i < ngr; ++i) gc.gmask[i] = 1 << LPP_SHAPES;
+        gc.yread_frac = (float)plane_frac(1 << LPP_SHAPES);
+        LPP_CUDA(fft_yz<T>(grids, ngr, n, tw, gc, false, st, tm));
         if (tm) tm->begin(KK_COMBINE, st);
         LPP_CUDA(launch_combine<T>(cb, plan->n_sm, st));
         if (tm) tm->end(KK_COMBINE, st, shell_modes * sizeof(c2<T>) * (ngr + (cb.has_d ? 1 : 0) + (cb.has_g ? 2 : 0)));

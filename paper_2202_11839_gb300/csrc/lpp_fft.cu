@@ -71,6 +71,24 @@ __global__ void __launch_bounds__(PassShape<LOGN>::THREADS, sizeof(T) == 4 ? 2 :
             if (kept(e, N, g.nk_pos, g.nk_neg)) base[e * es + c * cs] = tile[e * LD + c];
         }
     } else {
+        if (MODE == 1 && g.pmask && g.gmask[blockIdx.y]) {
+            // a z plane that no particle of the grid's roles reaches: its pencils are zero
+            // (the fused assignment did not store them); write the kept zeros directly
+            const int z = tile_id / g.ntx;
+            int hit = 0;
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                if (g.gmask[blockIdx.y] & (1 << r)) hit |= g.pmask[r * N + z];
+            if (!hit) {
+                constexpr int ROWS = S::THREADS / W;
+                const int c = tid & (W - 1), e0 = tid >> S::LOGW;
+                c2<T>* gp = base + (size_t)e0 * N + c;
+#pragma unroll
+                for (int k = 0; k < S::PER; ++k)
+                    if (kept(e0 + k * ROWS, N, g.nk_pos, g.nk_neg)) gp[(size_t)k * ROWS * N] = mk<T>((T)0, (T)0);
+                return;
+            }
+        }
         // rows e0 + k ROWS of W consecutive x values: one base pointer, compile-time strides
         constexpr int ROWS = S::THREADS / W;
         constexpr unsigned ES = MODE == 1 ? (unsigned)N : (unsigned)N * N;
@@ -135,7 +153,7 @@ static cudaError_t launch_passes(c2<T>* data, int n_grids, const c2<T>* tw, cons
     }
     if (timer) timer->begin(KK_FFT, st);
     k_fft_pass<T, LOGN, INV, 1><<<dim3(g.ntx * N, n_grids), S::THREADS, smem, st>>>(data, tw, g);
-    if (timer) timer->end(KK_FFT, st, n_grids * n3 * es * xcols * (1.0 + keep));
+    if (timer) timer->end(KK_FFT, st, n_grids * n3 * es * xcols * ((double)g.yread_frac + keep));
     if (timer) timer->begin(KK_FFT, st);
     k_fft_pass<T, LOGN, INV, 2><<<dim3(g.ntx * g.nky, n_grids), S::THREADS, smem, st>>>(data, tw, g);
     if (timer) timer->end(KK_FFT, st, n_grids * n3 * es * xcols * keep * (1.0 + keep));

@@ -56,6 +56,12 @@ struct FftGeom {
     int ntx;     // kept x tiles (of W columns)
     int nlo;     // x tiles taken from the low end
     int nky;     // kept y indices
+    // optional skipping of empty z planes in the y pass: pmask [3][n] (per catalogue role,
+    // nonzero where a particle of that role can reach plane z) and, per grid of the call,
+    // the bit set of roles assigned to it (0: never skip)
+    const int* pmask = nullptr;
+    int gmask[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    float yread_frac = 1.0f;   // host bookkeeping: fraction of z planes the y pass reads
 };
 
 int fft_tile_width(int n);
@@ -70,7 +76,7 @@ cudaError_t fft_yz(c2<T>* data, int n_grids, int n, const c2<T>* tw, const FftGe
 
 // ---------------------------------------------------------- per-particle weights
 constexpr int kMaxGroups = 16;
-constexpr int kMaxSlots = 8;       // complex grids per batch
+constexpr int kMaxSlots = 8;       // complex grids per batch (FftGeom::gmask has as many)
 constexpr int kMaxBatchCh = 16;    // real fields per batch
 
 struct CoeffGroup {
@@ -190,9 +196,14 @@ struct FusedArgs {
     const c2<T>* tw;
     const double* sums;
     double observer[3], origin[3], h;   // for the harmonic weights
+    const int* pmask;                    // [3][n] planes reached per role, or null (write every pencil)
 };
 
 void fused_geometry(int n, size_t elem_bytes, int* ty, int* tz, int* ipt, int* threads, size_t* smem);
+// pmask[r][z] = 1 when a particle of role r (set[r] != 0) sits in a key row f with
+// z - 2 <= f <= z + 1 (mod n): the planes its CIC/TSC stencils (interlaced or not) reach.
+cudaError_t launch_plane_mask(const int* off0, const int* off1, const int* off2, int set0, int set1, int set2, int n,
+                              int* pmask, cudaStream_t st);
 template <typename T>
 cudaError_t launch_pencil_sort(const T* pos, const T* w, long long count, long long cap, int n, double box,
                                const double origin[3], int* key, int* counts, int* off, int* cursor, T* su, T* sw,

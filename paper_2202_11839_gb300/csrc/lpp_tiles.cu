@@ -286,10 +286,20 @@ k_assign_xfft(FusedArgs<T> a) {
     constexpr int LPL = S::THREADS / W;
     const int cw = tid / LPL;
     if (total == 0) {
-        // no particle reaches these pencils: their transform is zero
-        for (int k = tid & (LPL - 1); k < nkept; k += LPL) {
-            const int e = k <= a.nk_pos ? k : N - nkept + k;
-            out[((cw / TY) * N + (cw & (TY - 1))) * N + e] = mk<T>((T)0, (T)0);
+        // no particle reaches these pencils: their transform is zero.  Planes that no
+        // particle of the slot's roles reaches are skipped by the y pass, which writes
+        // their zeros itself: nothing to store for those.
+        bool write = true;
+        if (a.pmask) {
+            const int z = z0 + cw / TY;
+            write = false;
+            for (int sidx = 0; sidx < sl.n_src; ++sidx) write |= a.pmask[sl.src[sidx].cat * N + z] != 0;
+        }
+        if (write) {
+            for (int k = tid & (LPL - 1); k < nkept; k += LPL) {
+                const int e = k <= a.nk_pos ? k : N - nkept + k;
+                out[((cw / TY) * N + (cw & (TY - 1))) * N + e] = mk<T>((T)0, (T)0);
+            }
         }
         return;
     }
@@ -332,6 +342,29 @@ k_assign_xfft(FusedArgs<T> a) {
         const int e = k <= a.nk_pos ? k : N - nkept + k;
         out[((cw / TY) * N + (cw & (TY - 1))) * N + e] = tile[e * LD + cw];
     }
+}
+
+__global__ void k_plane_mask(const int* __restrict__ off0, const int* __restrict__ off1, const int* __restrict__ off2,
+                             int set0, int set1, int set2, int n, int* __restrict__ pmask) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * n) return;
+    const int r = i / n, z = i - r * n;
+    const int* off = r == 0 ? off0 : (r == 1 ? off1 : off2);
+    const int set = r == 0 ? set0 : (r == 1 ? set1 : set2);
+    int hit = 0;
+    if (set) {
+        for (int d = -2; d <= 1; ++d) {
+            const int f = (z + d) & (n - 1);
+            hit |= off[(size_t)(f + 1) * n] > off[(size_t)f * n];
+        }
+    }
+    pmask[i] = hit;
+}
+
+cudaError_t launch_plane_mask(const int* off0, const int* off1, const int* off2, int set0, int set1, int set2, int n,
+                              int* pmask, cudaStream_t st) {
+    k_plane_mask<<<(3 * n + 255) / 256, 256, 0, st>>>(off0, off1, off2, set0, set1, set2, n, pmask);
+    return cudaGetLastError();
 }
 
 // Tile shape (TY, TZ), pencils per thread, threads and shared memory of the fused kernel

@@ -12,19 +12,27 @@ ALL_MOMENTS = tuple(O.MOMENTS)
 
 
 def make_case(kind: str, n: int, count: int, seed: int, box: float = 300.0, n_rand: int = 0,
-              dtype=np.float64, separate_density: bool = False, gamma12: bool = False):
-    """Small synthetic catalogues: uniform positions, random tensors (or gamma_1,2), optional randoms."""
+              dtype=np.float64, separate_density: bool = False, gamma12: bool = False, zslab=None):
+    """Small synthetic catalogues: uniform positions, random tensors (or gamma_1,2), optional
+    randoms; with zslab = (a, b) every catalogue is confined to a <= z / box < b (so most z
+    planes of the grid receive nothing)."""
     rng = np.random.default_rng(seed)
     lo = 0.0
-    pos = S.uniform_positions(count, box, (lo, lo, lo), seed, 0, dtype)
+
+    def squeeze(p):
+        if zslab is not None:
+            p = p.copy()
+            p[2] = (zslab[0] * box + (p[2] / box) * (zslab[1] - zslab[0]) * box).astype(p.dtype)
+        return p
+    pos = squeeze(S.uniform_positions(count, box, (lo, lo, lo), seed, 0, dtype))
     shape = rng.standard_normal((2 if gamma12 else 6, count)).astype(dtype)
     w = rng.uniform(0.5, 1.5, count).astype(dtype)
     out = dict(pos=pos, w=w, shape=shape)
     if separate_density:
-        out["dpos"] = S.uniform_positions(count // 2 + 7, box, (lo, lo, lo), seed, 5, dtype)
+        out["dpos"] = squeeze(S.uniform_positions(count // 2 + 7, box, (lo, lo, lo), seed, 5, dtype))
         out["dw"] = rng.uniform(0.5, 1.5, out["dpos"].shape[1]).astype(dtype)
     if n_rand:
-        out["rpos"] = S.uniform_positions(n_rand, box, (lo, lo, lo), seed, 6, dtype)
+        out["rpos"] = squeeze(S.uniform_positions(n_rand, box, (lo, lo, lo), seed, 6, dtype))
         out["rw"] = rng.uniform(0.8, 1.2, n_rand).astype(dtype)
         out["rnbar"] = rng.uniform(0.5, 2.0, n_rand).astype(dtype)
     return out

@@ -45,6 +45,10 @@ CASES64 = {
     "tiny_grid_n8": (_cfg(8, 100.0, scheme=3, nb=3), dict(count=300)),
     "batch1_ragged": (_cfg(16, 300.0, batch=1, scheme=3, interlace=True), dict(count=700)),
     "batch3_noninterlaced": (_cfg(16, 300.0, batch=3), dict(count=700)),
+    # most z planes empty: the fused pass stores nothing there and the y pass writes zeros
+    "zslab_tsc_il_randoms_density_n32": (_cfg(32, 300.0, scheme=3, interlace=True),
+                                         dict(count=1500, n_rand=3000, separate_density=True, zslab=(0.3, 0.45))),
+    "zslab_cic_wrapping_n32": (_cfg(32, 300.0, scheme=2), dict(count=1200, zslab=(0.0, 0.08))),
 }
 
 
@@ -61,6 +65,8 @@ CASES32 = {
     "tsc_interlaced_n32": (_cfg(32, 500.0, scheme=3, interlace=True), dict(count=6000)),
     "cic_randoms_n32": (_cfg(32, 500.0, scheme=2, frac=0.5), dict(count=4000, n_rand=12000)),
     "gamma12_n64_pruned": (_cfg(64, 800.0, scheme=3, interlace=True, frac=0.4, nb=6), dict(count=5000, gamma12=True)),
+    "zslab_randoms_n64": (_cfg(64, 800.0, scheme=3, interlace=True, frac=0.5), dict(count=6000, n_rand=12000,
+                                                                                   zslab=(0.55, 0.7))),
 }
 
 
