@@ -349,6 +349,30 @@ cudaError_t launch_assign(const AssignArgs<T>& a, int scheme, int interlace, cud
     return cudaGetLastError();
 }
 
+// Per-row maximum of |coefficient|: a grid-stride loop per row (blockIdx.y), a warp
+// reduction and one atomicMax on the float's bits (non-negative floats order like ints).
+__global__ void __launch_bounds__(256) k_rowmax(const float* __restrict__ coeff, long long stride, long long count,
+                                                float* __restrict__ rmax) {
+    const float* row = coeff + (long long)blockIdx.y * stride;
+    float m = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(row[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(reinterpret_cast<int*>(rmax) + blockIdx.y, __float_as_int(m));
+}
+
+cudaError_t launch_rowmax(const float* coeff, long long stride, long long count, int rows, float* rmax,
+                          cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(rmax, 0, (size_t)rows * sizeof(float), st);
+    if (e != cudaSuccess || count == 0 || rows == 0) return e;
+    long long bx = (count + 255) / 256;
+    if (bx > 64) bx = 64;
+    k_rowmax<<<dim3((unsigned)bx, (unsigned)rows), 256, 0, st>>>(coeff, stride, count, rmax);
+    return cudaGetLastError();
+}
+
 template cudaError_t launch_coeffs<float>(const CoeffArgs<float>&, cudaStream_t);
 template cudaError_t launch_coeffs<double>(const CoeffArgs<double>&, cudaStream_t);
 template cudaError_t launch_sums<float>(const float*, const float*, long long, double*, int, int, int, cudaStream_t);

@@ -67,6 +67,7 @@ struct lpp_plan_s {
     size_t off_perm = 0, off_counts = 0, off_cursor = 0;
     size_t off_wout = 0, off_wthr = 0;   // window multipoles: per-channel shell sums, thresholds
     size_t off_pmask = 0;                // [3][n] z planes reached per catalogue role
+    size_t off_rmax = 0;                 // [n_coeff_rows] max |coefficient| per row (FP32 plans)
     int fty = 4, ftz = 4;
     int n_partner = 0;
     int out_rows = 0;
@@ -290,6 +291,7 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
     plan->off_counts = take((size_t)n * n * sizeof(int));
     plan->off_cursor = take((size_t)n * n * sizeof(int));
     plan->off_pmask = take((size_t)3 * n * sizeof(int));
+    plan->off_rmax = take((size_t)std::max(1, plan->n_coeff_rows) * sizeof(float));
     plan->off_wout = take((size_t)kWindowChannels * 256 * 2 * sizeof(double));
     plan->off_wthr = take(257 * sizeof(int));
     plan->off_partner = take((size_t)std::max(1, plan->n_partner) * n3 * cs);
@@ -483,6 +485,7 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
     c2<T>* grids = (c2<T>*)(plan->ws + plan->off_grids);
     c2<T>* partner = (c2<T>*)(plan->ws + plan->off_partner);
     T* coeff = (T*)(plan->ws + plan->off_coeff);
+    float* rmax = (float*)(plan->ws + plan->off_rmax);
     const long long stride = std::max<long long>(1, plan->d.max_shapes);
     const Catalogue& sh = plan->cat[LPP_SHAPES];
     const Catalogue& de = plan->cat[LPP_DENSITY].set ? plan->cat[LPP_DENSITY] : plan->cat[LPP_SHAPES];
@@ -567,6 +570,11 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         if (tm) tm->begin(KK_COEFF, st);
         LPP_CUDA(launch_coeffs<T>(ca, st));
         if (tm) tm->end(KK_COEFF, st, (double)sh.count * plan->es * (3 + 1 + 6 + plan->n_coeff_rows));
+        if (!plan->fp64) {
+            if (tm) tm->begin(KK_OTHER, st);
+            LPP_CUDA(launch_rowmax((const float*)coeff, stride, sh.count, plan->n_coeff_rows, rmax, st));
+            if (tm) tm->end(KK_OTHER, st, (double)sh.count * plan->n_coeff_rows * sizeof(float));
+        }
     } else {
         if (tm) tm->begin(KK_OTHER, st);
         LPP_CUDA(launch_sums<T>((const T*)sh.w, nullptr, sh.count, sums, SUM_W_SHAPES, -1, -1, st));
@@ -730,6 +738,10 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
             fs.n_src = 1;
             fs.src[0] = FusedSrc{LPP_SHAPES, coeff + (long long)plan->channels[ca0].coeff * stride, 0};
             fs.vals_b = (!il && ca0 + 1 < c1) ? coeff + (long long)plan->channels[ca0 + 1].coeff * stride : nullptr;
+            if (!plan->fp64) {
+                fs.amax_a = rmax + plan->channels[ca0].coeff;
+                fs.amax_b = fs.vals_b ? rmax + plan->channels[ca0 + 1].coeff : nullptr;
+            }
             fs.grid = gi;
             fa.slots[fa.n_slots++] = fs;
         }

@@ -140,7 +140,7 @@ __device__ __forceinline__ void stencil1(T u, int n, int P, int cells[3], T w[3]
 
 // Scatter one particle's weights (stencil at offset `shift` cells) into the tile part `im`.
 // The loops run to the fixed bound 3 with a guard on P so the stencil stays in registers.
-template <typename T>
+template <typename T, bool FIXED>
 __device__ __forceinline__ void scatter_one(T* tilef, int ld, int n, int P, T ux, T uy, T uz, T shift, int y0,
                                             int z0, int ty, int tz, T va, T vb, bool two_fields, int im) {
     int cx[3], cy[3], cz[3];
@@ -163,8 +163,15 @@ __device__ __forceinline__ void scatter_one(T* tilef, int ld, int n, int P, T ux
                 if (kx >= P) continue;
                 const int idx = 2 * (cx[kx] * ld + line);
                 const T ww = wyz * wx[kx];
-                atomicAdd(tilef + idx + im, va * ww);
-                if (two_fields) atomicAdd(tilef + idx + 1, vb * ww);
+                if constexpr (FIXED) {
+                    // va, vb arrive pre-scaled to the tile's fixed-point unit
+                    int* ti = reinterpret_cast<int*>(tilef);
+                    atomicAdd(ti + idx + im, __float2int_rn((float)(va * ww)));
+                    if (two_fields) atomicAdd(ti + idx + 1, __float2int_rn((float)(vb * ww)));
+                } else {
+                    atomicAdd(tilef + idx + im, va * ww);
+                    if (two_fields) atomicAdd(tilef + idx + 1, vb * ww);
+                }
             }
         }
     }
@@ -306,6 +313,20 @@ k_assign_xfft(FusedArgs<T> a) {
     const T alpha = (T)a.sums[SUM_ALPHA];
     const int P = a.scheme;
     const T* vb_ptr = (!a.interlace && sl.vals_b) ? static_cast<const T*>(sl.vals_b) : nullptr;
+    // fixed-point accumulation (FP32 channel slots): a cell sums at most `total` contributions
+    // of magnitude <= amax (the TSC/CIC weights are <= 1), so 2^30 / (total amax) units keep
+    // every cell and its rounding (<= total / 2 units) inside int32
+    const bool fixed = sizeof(T) == 4 && sl.amax_a != nullptr;
+    float fscale = 1.f, finv = 1.f;
+    if (fixed) {
+        float am = *sl.amax_a;
+        if (sl.amax_b) am = fmaxf(am, *sl.amax_b);
+        const float bound = (float)total * am;
+        if (bound > 0.f) {
+            fscale = 1073741824.f / bound;
+            finv = bound / 1073741824.f;
+        }
+    }
     int r = 0;
     for (int t = tid; t < total; t += S::THREADS) {
         while (r + 1 < nr && r_pref[r + 1] <= t) ++r;   // t increases, so the range index only grows
@@ -333,10 +354,23 @@ k_assign_xfft(FusedArgs<T> a) {
                 two = true;
             }
         }
-        scatter_one<T>(tilef, LD, N, P, ux, uy, uz, (T)0, y0, z0, TY, TZ, va, vb, two, 0);
-        if (a.interlace) scatter_one<T>(tilef, LD, N, P, ux, uy, uz, (T)0.5, y0, z0, TY, TZ, va, (T)0, false, 1);
+        if (fixed) {
+            va *= fscale;
+            vb *= fscale;
+            scatter_one<T, true>(tilef, LD, N, P, ux, uy, uz, (T)0, y0, z0, TY, TZ, va, vb, two, 0);
+            if (a.interlace) scatter_one<T, true>(tilef, LD, N, P, ux, uy, uz, (T)0.5, y0, z0, TY, TZ, va, (T)0, false, 1);
+        } else {
+            scatter_one<T, false>(tilef, LD, N, P, ux, uy, uz, (T)0, y0, z0, TY, TZ, va, vb, two, 0);
+            if (a.interlace) scatter_one<T, false>(tilef, LD, N, P, ux, uy, uz, (T)0.5, y0, z0, TY, TZ, va, (T)0, false, 1);
+        }
     }
     __syncthreads();
+    if (fixed) {
+        // fixed point back to floating point before the transform
+        const int* ti = reinterpret_cast<const int*>(tilef);
+        for (int i = tid; i < 2 * N * LD; i += S::THREADS) tilef[i] = (T)((float)ti[i] * finv);
+        __syncthreads();
+    }
     fft_columns<T, LOGN, false, S::IPT, LD>(tile, tid & (W - 1), tid >> ilog2(W), tw);
     for (int k = tid & (LPL - 1); k < nkept; k += LPL) {
         const int e = k <= a.nk_pos ? k : N - nkept + k;
