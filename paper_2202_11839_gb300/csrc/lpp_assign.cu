@@ -349,27 +349,45 @@ cudaError_t launch_assign(const AssignArgs<T>& a, int scheme, int interlace, cud
     return cudaGetLastError();
 }
 
-// Per-row maximum of |coefficient|: a grid-stride loop per row (blockIdx.y), a warp
-// reduction and one atomicMax on the float's bits (non-negative floats order like ints).
-__global__ void __launch_bounds__(256) k_rowmax(const float* __restrict__ coeff, long long stride, long long count,
-                                                float* __restrict__ rmax) {
+// Per-row statistics of the coefficients: rstat[2r] = max |c| (atomicMax on the float's
+// bits: non-negative floats order like ints) and rstat[2r + 1] = rms c, from a grid-stride
+// loop per row (blockIdx.y), warp reductions and FP64 sums of squares in rsq.
+__global__ void __launch_bounds__(256) k_rowstat(const float* __restrict__ coeff, long long stride, long long count,
+                                                 float* __restrict__ rstat, double* __restrict__ rsq) {
     const float* row = coeff + (long long)blockIdx.y * stride;
-    float m = 0.f;
+    float m = 0.f, qf = 0.f;   // per-thread sums cover count / (64 * 256) values: FP32 is plenty
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
-         i += (long long)gridDim.x * blockDim.x)
-        m = fmaxf(m, fabsf(row[i]));
+         i += (long long)gridDim.x * blockDim.x) {
+        const float v = row[i];
+        m = fmaxf(m, fabsf(v));
+        qf = fmaf(v, v, qf);
+    }
+    double q = (double)qf;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(reinterpret_cast<int*>(rmax) + blockIdx.y, __float_as_int(m));
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+        q += __shfl_down_sync(0xffffffffu, q, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (m > 0.f) atomicMax(reinterpret_cast<int*>(rstat) + 2 * blockIdx.y, __float_as_int(m));
+        if (q > 0.0) atomicAdd(rsq + blockIdx.y, q);
+    }
 }
 
-cudaError_t launch_rowmax(const float* coeff, long long stride, long long count, int rows, float* rmax,
-                          cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(rmax, 0, (size_t)rows * sizeof(float), st);
+__global__ void k_rowrms(const double* __restrict__ rsq, long long count, int rows, float* __restrict__ rstat) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < rows) rstat[2 * r + 1] = count > 0 ? (float)sqrt(rsq[r] / (double)count) : 0.f;
+}
+
+cudaError_t launch_rowstat(const float* coeff, long long stride, long long count, int rows, float* rstat,
+                           double* rsq, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(rstat, 0, (size_t)rows * 2 * sizeof(float), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(rsq, 0, (size_t)rows * sizeof(double), st);
     if (e != cudaSuccess || count == 0 || rows == 0) return e;
     long long bx = (count + 255) / 256;
     if (bx > 64) bx = 64;
-    k_rowmax<<<dim3((unsigned)bx, (unsigned)rows), 256, 0, st>>>(coeff, stride, count, rmax);
+    k_rowstat<<<dim3((unsigned)bx, (unsigned)rows), 256, 0, st>>>(coeff, stride, count, rstat, rsq);
+    k_rowrms<<<(rows + 127) / 128, 128, 0, st>>>(rsq, count, rows, rstat);
     return cudaGetLastError();
 }
 

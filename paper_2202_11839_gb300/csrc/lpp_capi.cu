@@ -67,7 +67,8 @@ struct lpp_plan_s {
     size_t off_perm = 0, off_counts = 0, off_cursor = 0;
     size_t off_wout = 0, off_wthr = 0;   // window multipoles: per-channel shell sums, thresholds
     size_t off_pmask = 0;                // [3][n] z planes reached per catalogue role
-    size_t off_rmax = 0;                 // [n_coeff_rows] max |coefficient| per row (FP32 plans)
+    size_t off_rmax = 0;                 // [n_coeff_rows][2] max |coefficient|, rms per row (FP32 plans)
+    size_t off_rsq = 0;                  // [n_coeff_rows] FP64 sums of squares
     int fty = 4, ftz = 4;
     int n_partner = 0;
     int out_rows = 0;
@@ -291,7 +292,8 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
     plan->off_counts = take((size_t)n * n * sizeof(int));
     plan->off_cursor = take((size_t)n * n * sizeof(int));
     plan->off_pmask = take((size_t)3 * n * sizeof(int));
-    plan->off_rmax = take((size_t)std::max(1, plan->n_coeff_rows) * sizeof(float));
+    plan->off_rmax = take((size_t)std::max(1, plan->n_coeff_rows) * 2 * sizeof(float));
+    plan->off_rsq = take((size_t)std::max(1, plan->n_coeff_rows) * sizeof(double));
     plan->off_wout = take((size_t)kWindowChannels * 256 * 2 * sizeof(double));
     plan->off_wthr = take(257 * sizeof(int));
     plan->off_partner = take((size_t)std::max(1, plan->n_partner) * n3 * cs);
@@ -572,7 +574,8 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         if (tm) tm->end(KK_COEFF, st, (double)sh.count * plan->es * (3 + 1 + 6 + plan->n_coeff_rows));
         if (!plan->fp64) {
             if (tm) tm->begin(KK_OTHER, st);
-            LPP_CUDA(launch_rowmax((const float*)coeff, stride, sh.count, plan->n_coeff_rows, rmax, st));
+            LPP_CUDA(launch_rowstat((const float*)coeff, stride, sh.count, plan->n_coeff_rows, rmax,
+                                    (double*)(plan->ws + plan->off_rsq), st));
             if (tm) tm->end(KK_OTHER, st, (double)sh.count * plan->n_coeff_rows * sizeof(float));
         }
     } else {
@@ -739,8 +742,8 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
             fs.src[0] = FusedSrc{LPP_SHAPES, coeff + (long long)plan->channels[ca0].coeff * stride, 0};
             fs.vals_b = (!il && ca0 + 1 < c1) ? coeff + (long long)plan->channels[ca0 + 1].coeff * stride : nullptr;
             if (!plan->fp64) {
-                fs.amax_a = rmax + plan->channels[ca0].coeff;
-                fs.amax_b = fs.vals_b ? rmax + plan->channels[ca0 + 1].coeff : nullptr;
+                fs.amax_a = rmax + 2 * plan->channels[ca0].coeff;
+                fs.amax_b = fs.vals_b ? rmax + 2 * plan->channels[ca0 + 1].coeff : nullptr;
             }
             fs.grid = gi;
             fa.slots[fa.n_slots++] = fs;

@@ -124,9 +124,10 @@ enum { ERRF_DOMAIN = 1, ERRF_POLE = 2, ERRF_OBSERVER = 4 };
 
 template <typename T>
 cudaError_t launch_coeffs(const CoeffArgs<T>& a, cudaStream_t st);
-// rmax[r] = max_i |coeff[r * stride + i]| over i < count for r < rows (rmax zeroed first)
-cudaError_t launch_rowmax(const float* coeff, long long stride, long long count, int rows, float* rmax,
-                          cudaStream_t st);
+// rstat[2r] = max_i |coeff[r * stride + i]|, rstat[2r + 1] = rms over i < count, for r < rows
+// (rsq: FP64 scratch of rows entries)
+cudaError_t launch_rowstat(const float* coeff, long long stride, long long count, int rows, float* rstat,
+                           double* rsq, cudaStream_t st);
 
 // plain weight sums of a catalogue: sums[s_w] += w, sums[s_w2] += w^2, sums[s_nw2] += nbar w^2
 template <typename T>
@@ -186,9 +187,9 @@ struct FusedSlot {
     int use_ylm;
     int yl_a, yn_a, yl_b, yn_b;
     double ynorm_a, ynorm_b;
-    // FP32 channel slots: max |value| of the field a (and b) rows; when set the tile is
-    // accumulated in 32-bit fixed point (integer shared-memory atomics) with a per-tile
-    // scale that no cell can overflow
+    // FP32 channel slots: (max |value|, rms value) of the field a (and b) rows; when set, a
+    // tile whose fixed-point unit is fine enough is accumulated in 32-bit fixed point
+    // (integer shared-memory atomics) with a per-tile scale that no cell can overflow
     const float* amax_a;
     const float* amax_b;
 };

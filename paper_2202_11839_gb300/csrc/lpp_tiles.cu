@@ -201,6 +201,9 @@ k_assign_xfft(FusedArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int r_begin[S::MAXR], r_pref[S::MAXR + 1], r_src[S::MAXR];
     __shared__ int n_ranges;
+    // particles per key row around the tile (fixed-point bound; rows of source 0)
+    __shared__ int rcount[TZ + 3][TY + 3];
+    __shared__ int wmax;
     c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
     c2<T>* tile = tw + N;
     T* tilef = reinterpret_cast<T*>(tile);
@@ -240,6 +243,7 @@ k_assign_xfft(FusedArgs<T> a) {
             }
             r_pref[nr] = acc;
             n_ranges = nr;
+            wmax = acc;   // every particle of the tile: a looser but valid per-cell bound
         }
         for (int i = tid; i < N; i += S::THREADS) tw[i] = a.tw[i];
         for (int i = tid; i < N * LD; i += S::THREADS) tile[i] = mk<T>((T)0, (T)0);
@@ -280,6 +284,31 @@ k_assign_xfft(FusedArgs<T> a) {
             r_pref[nr_inc] = cnt_inc;
             n_ranges = nr_inc;
         }
+        if (sl.amax_a != nullptr) {
+            // a cell (y, z) of the tile receives only from the key rows y-2..y+1, z-2..z+1:
+            // the largest such 4 x 4 window sum bounds the contributions of any one cell
+            if (lane < TZ + 3) {
+                const int* off = a.cat[sl.src[0].cat].off;
+                const int zr = (z0 - 2 + lane) & (N - 1);
+#pragma unroll
+                for (int dy = 0; dy < TY + 3; ++dy) {
+                    const int yr = (y0 - 2 + dy) & (N - 1);
+                    rcount[lane][dy] = off[zr * N + yr + 1] - off[zr * N + yr];
+                }
+            }
+            __syncwarp();
+            int wsum = 0;
+            if (lane < TY * TZ) {
+                const int ly = lane % TY, lz = lane / TY;   // cell (y0 + ly, z0 + lz): rows ly..ly+3
+#pragma unroll
+                for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+                    for (int b2 = 0; b2 < 4; ++b2) wsum += rcount[lz + a2][ly + b2];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) wsum = max(wsum, __shfl_down_sync(0xffffffffu, wsum, o));
+            if (lane == 0) wmax = wsum;
+        }
     } else {
         for (int i = tid - 32; i < N; i += S::THREADS - 32) tw[i] = a.tw[i];
         for (int i = tid - 32; i < N * LD; i += S::THREADS - 32) tile[i] = mk<T>((T)0, (T)0);
@@ -313,16 +342,26 @@ k_assign_xfft(FusedArgs<T> a) {
     const T alpha = (T)a.sums[SUM_ALPHA];
     const int P = a.scheme;
     const T* vb_ptr = (!a.interlace && sl.vals_b) ? static_cast<const T*>(sl.vals_b) : nullptr;
-    // fixed-point accumulation (FP32 channel slots): a cell sums at most `total` contributions
-    // of magnitude <= amax (the TSC/CIC weights are <= 1), so 2^30 / (total amax) units keep
-    // every cell and its rounding (<= total / 2 units) inside int32
-    const bool fixed = sizeof(T) == 4 && sl.amax_a != nullptr;
+    // fixed-point accumulation (FP32 channel slots): a cell sums at most wmax contributions
+    // (particles of its 4 x 4 key-row window) of magnitude <= amax (the TSC/CIC weights are
+    // <= 1), so 2^30 / (wmax amax) units keep every cell and its rounding (<= wmax units, two
+    // sub-grid stencils) inside int32.  The tile takes it only
+    // when that unit is at most 2^-16 of the rows' rms value, so that rounding each
+    // contribution to the unit costs no more than the FP32 sums it replaces; otherwise float
+    // atomics.
+    bool fixed = false;
     float fscale = 1.f, finv = 1.f;
-    if (fixed) {
-        float am = *sl.amax_a;
-        if (sl.amax_b) am = fmaxf(am, *sl.amax_b);
-        const float bound = (float)total * am;
-        if (bound > 0.f) {
+    if (sizeof(T) == 4 && sl.amax_a != nullptr) {
+        float am = sl.amax_a[0], rms = sl.amax_a[1];
+        if (sl.amax_b) {
+            am = fmaxf(am, sl.amax_b[0]);
+            rms = fminf(rms, sl.amax_b[1]);
+        }
+        const float bound = (float)wmax * am;
+        if (bound == 0.f) {
+            fixed = true;                        // every value is zero
+        } else if (bound * (1.f / 1073741824.f) <= rms * (1.f / 65536.f)) {
+            fixed = true;
             fscale = 1073741824.f / bound;
             finv = bound / 1073741824.f;
         }

@@ -12,7 +12,8 @@ ALL_MOMENTS = tuple(O.MOMENTS)
 
 
 def make_case(kind: str, n: int, count: int, seed: int, box: float = 300.0, n_rand: int = 0,
-              dtype=np.float64, separate_density: bool = False, gamma12: bool = False, zslab=None):
+              dtype=np.float64, separate_density: bool = False, gamma12: bool = False, zslab=None,
+              outlier: float = 0.0):
     """Small synthetic catalogues: uniform positions, random tensors (or gamma_1,2), optional
     randoms; with zslab = (a, b) every catalogue is confined to a <= z / box < b (so most z
     planes of the grid receive nothing)."""
@@ -27,6 +28,8 @@ def make_case(kind: str, n: int, count: int, seed: int, box: float = 300.0, n_ra
     pos = squeeze(S.uniform_positions(count, box, (lo, lo, lo), seed, 0, dtype))
     shape = rng.standard_normal((2 if gamma12 else 6, count)).astype(dtype)
     w = rng.uniform(0.5, 1.5, count).astype(dtype)
+    if outlier:
+        w[count // 3] *= dtype(outlier)   # one galaxy far heavier than the rest
     out = dict(pos=pos, w=w, shape=shape)
     if separate_density:
         out["dpos"] = squeeze(S.uniform_positions(count // 2 + 7, box, (lo, lo, lo), seed, 5, dtype))

@@ -65,6 +65,8 @@ CASES32 = {
     "tsc_interlaced_n32": (_cfg(32, 500.0, scheme=3, interlace=True), dict(count=6000)),
     "cic_randoms_n32": (_cfg(32, 500.0, scheme=2, frac=0.5), dict(count=4000, n_rand=12000)),
     "gamma12_n64_pruned": (_cfg(64, 800.0, scheme=3, interlace=True, frac=0.4, nb=6), dict(count=5000, gamma12=True)),
+    # one weight 1e4 times the others: coefficient maxima far above the typical value
+    "outlier_weight_n32": (_cfg(32, 500.0, scheme=3, interlace=True), dict(count=6000, outlier=1.0e4)),
     "zslab_randoms_n64": (_cfg(64, 800.0, scheme=3, interlace=True, frac=0.5), dict(count=6000, n_rand=12000,
                                                                                    zslab=(0.55, 0.7))),
 }
