@@ -64,7 +64,7 @@ struct lpp_plan_s {
     size_t off_partner = 0, off_grids = 0, off_stage[3] = {0, 0, 0};
     // pencil-sorted catalogues: key, cell coordinates, weights, key offsets; shapes permutation
     size_t off_key[3] = {0, 0, 0}, off_su[3] = {0, 0, 0}, off_sw[3] = {0, 0, 0}, off_koff[3] = {0, 0, 0};
-    size_t off_perm = 0, off_counts = 0, off_cursor = 0;
+    size_t off_perm = 0, off_counts = 0, off_cursor = 0, off_scan = 0;
     size_t off_wout = 0, off_wthr = 0;   // window multipoles: per-channel shell sums, thresholds
     size_t off_pmask = 0;                // [3][n] z planes reached per catalogue role
     size_t off_rmax = 0;                 // [n_coeff_rows][2] max |coefficient|, rms per row (FP32 plans)
@@ -291,6 +291,7 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
     plan->off_perm = take((size_t)caps[0] * sizeof(int));
     plan->off_counts = take((size_t)n * n * sizeof(int));
     plan->off_cursor = take((size_t)n * n * sizeof(int));
+    plan->off_scan = take(1024 * sizeof(int));
     plan->off_pmask = take((size_t)3 * n * sizeof(int));
     plan->off_rmax = take((size_t)std::max(1, plan->n_coeff_rows) * 2 * sizeof(float));
     plan->off_rsq = take((size_t)std::max(1, plan->n_coeff_rows) * sizeof(double));
@@ -507,7 +508,8 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         LPP_CUDA(launch_pencil_sort<T>((const T*)c.pos, (const T*)c.w, c.count, caps[role], n, plan->box,
                                        plan->d.origin, (int*)(plan->ws + plan->off_key[role]),
                                        (int*)(plan->ws + plan->off_counts), (int*)(plan->ws + plan->off_koff[role]),
-                                       (int*)(plan->ws + plan->off_cursor), (T*)(plan->ws + plan->off_su[role]),
+                                       (int*)(plan->ws + plan->off_cursor), (int*)(plan->ws + plan->off_scan),
+                                       (T*)(plan->ws + plan->off_su[role]),
                                        (T*)(plan->ws + plan->off_sw[role]), role == LPP_SHAPES ? perm : nullptr, err,
                                        st));
         if (tm) tm->end(KK_OTHER, st, (double)c.count * (plan->es * 8 + 12));
@@ -926,7 +928,8 @@ static lpp_status run_window(lpp_plan_t plan, int nb, const double* s_edges, dou
     LPP_CUDA(launch_pencil_sort<T>((const T*)ra.pos, (const T*)ra.w, ra.count, cap, n, plan->box, plan->d.origin,
                                    (int*)(plan->ws + plan->off_key[LPP_RANDOMS]), (int*)(plan->ws + plan->off_counts),
                                    (int*)(plan->ws + plan->off_koff[LPP_RANDOMS]),
-                                   (int*)(plan->ws + plan->off_cursor), (T*)(plan->ws + plan->off_su[LPP_RANDOMS]),
+                                   (int*)(plan->ws + plan->off_cursor), (int*)(plan->ws + plan->off_scan),
+                                   (T*)(plan->ws + plan->off_su[LPP_RANDOMS]),
                                    (T*)(plan->ws + plan->off_sw[LPP_RANDOMS]), nullptr, err, st));
     // forward transforms keep every frequency; the inverse keeps the separations of the shells
     const FftGeom gfull = fft_geometry(n, n / 2 - 1, n / 2);

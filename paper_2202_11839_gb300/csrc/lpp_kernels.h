@@ -215,8 +215,8 @@ cudaError_t launch_plane_mask(const int* off0, const int* off1, const int* off2,
                               int* pmask, cudaStream_t st);
 template <typename T>
 cudaError_t launch_pencil_sort(const T* pos, const T* w, long long count, long long cap, int n, double box,
-                               const double origin[3], int* key, int* counts, int* off, int* cursor, T* su, T* sw,
-                               int* perm, int* err, cudaStream_t st);
+                               const double origin[3], int* key, int* counts, int* off, int* cursor, int* scan_tmp,
+                               T* su, T* sw, int* perm, int* err, cudaStream_t st);
 template <typename T>
 cudaError_t launch_assign_xfft(const FusedArgs<T>& a, cudaStream_t st);
 

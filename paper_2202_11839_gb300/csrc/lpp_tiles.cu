@@ -45,30 +45,71 @@ __global__ void __launch_bounds__(256) k_pencil_count(const T* __restrict__ pos,
     }
 }
 
-// Exclusive scan of counts[0..nk) into off[0..nk] and cursor[0..nk) (one CTA of 1024 threads).
-__global__ void __launch_bounds__(1024) k_scan_offsets(const int* __restrict__ counts, int nk, int* __restrict__ off,
-                                                       int* __restrict__ cursor) {
-    __shared__ long long part[1024];
-    const int t = threadIdx.x;
-    const int chunk = (nk + 1023) / 1024;
-    const int b = t * chunk, e = min(nk, b + chunk);
-    long long s = 0;
-    for (int i = b; i < e; ++i) s += counts[i];
-    part[t] = s;
+// Exclusive scan of counts[0..nk) into off[0..nk] and cursor[0..nk) in three steps:
+// segments of 2048 keys per CTA (local exclusive prefix and the segment total), one CTA's
+// scan of the segment totals (at most 512 of them for n <= 1024), and the add.
+constexpr int kScanSeg = 2048;   // keys per CTA (256 threads x 8)
+
+__global__ void __launch_bounds__(256) k_scan_part(const int* __restrict__ counts, int nk, int* __restrict__ off,
+                                                   int* __restrict__ bsum) {
+    __shared__ int wsum[8];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int base = blockIdx.x * kScanSeg + t * 8;
+    int v[8], s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        v[k] = base + k < nk ? counts[base + k] : 0;
+        s += v[k];
+    }
+    int inc = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += o;
+    }
+    if (lane == 31) wsum[wid] = inc;
     __syncthreads();
-    for (int d = 1; d < 1024; d <<= 1) {
-        const long long v = t >= d ? part[t - d] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
+    int wpre = 0;
+    for (int w = 0; w < wid; ++w) wpre += wsum[w];
+    int run = wpre + inc - s;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (base + k < nk) off[base + k] = run;
+        run += v[k];
     }
-    long long run = part[t] - s;  // exclusive prefix of this chunk
-    for (int i = b; i < e; ++i) {
-        off[i] = (int)run;
-        cursor[i] = (int)run;
-        run += counts[i];
+    if (t == 255) bsum[blockIdx.x] = wpre + inc;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(int* __restrict__ bsum, int nb, int* __restrict__ total) {
+    __shared__ int wsum[32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int s = t < nb ? bsum[t] : 0;
+    int inc = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += o;
     }
-    if (t == 1023) off[nk] = (int)part[1023];
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    int wpre = 0;
+    for (int w = 0; w < wid; ++w) wpre += wsum[w];
+    if (t < nb) bsum[t] = wpre + inc - s;
+    if (t == 1023) *total = wpre + inc;
+}
+
+__global__ void __launch_bounds__(256) k_scan_add(const int* __restrict__ bsum, int nk, int* __restrict__ off,
+                                                  int* __restrict__ cursor) {
+    const int add = bsum[blockIdx.x];
+    const int base = blockIdx.x * kScanSeg;
+    for (int k = threadIdx.x; k < kScanSeg; k += 256) {
+        const int i = base + k;
+        if (i < nk) {
+            const int o = off[i] + add;
+            off[i] = o;
+            cursor[i] = o;
+        }
+    }
 }
 
 template <typename T>
@@ -91,8 +132,8 @@ __global__ void __launch_bounds__(256) k_pencil_scatter(const T* __restrict__ po
 
 template <typename T>
 cudaError_t launch_pencil_sort(const T* pos, const T* w, long long count, long long cap, int n, double box,
-                               const double origin[3], int* key, int* counts, int* off, int* cursor, T* su, T* sw,
-                               int* perm, int* err, cudaStream_t st) {
+                               const double origin[3], int* key, int* counts, int* off, int* cursor, int* scan_tmp,
+                               T* su, T* sw, int* perm, int* err, cudaStream_t st) {
     const int nk = n * n;
     cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)nk * sizeof(int), st);
     if (e != cudaSuccess) return e;
@@ -102,7 +143,12 @@ cudaError_t launch_pencil_sort(const T* pos, const T* w, long long count, long l
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
     if (count > 0) k_pencil_count<T><<<(int)blocks, 256, 0, st>>>(pos, count, n, ih, ox, oy, oz, key, counts, err);
-    k_scan_offsets<<<1, 1024, 0, st>>>(counts, nk, off, cursor);
+    // segment totals in scan_tmp (at most 1024 entries: nk <= 1024^2 = 512 segments)
+    const int nb = (nk + kScanSeg - 1) / kScanSeg;
+    int* bsum = scan_tmp;
+    k_scan_part<<<nb, 256, 0, st>>>(counts, nk, off, bsum);
+    k_scan_top<<<1, 1024, 0, st>>>(bsum, nb, off + nk);
+    k_scan_add<<<nb, 256, 0, st>>>(bsum, nk, off, cursor);
     if (count > 0)
         k_pencil_scatter<T><<<(int)blocks, 256, 0, st>>>(pos, w, count, cap, ih, ox, oy, oz, key, cursor, su, sw,
                                                          perm);
@@ -480,10 +526,10 @@ cudaError_t launch_assign_xfft(const FusedArgs<T>& a, cudaStream_t st) {
 }
 
 template cudaError_t launch_pencil_sort<float>(const float*, const float*, long long, long long, int, double,
-                                               const double*, int*, int*, int*, int*, float*, float*, int*, int*,
+                                               const double*, int*, int*, int*, int*, int*, float*, float*, int*, int*,
                                                cudaStream_t);
 template cudaError_t launch_pencil_sort<double>(const double*, const double*, long long, long long, int, double,
-                                                const double*, int*, int*, int*, int*, double*, double*, int*, int*,
+                                                const double*, int*, int*, int*, int*, int*, double*, double*, int*, int*,
                                                 cudaStream_t);
 template cudaError_t launch_assign_xfft<float>(const FusedArgs<float>&, cudaStream_t);
 template cudaError_t launch_assign_xfft<double>(const FusedArgs<double>&, cudaStream_t);
