@@ -69,6 +69,7 @@ struct lpp_plan_s {
     size_t off_pmask = 0;                // [3][n] z planes reached per catalogue role
     size_t off_rmax = 0;                 // [n_coeff_rows][2] max |coefficient|, rms per row (FP32 plans)
     size_t off_rsq = 0;                  // [n_coeff_rows] FP64 sums of squares
+    size_t off_trows = 0;                // [2][256] z-tile rows to visit, then [2] counts
     int fty = 4, ftz = 4;
     int n_partner = 0;
     int out_rows = 0;
@@ -295,6 +296,7 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
     plan->off_pmask = take((size_t)3 * n * sizeof(int));
     plan->off_rmax = take((size_t)std::max(1, plan->n_coeff_rows) * 2 * sizeof(float));
     plan->off_rsq = take((size_t)std::max(1, plan->n_coeff_rows) * sizeof(double));
+    plan->off_trows = take((2 * 256 + 2) * sizeof(int));
     plan->off_wout = take((size_t)kWindowChannels * 256 * 2 * sizeof(double));
     plan->off_wthr = take(257 * sizeof(int));
     plan->off_partner = take((size_t)std::max(1, plan->n_partner) * n3 * cs);
@@ -522,6 +524,16 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
     LPP_CUDA(launch_plane_mask((const int*)(plan->ws + plan->off_koff[0]), (const int*)(plan->ws + plan->off_koff[1]),
                                (const int*)(plan->ws + plan->off_koff[2]), 1, plan->cat[LPP_DENSITY].set ? 1 : 0,
                                has_rand ? 1 : 0, n, pmask, st));
+    // the z-tile rows the fused passes visit: channel slots (shapes) and the partner slots
+    int* trows = (int*)(plan->ws + plan->off_trows);
+    int* tcount = trows + 512;
+    const int part_bits = (1 << LPP_SHAPES) | (plan->cat[LPP_DENSITY].set ? 1 << LPP_DENSITY : 0) |
+                          (has_rand ? 1 << LPP_RANDOMS : 0);
+    const bool use_rows = n / plan->ftz <= 256;
+    if (use_rows) {
+        LPP_CUDA(launch_tile_rows(pmask, 1 << LPP_SHAPES, n, plan->ftz, trows, tcount, st));
+        LPP_CUDA(launch_tile_rows(pmask, part_bits, n, plan->ftz, trows + 256, tcount + 1, st));
+    }
     // timing only: which planes are reached, for the byte counts of the skipping kernels
     // (one small synchronisation per estimate)
     std::vector<int> hmask;
@@ -707,6 +719,8 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
             fa.slots[fa.n_slots++] = dsl;
             parts += de.count + (has_rand ? ra.count : 0);
         }
+        fa.trows = use_rows ? trows + 256 : nullptr;
+        fa.trow_count = use_rows ? tcount + 1 : nullptr;
         { lpp_status s0 = assign_fused(parts); if (s0 != LPP_OK) return s0; }
         FftGeom gp = geom;
         gp.pmask = pmask;
@@ -763,6 +777,8 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
             cc.ynorm = ylm_norm_scaled(ch.L, ch.n);
             if (ch.kind == KIND_CROSS) cb.has_d = 1; else cb.has_g = 1;
         }
+        fa.trows = use_rows ? trows : nullptr;
+        fa.trow_count = use_rows ? tcount : nullptr;
         { lpp_status s0 = assign_fused(sh.count); if (s0 != LPP_OK) return s0; }
         FftGeom gc = geom;
         gc.pmask = pmask;

@@ -206,11 +206,16 @@ struct FusedArgs {
     const double* sums;
     double observer[3], origin[3], h;   // for the harmonic weights
     const int* pmask;                    // [3][n] planes reached per role, or null (write every pencil)
+    const int* trows;                    // z-tile rows to visit (persistent grid), or null (all tiles)
+    const int* trow_count;
 };
 
 void fused_geometry(int n, size_t elem_bytes, int* ty, int* tz, int* ipt, int* threads, size_t* smem);
 // pmask[r][z] = 1 when a particle of role r (set[r] != 0) sits in a key row f with
 // z - 2 <= f <= z + 1 (mod n): the planes its CIC/TSC stencils (interlaced or not) reach.
+// rows[0 .. *count) = the z-tile rows (tz planes each) holding a plane reached by a role in
+// bits (n / tz <= 256)
+cudaError_t launch_tile_rows(const int* pmask, int bits, int n, int tz, int* rows, int* count, cudaStream_t st);
 cudaError_t launch_plane_mask(const int* off0, const int* off1, const int* off2, int set0, int set1, int set2, int n,
                               int* pmask, cudaStream_t st);
 template <typename T>

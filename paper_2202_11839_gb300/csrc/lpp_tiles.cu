@@ -15,6 +15,8 @@
 // never read back for an x pass.
 #include <string.h>
 
+#include <algorithm>
+
 #include "lpp_internal.h"
 #include "lpp_kernels.h"
 #include "lpp_fft_dev.cuh"
@@ -236,12 +238,13 @@ struct FusedShape {
     static constexpr int MAXR = 2 * 2 * (TZ + 3);   // key ranges: sources x z rows x (1 or 2)
     // resident CTAs per SM the register budget is sized for (shared memory allows 3 at
     // n = 512 in FP32)
-    static constexpr int MINB = (sizeof(T) == 4 && LOGN == 9) ? 3 : 1;
+    static constexpr int MINB = (sizeof(T) == 4 && LOGN == 9) ? 3 : ((sizeof(T) == 4 && LOGN == 8) ? 2 : 1);
 };
 
+// One tile (tile_y, tile_z) of TY x TZ pencils of the slot blockIdx.y: particle ranges,
+// scatter, x transform, store of the kept x frequencies.  Every return is CTA-uniform.
 template <typename T, int LOGN>
-__global__ void __launch_bounds__(FusedShape<T, LOGN>::THREADS, FusedShape<T, LOGN>::MINB)
-k_assign_xfft(FusedArgs<T> a) {
+__device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int tile_y, int tile_z) {
     using S = FusedShape<T, LOGN>;
     constexpr int N = S::N, TY = S::TY, TZ = S::TZ, W = S::W, LD = S::LD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -254,8 +257,8 @@ k_assign_xfft(FusedArgs<T> a) {
     c2<T>* tile = tw + N;
     T* tilef = reinterpret_cast<T*>(tile);
     const int tid = threadIdx.x;
-    const int y0 = (blockIdx.x & (N / TY - 1)) * TY;
-    const int z0 = (blockIdx.x >> (LOGN - ilog2(TY))) * TZ;
+    const int y0 = tile_y * TY;
+    const int z0 = tile_z * TZ;
     const FusedSlot& sl = a.slots[blockIdx.y];
     c2<T>* out = a.grids + (size_t)sl.grid * a.grid_stride + ((size_t)z0 * N + y0) * N;
 
@@ -498,13 +501,65 @@ void fused_geometry(int n, size_t elem_bytes, int* ty, int* tz, int* ipt, int* t
     *smem = (size_t)(n + n * (w + 1)) * 2 * elem_bytes;
 }
 
+// Without a tile-row list one CTA per tile; with one (trows: z-tile rows that contain a
+// plane some particle reaches, *trow_count of them) a persistent grid walks those rows' tiles.
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(FusedShape<T, LOGN>::THREADS, FusedShape<T, LOGN>::MINB)
+k_assign_xfft(FusedArgs<T> a) {
+    using S = FusedShape<T, LOGN>;
+    constexpr int NTY = S::N / S::TY;
+    if (a.trows == nullptr) {
+        fused_tile<T, LOGN>(a, blockIdx.x % NTY, blockIdx.x / NTY);
+        return;
+    }
+    const int total = *a.trow_count * NTY;
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        fused_tile<T, LOGN>(a, t % NTY, a.trows[t / NTY]);
+        __syncthreads();   // the tile's shared memory is reused by the next one
+    }
+}
+
+// Tile rows (of tz planes) that contain a plane reached by a role in `bits`; one CTA.
+__global__ void __launch_bounds__(256) k_tile_rows(const int* __restrict__ pmask, int bits, int n, int tz,
+                                                   int* __restrict__ rows, int* __restrict__ count) {
+    __shared__ int woff[8];
+    const int r = threadIdx.x, lane = r & 31, wid = r >> 5;
+    int live = 0;
+    if (r < n / tz) {
+        for (int z = r * tz; z < r * tz + tz; ++z)
+            for (int q = 0; q < 3; ++q)
+                if (bits & (1 << q)) live |= pmask[q * n + z];
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, live != 0);
+    if (lane == 0) woff[wid] = __popc(b);
+    __syncthreads();
+    int base = 0;
+    for (int w = 0; w < wid; ++w) base += woff[w];
+    if (live) rows[base + __popc(b & ((1u << lane) - 1u))] = r;
+    if (r == 255) *count = base + __popc(b);
+}
+
+cudaError_t launch_tile_rows(const int* pmask, int bits, int n, int tz, int* rows, int* count, cudaStream_t st) {
+    if (n / tz > 256) return cudaErrorInvalidValue;
+    k_tile_rows<<<1, 256, 0, st>>>(pmask, bits, n, tz, rows, count);
+    return cudaGetLastError();
+}
+
 template <typename T, int LOGN>
 static cudaError_t launch_fused_n(const FusedArgs<T>& a, int n_tiles, cudaStream_t st) {
     using S = FusedShape<T, LOGN>;
     if (a.ty != S::TY || a.tz != S::TZ) return cudaErrorInvalidConfiguration;
     const size_t smem = (size_t)(S::N + S::N * S::LD) * sizeof(c2<T>);
     cudaFuncSetAttribute(k_assign_xfft<T, LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_assign_xfft<T, LOGN><<<dim3(n_tiles, a.n_slots), S::THREADS, smem, st>>>(a);
+    int grid = n_tiles;
+    if (a.trows) {
+        // persistent: about two resident waves over all slots
+        int dev = 0, sms = 152;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int per_sm = std::max(1, (int)((227 * 1024) / (smem + 1024)));
+        grid = std::max(1, std::min(n_tiles, 2 * sms * per_sm / std::max(1, a.n_slots)));
+    }
+    k_assign_xfft<T, LOGN><<<dim3(grid, a.n_slots), S::THREADS, smem, st>>>(a);
     return cudaGetLastError();
 }
 
