@@ -238,7 +238,7 @@ struct FusedShape {
     static constexpr int MAXR = 2 * 2 * (TZ + 3);   // key ranges: sources x z rows x (1 or 2)
     // resident CTAs per SM the register budget is sized for (shared memory allows 3 at
     // n = 512 in FP32)
-    static constexpr int MINB = (sizeof(T) == 4 && LOGN == 9) ? 3 : ((sizeof(T) == 4 && LOGN == 8) ? 2 : 1);
+    static constexpr int MINB = (sizeof(T) == 4 && (LOGN == 9 || LOGN == 8)) ? 2 : 1;
 };
 
 // One tile (tile_y, tile_z) of TY x TZ pencils of the slot blockIdx.y: particle ranges,
