@@ -22,7 +22,7 @@ namespace lpp {
 // MODE 2: pencils along z (W consecutive kept x columns at a fixed kept y)
 // Offsets inside one grid fit in 32 bits (n <= 1024); the tile base is a 64-bit pointer.
 template <typename T, int LOGN, bool INV, int MODE>
-__global__ void __launch_bounds__(PassShape<LOGN>::THREADS, sizeof(T) == 4 ? 2 : 1) k_fft_pass(c2<T>* __restrict__ data,
+__global__ void __launch_bounds__(PassShape<LOGN>::THREADS, sizeof(T) == 4 ? (LOGN == 9 ? 3 : 2) : 1) k_fft_pass(c2<T>* __restrict__ data,
                                                                       const c2<T>* __restrict__ twg, FftGeom g) {
     using S = PassShape<LOGN>;
     constexpr int N = S::N, W = S::W, LD = S::LD;

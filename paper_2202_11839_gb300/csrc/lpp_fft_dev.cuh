@@ -140,7 +140,7 @@ struct PassShape {
     static constexpr int W0 = (8192 >> LOGN) > 32 ? 32 : (8192 >> LOGN);
     static constexpr int W = W0 > N ? N : W0;
     static constexpr int LOGW = ilog2(W);
-    static constexpr int IPT = LOGN >= 8 ? 2 : 1;
+    static constexpr int IPT = LOGN == 9 ? 4 : (LOGN >= 8 ? 2 : 1);
     static constexpr int THREADS = W * N / (8 * IPT);
     static constexpr int LD = W + 1;
     static constexpr int PER = N * W / THREADS;   // tile elements per thread
