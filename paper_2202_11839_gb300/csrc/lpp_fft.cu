@@ -72,22 +72,14 @@ __global__ void __launch_bounds__(PassShape<LOGN>::THREADS, sizeof(T) == 4 ? (LO
         }
     } else {
         if (MODE == 1 && g.pmask && g.gmask[blockIdx.y]) {
-            // a z plane that no particle of the grid's roles reaches: its pencils are zero
-            // (the fused assignment did not store them); write the kept zeros directly
+            // a z plane that no particle of the grid's roles reaches: its pencils are zero;
+            // neither the fused assignment nor this pass stores it
             const int z = tile_id / g.ntx;
             int hit = 0;
 #pragma unroll
             for (int r = 0; r < 3; ++r)
                 if (g.gmask[blockIdx.y] & (1 << r)) hit |= g.pmask[r * N + z];
-            if (!hit) {
-                constexpr int ROWS = S::THREADS / W;
-                const int c = tid & (W - 1), e0 = tid >> S::LOGW;
-                c2<T>* gp = base + (size_t)e0 * N + c;
-#pragma unroll
-                for (int k = 0; k < S::PER; ++k)
-                    if (kept(e0 + k * ROWS, N, g.nk_pos, g.nk_neg)) gp[(size_t)k * ROWS * N] = mk<T>((T)0, (T)0);
-                return;
-            }
+            if (!hit) return;   // nothing stored: the z pass reads zeros for this plane
         }
         // rows e0 + k ROWS of W consecutive x values: one base pointer, compile-time strides
         constexpr int ROWS = S::THREADS / W;
@@ -97,10 +89,30 @@ __global__ void __launch_bounds__(PassShape<LOGN>::THREADS, sizeof(T) == 4 ? (LO
         c2<T>* sp = tile + e0 * LD + c;
         // z pencils: 64-bit strides; two batches of loads keep the live registers under the cap
         constexpr int KB = (MODE == 2 && S::PER > 8) ? 8 : S::PER;
+        static_assert(S::PER <= 32, "one liveness bit per loaded row");
+        // z pencils: entries on planes no particle reaches are zero and are not loaded
+        unsigned live = 0xffffffffu;
+        if (MODE == 2 && g.pmask && g.gmask[blockIdx.y]) {
+            const int gm = g.gmask[blockIdx.y];
+            live = 0u;
+#pragma unroll
+            for (int k = 0; k < S::PER; ++k) {
+                const int z = e0 + k * ROWS;
+                int hit = 0;
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+                    if (gm & (1 << r)) hit |= __ldg(g.pmask + r * N + z);
+                live |= (hit ? 1u : 0u) << k;
+            }
+        }
 #pragma unroll 1
         for (int k0 = 0; k0 < S::PER; k0 += KB) {
 #pragma unroll
-            for (int k = k0; k < k0 + KB; ++k) sp[k * ROWS * LD] = gp[(size_t)k * ROWS * ES];
+            for (int k = k0; k < k0 + KB; ++k) {
+                c2<T> v = mk<T>((T)0, (T)0);
+                if ((live >> k) & 1u) v = gp[(size_t)k * ROWS * ES];
+                sp[k * ROWS * LD] = v;
+            }
         }
         __syncthreads();
         fft_columns<T, LOGN, INV, S::IPT, LD>(tile, tid & (W - 1), tid >> S::LOGW, tw);
@@ -153,10 +165,11 @@ static cudaError_t launch_passes(c2<T>* data, int n_grids, const c2<T>* tw, cons
     }
     if (timer) timer->begin(KK_FFT, st);
     k_fft_pass<T, LOGN, INV, 1><<<dim3(g.ntx * N, n_grids), S::THREADS, smem, st>>>(data, tw, g);
-    if (timer) timer->end(KK_FFT, st, n_grids * n3 * es * xcols * ((double)g.yread_frac + keep));
+    // y: only the reached planes are read and written; z: their entries are read, all written
+    if (timer) timer->end(KK_FFT, st, n_grids * n3 * es * xcols * (double)g.yread_frac * (1.0 + keep));
     if (timer) timer->begin(KK_FFT, st);
     k_fft_pass<T, LOGN, INV, 2><<<dim3(g.ntx * g.nky, n_grids), S::THREADS, smem, st>>>(data, tw, g);
-    if (timer) timer->end(KK_FFT, st, n_grids * n3 * es * xcols * keep * (1.0 + keep));
+    if (timer) timer->end(KK_FFT, st, n_grids * n3 * es * xcols * keep * ((double)g.yread_frac + keep));
     return cudaGetLastError();
 }
 
