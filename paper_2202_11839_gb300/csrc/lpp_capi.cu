@@ -724,6 +724,7 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         { lpp_status s0 = assign_fused(parts); if (s0 != LPP_OK) return s0; }
         FftGeom gp = geom;
         gp.pmask = pmask;
+        gp.q_max = plan->thr[nb];
         double fr = 0.0;
         for (int i = 0; i < fa.n_slots; ++i) {
             gp.gmask[fa.slots[i].grid] = slot_bits(fa.slots[i]);
@@ -782,6 +783,7 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         { lpp_status s0 = assign_fused(sh.count); if (s0 != LPP_OK) return s0; }
         FftGeom gc = geom;
         gc.pmask = pmask;
+        gc.q_max = plan->thr[nb];
         for (int i = 0; i < ngr; ++i) gc.gmask[i] = 1 << LPP_SHAPES;
         gc.yread_frac = (float)plane_frac(1 << LPP_SHAPES);
         LPP_CUDA(fft_yz<T>(grids, ngr, n, tw, gc, false, st, tm));

@@ -11,6 +11,8 @@
 // range f in [-nk_neg, nk_pos] per axis, the x pass writes only kept x, the y pass
 // runs only on kept x columns and writes kept y, and the z pass runs only on kept
 // (x, y) columns and writes kept z.  Values outside the kept range are left stale.
+#include <algorithm>
+
 #include "lpp_internal.h"
 #include "lpp_kernels.h"
 #include "lpp_fft_dev.cuh"
@@ -49,6 +51,17 @@ __global__ void __launch_bounds__(PassShape<LOGN>::THREADS, sizeof(T) == 4 ? (LO
             es = N;
         } else {
             const int y = (o <= g.nk_pos) ? o : N - (g.nky - o);
+            if (g.q_max > 0) {
+                // columns outside the last shell in (fx, fy) for every fz: nothing to transform
+                const int fy = y < N / 2 ? y : y - N;
+                int m2 = 0x7fffffff;
+                for (int c = 0; c < W; ++c) {
+                    const int x = x0 + c;
+                    const int fx = x < N / 2 ? x : x - N;
+                    m2 = min(m2, fx * fx);
+                }
+                if (m2 + fy * fy >= g.q_max) return;
+            }
             base += (size_t)y * N + x0;
             es = N2;
         }
@@ -169,7 +182,29 @@ static cudaError_t launch_passes(c2<T>* data, int n_grids, const c2<T>* tw, cons
     if (timer) timer->end(KK_FFT, st, n_grids * n3 * es * xcols * (double)g.yread_frac * (1.0 + keep));
     if (timer) timer->begin(KK_FFT, st);
     k_fft_pass<T, LOGN, INV, 2><<<dim3(g.ntx * g.nky, n_grids), S::THREADS, smem, st>>>(data, tw, g);
-    if (timer) timer->end(KK_FFT, st, n_grids * n3 * es * xcols * keep * ((double)g.yread_frac + keep));
+    if (timer) {
+        // the z pass transforms the columns that some shell can use
+        double zfrac = 1.0;
+        if (g.q_max > 0) {
+            long long live = 0, all = 0;
+            for (int o = 0; o < g.nky; ++o) {
+                const int y = (o <= g.nk_pos) ? o : N - (g.nky - o);
+                const int fy = y < N / 2 ? y : y - N;
+                for (int i = 0; i < g.ntx; ++i) {
+                    const int x0 = (g.ntx == N / W || i < g.nlo) ? i * W : N - (g.ntx - i) * W;
+                    int m2 = 0x7fffffff;
+                    for (int c = 0; c < W; ++c) {
+                        const int fx = (x0 + c) < N / 2 ? x0 + c : x0 + c - N;
+                        m2 = std::min(m2, fx * fx);
+                    }
+                    ++all;
+                    live += (m2 + fy * fy < g.q_max);
+                }
+            }
+            zfrac = all ? (double)live / all : 1.0;
+        }
+        timer->end(KK_FFT, st, n_grids * n3 * es * xcols * keep * zfrac * ((double)g.yread_frac + keep));
+    }
     return cudaGetLastError();
 }
 

@@ -62,6 +62,9 @@ struct FftGeom {
     const int* pmask = nullptr;
     int gmask[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     float yread_frac = 1.0f;   // host bookkeeping: fraction of z planes the y pass reads
+    // z pass: skip (kx, ky) columns whose every mode has |f|^2 >= q_max (beyond the last
+    // shell; never read by the combine); 0 transforms every column
+    int q_max = 0;
 };
 
 int fft_tile_width(int n);
