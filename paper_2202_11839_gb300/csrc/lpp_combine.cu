@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(1024) k_combine(CombineArgs<T> a) {
         const int yp = (n - y) & (n - 1);
         const int fz = freq_of<T>(z, n), fy = freq_of<T>(y, n);
         const int fzp = freq_of<T>(zp, n), fyp = freq_of<T>(yp, n);
+        if (fy * fy + fz * fz >= thr[nb]) continue;   // no mode of this row lies in a shell (CTA-uniform)
 
         // shell label (contiguous along the warp) and whether this lane owns the pair
         const int q2 = fx * fx + fy * fy + fz * fz;
