@@ -19,7 +19,7 @@ namespace lpp {
 template <typename T>
 __device__ __forceinline__ T horner(const T* c, int nc, T x) {
     T r = (T)0;
-    for (int i = nc - 1; i >= 0; --i) r = r * x + __ldg(c + i);
+    for (int i = nc - 1; i >= 0; --i) r = r * x + c[i];
     return r;
 }
 
@@ -43,20 +43,29 @@ __device__ __forceinline__ void sky_frame(const T xh[3], const double pole[3], T
     et[2] = ep[0] * xh[1] - ep[1] * xh[0];
 }
 
+// sm: the block's shared copy of the quadrature directions, tables and polynomials (in the
+// order of coeff_smem_words)
 template <typename T, int L, bool HAS_IM>
 __device__ __forceinline__ void project_group(const CoeffArgs<T>& a, const CoeffGroup& g, long long i, T wgt,
-                                              T gre, T gim, const T et[3], const T ep[3], const T xh[3]) {
+                                              T gre, T gim, const T et[3], const T ep[3], const T xh[3],
+                                              const T* sm) {
     constexpr int NH = 2 * L + 1;
-    const int q = L / 2 - 1;
+    constexpr int q = L / 2 - 1;
+    int o = 0;
+#pragma unroll
+    for (int qq = 0; qq < q; ++qq) o += a.quad_S[qq] * (3 + 2 * (2 * (qq + 1)) + 1);
     const int S = a.quad_S[q];
-    const T* dirs = a.quad_dirs[q];
-    const T* tab = a.quad_tab[q];
-    const T* poly = a.polys + g.poly;
+    const T* dirs = sm + o;
+    const T* tab = dirs + 3 * S;
+    int op = 0;
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) op += a.quad_S[qq] * (3 + 2 * (2 * (qq + 1)) + 1);
+    const T* poly = sm + op + g.poly;
     T accr[NH], acci[NH];
 #pragma unroll
     for (int n = 0; n < NH; ++n) { accr[n] = (T)0; acci[n] = (T)0; }
     for (int s = 0; s < S; ++s) {
-        const T kx = __ldg(dirs + 3 * s), ky = __ldg(dirs + 3 * s + 1), kz = __ldg(dirs + 3 * s + 2);
+        const T kx = dirs[3 * s], ky = dirs[3 * s + 1], kz = dirs[3 * s + 2];
         const T mu = kx * xh[0] + ky * xh[1] + kz * xh[2];
         const T pm = horner(poly, g.npoly, mu);
         T kre, kim;
@@ -79,7 +88,7 @@ __device__ __forceinline__ void project_group(const CoeffArgs<T>& a, const Coeff
         }
 #pragma unroll
         for (int n = 0; n < NH; ++n) {
-            const T t = __ldg(tab + n * S + s);
+            const T t = tab[n * S + s];
             accr[n] += t * kre;
             if (HAS_IM) acci[n] += t * kim;
         }
@@ -128,8 +137,31 @@ __device__ __forceinline__ void block_add(double v, double* dst) {
     }
 }
 
+// Shared-memory words for the quadrature directions and tables (L = 2, 4, 6, 8) and the
+// polynomials: every thread of a block reads the same entry at the same time (broadcast).
+template <typename T>
+__host__ __device__ inline int coeff_smem_words(const CoeffArgs<T>& a) {
+    int w = a.n_polys;
+    for (int q = 0; q < 4; ++q) w += a.quad_S[q] * (3 + 2 * (2 * (q + 1)) + 1);
+    return w;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_coeffs(CoeffArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char coeff_smem[];
+    T* sm = reinterpret_cast<T*>(coeff_smem);
+    {
+        int o = 0;
+        for (int q = 0; q < 4; ++q) {
+            const int S = a.quad_S[q], nh = 2 * (2 * (q + 1)) + 1;
+            for (int i = threadIdx.x; i < 3 * S; i += blockDim.x) sm[o + i] = a.quad_dirs[q][i];
+            o += 3 * S;
+            for (int i = threadIdx.x; i < nh * S; i += blockDim.x) sm[o + i] = a.quad_tab[q][i];
+            o += nh * S;
+        }
+        for (int i = threadIdx.x; i < a.n_polys; i += blockDim.x) sm[o + i] = a.polys[i];
+        __syncthreads();
+    }
     double sw = 0.0, sg = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.count;
          i += (long long)gridDim.x * blockDim.x) {
@@ -175,16 +207,16 @@ __global__ void __launch_bounds__(256) k_coeffs(CoeffArgs<T> a) {
         for (int gi = 0; gi < a.n_groups; ++gi) {
             const CoeffGroup& g = a.groups[gi];
             if (g.L == 2) {
-                if (g.has_im) project_group<T, 2, true>(a, g, i, w, g1, g2, ete, epe, xe);
-                else project_group<T, 2, false>(a, g, i, w, g1, g2, ete, epe, xe);
+                if (g.has_im) project_group<T, 2, true>(a, g, i, w, g1, g2, ete, epe, xe, sm);
+                else project_group<T, 2, false>(a, g, i, w, g1, g2, ete, epe, xe, sm);
             } else if (g.L == 4) {
-                if (g.has_im) project_group<T, 4, true>(a, g, i, w, g1, g2, ete, epe, xe);
-                else project_group<T, 4, false>(a, g, i, w, g1, g2, ete, epe, xe);
+                if (g.has_im) project_group<T, 4, true>(a, g, i, w, g1, g2, ete, epe, xe, sm);
+                else project_group<T, 4, false>(a, g, i, w, g1, g2, ete, epe, xe, sm);
             } else if (g.L == 6) {
-                if (g.has_im) project_group<T, 6, true>(a, g, i, w, g1, g2, ete, epe, xe);
-                else project_group<T, 6, false>(a, g, i, w, g1, g2, ete, epe, xe);
+                if (g.has_im) project_group<T, 6, true>(a, g, i, w, g1, g2, ete, epe, xe, sm);
+                else project_group<T, 6, false>(a, g, i, w, g1, g2, ete, epe, xe, sm);
             } else if (g.L == 8) {
-                project_group<T, 8, true>(a, g, i, w, g1, g2, ete, epe, xe);
+                project_group<T, 8, true>(a, g, i, w, g1, g2, ete, epe, xe, sm);
             }
         }
     }
@@ -197,7 +229,10 @@ cudaError_t launch_coeffs(const CoeffArgs<T>& a, cudaStream_t st) {
     if (a.count == 0) return cudaSuccess;
     long long blocks = (a.count + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    k_coeffs<T><<<(int)blocks, 256, 0, st>>>(a);
+    const size_t smem = (size_t)coeff_smem_words(a) * sizeof(T);
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    cudaFuncSetAttribute(k_coeffs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_coeffs<T><<<(int)blocks, 256, smem, st>>>(a);
     return cudaGetLastError();
 }
 

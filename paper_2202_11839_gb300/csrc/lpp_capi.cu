@@ -580,6 +580,7 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         ca.quad_S[qi] = plan->quad[qi].S;
     }
     ca.polys = (const T*)(plan->ws + plan->off_polys);
+    ca.n_polys = (int)plan->polys.size();
     ca.sums = sums;
     ca.err = err;
     if (sh.shape_kind != LPP_SHAPE_NONE) {

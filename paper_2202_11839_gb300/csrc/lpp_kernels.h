@@ -113,6 +113,7 @@ struct CoeffArgs {
     const T* quad_tab[4];    // per L: [2L+1][S]
     int quad_S[4];
     const T* polys;          // concatenated mu-polynomial coefficients
+    int n_polys;
     double* sums;            // FP64 reductions (see SumSlot)
     int* err;
 };
