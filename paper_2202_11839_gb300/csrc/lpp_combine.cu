@@ -94,6 +94,18 @@ __global__ void __launch_bounds__(1024) k_combine(CombineArgs<T> a) {
     const long long n2l = (long long)n * n;
     const int rows = a.nzi * a.nky;
 
+    int nrow = 0;
+    auto fold = [&]() {
+        __syncthreads();
+        for (int i = tid; i < E; i += nthr) {
+            const T v = acc[i];
+            if (v != (T)0) {
+                Owned<T>::add(own + i, own + E + i, v);
+                acc[i] = (T)0;
+            }
+        }
+        __syncthreads();
+    };
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
         const int zi = row / a.nky;
         const int yj = row - zi * a.nky;
@@ -246,16 +258,11 @@ __global__ void __launch_bounds__(1024) k_combine(CombineArgs<T> a) {
                 }
             }
         }
-        __syncthreads();
-        for (int i = tid; i < E; i += nthr) {
-            const T v = acc[i];
-            if (v != (T)0) {
-                Owned<T>::add(own + i, own + E + i, v);
-                acc[i] = (T)0;
-            }
-        }
-        __syncthreads();
+        // fold the partials into the compensated accumulators every second row (a row pair
+        // adds at most 2 x 16 warp segments per shell to an FP32 partial)
+        if ((++nrow & 1) == 0) fold();
     }
+    if (nrow & 1) fold();
     for (int i = tid; i < E; i += nthr) {
         const double v = Owned<T>::value(own + i, own + E + i);
         if (v != 0.0) {
