@@ -70,6 +70,7 @@ struct lpp_plan_s {
     size_t off_rmax = 0;                 // [n_coeff_rows][2] max |coefficient|, rms per row (FP32 plans)
     size_t off_rsq = 0;                  // [n_coeff_rows] FP64 sums of squares
     size_t off_trows = 0;                // [2][256] z-tile rows to visit, then [2] counts
+    size_t off_plive = 0;                // [3][n*n] bytes: x pencils reached per role
     int fty = 4, ftz = 4;
     int n_partner = 0;
     int out_rows = 0;
@@ -297,6 +298,7 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
     plan->off_rmax = take((size_t)std::max(1, plan->n_coeff_rows) * 2 * sizeof(float));
     plan->off_rsq = take((size_t)std::max(1, plan->n_coeff_rows) * sizeof(double));
     plan->off_trows = take((2 * 256 + 2) * sizeof(int));
+    plan->off_plive = take((size_t)3 * n * n);
     plan->off_wout = take((size_t)kWindowChannels * 256 * 2 * sizeof(double));
     plan->off_wthr = take(257 * sizeof(int));
     plan->off_partner = take((size_t)std::max(1, plan->n_partner) * n3 * cs);
@@ -534,14 +536,52 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         LPP_CUDA(launch_tile_rows(pmask, 1 << LPP_SHAPES, n, plan->ftz, trows, tcount, st));
         LPP_CUDA(launch_tile_rows(pmask, part_bits, n, plan->ftz, trows + 256, tcount + 1, st));
     }
+    unsigned char* plive = (unsigned char*)(plan->ws + plan->off_plive);
+    LPP_CUDA(launch_pencil_live((const int*)(plan->ws + plan->off_koff[0]), (const int*)(plan->ws + plan->off_koff[1]),
+                                (const int*)(plan->ws + plan->off_koff[2]), 1, plan->cat[LPP_DENSITY].set ? 1 : 0,
+                                has_rand ? 1 : 0, n, plive, st));
     // timing only: which planes are reached, for the byte counts of the skipping kernels
     // (one small synchronisation per estimate)
     std::vector<int> hmask;
+    std::vector<unsigned char> hlive;
     if (tm) {
         hmask.resize((size_t)3 * n);
+        hlive.resize((size_t)3 * n * n);
         LPP_CUDA(cudaMemcpyAsync(hmask.data(), pmask, hmask.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+        LPP_CUDA(cudaMemcpyAsync(hlive.data(), plive, hlive.size(), cudaMemcpyDeviceToHost, st));
         LPP_CUDA(cudaStreamSynchronize(st));
     }
+    auto live_at = [&](int bits, size_t zy) {
+        int hit = 0;
+        for (int r = 0; r < 3; ++r)
+            if (bits & (1 << r)) hit |= hlive[(size_t)r * n * n + zy];
+        return hit != 0;
+    };
+    // fraction of x pencils reached, and of fused tiles holding a reached pencil (those store)
+    double memo_p[8], memo_t[8];
+    for (int b = 0; b < 8; ++b) memo_p[b] = memo_t[b] = -1.0;
+    auto pencil_frac = [&](int bits) -> double {
+        if (hlive.empty() || bits == 0) return 1.0;
+        if (memo_p[bits & 7] >= 0.0) return memo_p[bits & 7];
+        long long c = 0;
+        for (size_t zy = 0; zy < (size_t)n * n; ++zy) c += live_at(bits, zy);
+        return memo_p[bits & 7] = (double)c / ((double)n * n);
+    };
+    auto tile_frac = [&](int bits) -> double {
+        if (hlive.empty() || bits == 0) return 1.0;
+        if (memo_t[bits & 7] >= 0.0) return memo_t[bits & 7];
+        const int ty = plan->fty, tz = plan->ftz;
+        long long c = 0, all = 0;
+        for (int z0 = 0; z0 < n; z0 += tz)
+            for (int y0 = 0; y0 < n; y0 += ty) {
+                bool any = false;
+                for (int dz = 0; dz < tz && !any; ++dz)
+                    for (int dy = 0; dy < ty && !any; ++dy) any = live_at(bits, (size_t)(z0 + dz) * n + y0 + dy);
+                c += any;
+                ++all;
+            }
+        return memo_t[bits & 7] = (double)c / all;
+    };
     auto plane_frac = [&](int bits) -> double {
         if (hmask.empty() || bits == 0) return 1.0;
         long long c = 0;
@@ -660,6 +700,7 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
     fa.tw = tw;
     fa.sums = sums;
     fa.pmask = pmask;
+    fa.skip_empty = 1;
     const double xbytes = (double)n * n * plan->nky * sizeof(c2<T>);   // kept x pencils of one grid
     auto slot_bits = [&](const FusedSlot& f) {
         int bits = 0;
@@ -672,7 +713,7 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         if (tm) {
             // kept x pencils are stored on the planes the slot's particles reach
             double wb = 0.0;
-            for (int i = 0; i < fa.n_slots; ++i) wb += xbytes * plane_frac(slot_bits(fa.slots[i]));
+            for (int i = 0; i < fa.n_slots; ++i) wb += xbytes * tile_frac(slot_bits(fa.slots[i]));
             tm->end(KK_ASSIGN, st, wb + fa.n_slots * (double)particles * 4 * plan->es);
         }
         return LPP_OK;
@@ -732,6 +773,10 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
             fr += plane_frac(gp.gmask[fa.slots[i].grid]);
         }
         gp.yread_frac = fa.n_slots ? (float)(fr / fa.n_slots) : 1.0f;
+        gp.plive = plive;
+        double fl = 0.0;
+        for (int i = 0; i < fa.n_slots; ++i) fl += pencil_frac(gp.gmask[fa.slots[i].grid]);
+        gp.ylive_frac = fa.n_slots ? (float)(fl / fa.n_slots) : 1.0f;
         LPP_CUDA(fft_yz<T>(grids, pgrids, n, tw, gp, false, st, tm));
         cb.partner_mode = 1;
         cb.has_d = plan->need_d;
@@ -787,6 +832,8 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         gc.q_max = plan->thr[nb];
         for (int i = 0; i < ngr; ++i) gc.gmask[i] = 1 << LPP_SHAPES;
         gc.yread_frac = (float)plane_frac(1 << LPP_SHAPES);
+        gc.plive = plive;
+        gc.ylive_frac = (float)pencil_frac(1 << LPP_SHAPES);
         LPP_CUDA(fft_yz<T>(grids, ngr, n, tw, gc, false, st, tm));
         if (tm) tm->begin(KK_COMBINE, st);
         LPP_CUDA(launch_combine<T>(cb, plan->n_sm, st));

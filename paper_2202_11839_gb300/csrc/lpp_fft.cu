@@ -94,6 +94,24 @@ __global__ void __launch_bounds__(PassShape<LOGN>::THREADS, sizeof(T) == 4 ? (LO
                 if (g.gmask[blockIdx.y] & (1 << r)) hit |= g.pmask[r * N + z];
             if (!hit) return;   // nothing stored: the z pass reads zeros for this plane
         }
+        // y pencils that no particle of the grid's roles reaches are zero and not loaded
+        unsigned ylive = 0xffffffffu;
+        if (MODE == 1 && g.plive && g.gmask[blockIdx.y]) {
+            const int z = tile_id / g.ntx;
+            const int gm = g.gmask[blockIdx.y];
+            const int e0r = tid >> S::LOGW;
+            constexpr int ROWSr = S::THREADS / W;
+            ylive = 0u;
+#pragma unroll
+            for (int k = 0; k < S::PER; ++k) {
+                const int y = e0r + k * ROWSr;
+                int hit = 0;
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+                    if (gm & (1 << r)) hit |= __ldg(g.plive + (size_t)r * N * N + (size_t)z * N + y);
+                ylive |= (hit ? 1u : 0u) << k;
+            }
+        }
         // rows e0 + k ROWS of W consecutive x values: one base pointer, compile-time strides
         constexpr int ROWS = S::THREADS / W;
         constexpr unsigned ES = MODE == 1 ? (unsigned)N : (unsigned)N * N;
@@ -123,7 +141,7 @@ __global__ void __launch_bounds__(PassShape<LOGN>::THREADS, sizeof(T) == 4 ? (LO
 #pragma unroll
             for (int k = k0; k < k0 + KB; ++k) {
                 c2<T> v = mk<T>((T)0, (T)0);
-                if ((live >> k) & 1u) v = gp[(size_t)k * ROWS * ES];
+                if ((live >> k) & (ylive >> k) & 1u) v = gp[(size_t)k * ROWS * ES];
                 sp[k * ROWS * LD] = v;
             }
         }
@@ -179,7 +197,8 @@ static cudaError_t launch_passes(c2<T>* data, int n_grids, const c2<T>* tw, cons
     if (timer) timer->begin(KK_FFT, st);
     k_fft_pass<T, LOGN, INV, 1><<<dim3(g.ntx * N, n_grids), S::THREADS, smem, st>>>(data, tw, g);
     // y: only the reached planes are read and written; z: their entries are read, all written
-    if (timer) timer->end(KK_FFT, st, n_grids * n3 * es * xcols * (double)g.yread_frac * (1.0 + keep));
+    if (timer)
+        timer->end(KK_FFT, st, n_grids * n3 * es * xcols * ((double)g.ylive_frac + (double)g.yread_frac * keep));
     if (timer) timer->begin(KK_FFT, st);
     k_fft_pass<T, LOGN, INV, 2><<<dim3(g.ntx * g.nky, n_grids), S::THREADS, smem, st>>>(data, tw, g);
     if (timer) {

@@ -61,10 +61,14 @@ struct FftGeom {
     // the bit set of roles assigned to it (0: never skip)
     const int* pmask = nullptr;
     int gmask[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    float yread_frac = 1.0f;   // host bookkeeping: fraction of z planes the y pass reads
+    float yread_frac = 1.0f;   // host bookkeeping: fraction of z planes the y pass writes
+    float ylive_frac = 1.0f;   // host bookkeeping: fraction of x pencils the y pass reads
     // z pass: skip (kx, ky) columns whose every mode has |f|^2 >= q_max (beyond the last
     // shell; never read by the combine); 0 transforms every column
     int q_max = 0;
+    // optional per-pencil reach [3][n*n] bytes (role, z * n + y): the y pass reads zeros for
+    // x pencils that no particle of the grid's roles reaches (the fused pass stores nothing there)
+    const unsigned char* plive = nullptr;
 };
 
 int fft_tile_width(int n);
@@ -212,6 +216,7 @@ struct FusedArgs {
     const int* pmask;                    // [3][n] planes reached per role, or null (write every pencil)
     const int* trows;                    // z-tile rows to visit (persistent grid), or null (all tiles)
     const int* trow_count;
+    int skip_empty;                      // empty tiles store nothing (the y pass fills their zeros)
 };
 
 void fused_geometry(int n, size_t elem_bytes, int* ty, int* tz, int* ipt, int* threads, size_t* smem);
@@ -220,6 +225,11 @@ void fused_geometry(int n, size_t elem_bytes, int* ty, int* tz, int* ipt, int* t
 // rows[0 .. *count) = the z-tile rows (tz planes each) holding a plane reached by a role in
 // bits (n / tz <= 256)
 cudaError_t launch_tile_rows(const int* pmask, int bits, int n, int tz, int* rows, int* count, cudaStream_t st);
+// plive[r][z * n + y] = 1 when a particle of role r (set[r] != 0) sits in a key row
+// (fy, fz) with y - 2 <= fy <= y + 1 and z - 2 <= fz <= z + 1 (mod n): the x pencils that
+// its CIC/TSC stencils (interlaced or not) reach
+cudaError_t launch_pencil_live(const int* off0, const int* off1, const int* off2, int set0, int set1, int set2, int n,
+                               unsigned char* plive, cudaStream_t st);
 cudaError_t launch_plane_mask(const int* off0, const int* off1, const int* off2, int set0, int set1, int set2, int n,
                               int* pmask, cudaStream_t st);
 template <typename T>

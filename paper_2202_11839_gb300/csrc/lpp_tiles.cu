@@ -374,6 +374,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int tile_y, in
         // no particle reaches these pencils: their transform is zero.  Planes that no
         // particle of the slot's roles reaches are skipped by the y pass, which writes
         // their zeros itself: nothing to store for those.
+        if (a.skip_empty) return;   // the y pass reads zeros for every pencil of this tile
         bool write = true;
         if (a.pmask) {
             const int z = z0 + cw / TY;
@@ -481,6 +482,40 @@ __global__ void k_plane_mask(const int* __restrict__ off0, const int* __restrict
         }
     }
     pmask[i] = hit;
+}
+
+__global__ void k_pencil_live(const int* __restrict__ off0, const int* __restrict__ off1,
+                              const int* __restrict__ off2, int set0, int set1, int set2, int n,
+                              unsigned char* __restrict__ plive) {
+    const long long nn = (long long)n * n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 3 * nn;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / nn);
+        const int zy = (int)(i - r * nn);
+        const int z = zy / n, y = zy - z * n;
+        const int* off = r == 0 ? off0 : (r == 1 ? off1 : off2);
+        const int set = r == 0 ? set0 : (r == 1 ? set1 : set2);
+        int hit = 0;
+        if (set) {
+            for (int dz = -2; dz <= 1 && !hit; ++dz) {
+                const int fz = (z + dz) & (n - 1);
+                for (int dy = -2; dy <= 1; ++dy) {
+                    const int key = fz * n + ((y + dy) & (n - 1));
+                    if (off[key + 1] > off[key]) { hit = 1; break; }
+                }
+            }
+        }
+        plive[i] = (unsigned char)hit;
+    }
+}
+
+cudaError_t launch_pencil_live(const int* off0, const int* off1, const int* off2, int set0, int set1, int set2, int n,
+                               unsigned char* plive, cudaStream_t st) {
+    const long long total = 3LL * n * n;
+    long long blocks = (total + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    k_pencil_live<<<(int)blocks, 256, 0, st>>>(off0, off1, off2, set0, set1, set2, n, plive);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_plane_mask(const int* off0, const int* off1, const int* off2, int set0, int set1, int set2, int n,
