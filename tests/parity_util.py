@@ -13,7 +13,7 @@ ALL_MOMENTS = tuple(O.MOMENTS)
 
 def make_case(kind: str, n: int, count: int, seed: int, box: float = 300.0, n_rand: int = 0,
               dtype=np.float64, separate_density: bool = False, gamma12: bool = False, zslab=None,
-              outlier: float = 0.0):
+              outlier: float = 0.0, yslab=None):
     """Small synthetic catalogues: uniform positions, random tensors (or gamma_1,2), optional
     randoms; with zslab = (a, b) every catalogue is confined to a <= z / box < b (so most z
     planes of the grid receive nothing)."""
@@ -21,9 +21,11 @@ def make_case(kind: str, n: int, count: int, seed: int, box: float = 300.0, n_ra
     lo = 0.0
 
     def squeeze(p):
-        if zslab is not None:
-            p = p.copy()
-            p[2] = (zslab[0] * box + (p[2] / box) * (zslab[1] - zslab[0]) * box).astype(p.dtype)
+        # zslab / yslab = (a, b): confine that coordinate to a <= c / box < b
+        for ax, sl in ((2, zslab), (1, yslab)):
+            if sl is not None:
+                p = p.copy()
+                p[ax] = (sl[0] * box + (p[ax] / box) * (sl[1] - sl[0]) * box).astype(p.dtype)
         return p
     pos = squeeze(S.uniform_positions(count, box, (lo, lo, lo), seed, 0, dtype))
     shape = rng.standard_normal((2 if gamma12 else 6, count)).astype(dtype)

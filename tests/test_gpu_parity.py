@@ -49,6 +49,9 @@ CASES64 = {
     "zslab_tsc_il_randoms_density_n32": (_cfg(32, 300.0, scheme=3, interlace=True),
                                          dict(count=1500, n_rand=3000, separate_density=True, zslab=(0.3, 0.45))),
     "zslab_cic_wrapping_n32": (_cfg(32, 300.0, scheme=2), dict(count=1200, zslab=(0.0, 0.08))),
+    # confined in y and z: empty tiles and unreached pencils inside the reached planes
+    "yz_box_tsc_il_randoms_n32": (_cfg(32, 300.0, scheme=3, interlace=True, frac=0.6),
+                                  dict(count=1500, n_rand=4000, yslab=(0.55, 0.8), zslab=(0.2, 0.4))),
 }
 
 
@@ -67,6 +70,8 @@ CASES32 = {
     "gamma12_n64_pruned": (_cfg(64, 800.0, scheme=3, interlace=True, frac=0.4, nb=6), dict(count=5000, gamma12=True)),
     # one weight 1e4 times the others: coefficient maxima far above the typical value
     "outlier_weight_n32": (_cfg(32, 500.0, scheme=3, interlace=True), dict(count=6000, outlier=1.0e4)),
+    "yz_box_randoms_n64": (_cfg(64, 800.0, scheme=3, interlace=True, frac=0.5),
+                           dict(count=6000, n_rand=12000, yslab=(0.1, 0.35), zslab=(0.6, 0.75))),
     "zslab_randoms_n64": (_cfg(64, 800.0, scheme=3, interlace=True, frac=0.5), dict(count=6000, n_rand=12000,
                                                                                    zslab=(0.55, 0.7))),
 }
