@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(1024) k_combine(CombineArgs<T> a) {
             // the mirror is exactly -k unless an index sits at the Nyquist frequency; then an
             // even-degree harmonic takes the same value at both members of the pair
             const bool mirror_neg = (fxp == -fx) && (fyp == -fy) && (fzp == -fz);
+            const SegMask segm = seg_mask(bin);
             const int n_slots = (a.n_ch + a.per_grid - 1) / a.per_grid;
             // four slots at a time: their packed values at m and -m are loaded together
             for (int s0 = 0; s0 < n_slots; s0 += 4) {
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(1024) k_combine(CombineArgs<T> a) {
                             tre = t.x;
                             tim = t.y;
                         }
-                        warp_bin_add<T>(tre, tim, bin, acc + ci * 2 * nb);
+                        warp_bin_add_seg<T>(tre, tim, bin, segm, acc + ci * 2 * nb);
                     }
                 }
             }

@@ -53,4 +53,46 @@ __device__ __forceinline__ void warp_bin_add(T re, T im, int bin, T* acc) {
     }
 }
 
+// The shell labels of a row are the same for every channel: the steps of the segmented scan
+// that add (bit s: lane >= 2^s and the lane 2^s below is in the same shell) and whether the
+// lane ends its segment are computed once per row.
+struct SegMask {
+    unsigned add;   // bit s set: add the value shuffled up by 2^s
+    bool last;      // the lane holds its segment's sum after the scan
+};
+
+__device__ __forceinline__ SegMask seg_mask(int bin) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    SegMask m;
+    m.add = 0u;
+#pragma unroll
+    for (int s = 0, d = 1; d < 32; d <<= 1, ++s) {
+        const int ob = __shfl_up_sync(full, bin, d);
+        if (lane >= d && ob == bin) m.add |= 1u << s;
+    }
+    const int nb = __shfl_down_sync(full, bin, 1);
+    m.last = (lane == 31) || (nb != bin);
+    return m;
+}
+
+// warp_bin_add with the row's precomputed segment structure
+template <typename T>
+__device__ __forceinline__ void warp_bin_add_seg(T re, T im, int bin, const SegMask& m, T* acc) {
+    const unsigned full = 0xffffffffu;
+#pragma unroll
+    for (int s = 0, d = 1; d < 32; d <<= 1, ++s) {
+        const T ore = __shfl_up_sync(full, re, d);
+        const T oim = __shfl_up_sync(full, im, d);
+        if ((m.add >> s) & 1u) {
+            re += ore;
+            im += oim;
+        }
+    }
+    if (m.last && bin >= 0) {
+        atomicAdd(acc + 2 * bin, re);
+        atomicAdd(acc + 2 * bin + 1, im);
+    }
+}
+
 }  // namespace lpp
