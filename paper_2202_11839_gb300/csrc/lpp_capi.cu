@@ -826,7 +826,9 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         }
         fa.trows = use_rows ? trows : nullptr;
         fa.trow_count = use_rows ? tcount : nullptr;
+        fa.dual = (!plan->fp64 && il && use_rows && (n == 256 || n == 512) && fa.n_slots % 2 == 0) ? 1 : 0;
         { lpp_status s0 = assign_fused(sh.count); if (s0 != LPP_OK) return s0; }
+        fa.dual = 0;
         FftGeom gc = geom;
         gc.pmask = pmask;
         gc.q_max = plan->thr[nb];

@@ -217,6 +217,7 @@ struct FusedArgs {
     const int* trows;                    // z-tile rows to visit (persistent grid), or null (all tiles)
     const int* trow_count;
     int skip_empty;                      // empty tiles store nothing (the y pass fills their zeros)
+    int dual;                            // FP32 n = 256/512: two slots per CTA (see k_assign_xfft2)
 };
 
 void fused_geometry(int n, size_t elem_bytes, int* ty, int* tz, int* ipt, int* threads, size_t* smem);

@@ -225,6 +225,43 @@ __device__ __forceinline__ void scatter_one(T* tilef, int ld, int n, int P, T ux
     }
 }
 
+// Two channel slots of the same particles: the stencil is evaluated once and each weight
+// is added to both tiles (values v0, v1 already in the tiles' units).
+template <typename T, bool FIXED>
+__device__ __forceinline__ void scatter_two(T* t0, T* t1, int ld, int n, int P, T ux, T uy, T uz, T shift, int y0,
+                                            int z0, int ty, int tz, T v0, T v1, int im) {
+    int cx[3], cy[3], cz[3];
+    T wx[3], wy[3], wz[3];
+    stencil1<T>(ux - shift, n, P, cx, wx);
+    stencil1<T>(uy - shift, n, P, cy, wy);
+    stencil1<T>(uz - shift, n, P, cz, wz);
+#pragma unroll
+    for (int kz = 0; kz < 3; ++kz) {
+        const int lz = (cz[kz] - z0) & (n - 1);
+        if (kz >= P || lz >= tz) continue;
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky) {
+            const int ly = (cy[ky] - y0) & (n - 1);
+            if (ky >= P || ly >= ty) continue;
+            const int line = lz * ty + ly;
+            const T wyz = wz[kz] * wy[ky];
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx) {
+                if (kx >= P) continue;
+                const int idx = 2 * (cx[kx] * ld + line) + im;
+                const T ww = wyz * wx[kx];
+                if constexpr (FIXED) {
+                    atomicAdd(reinterpret_cast<int*>(t0) + idx, __float2int_rn((float)(v0 * ww)));
+                    atomicAdd(reinterpret_cast<int*>(t1) + idx, __float2int_rn((float)(v1 * ww)));
+                } else {
+                    atomicAdd(t0 + idx, v0 * ww);
+                    atomicAdd(t1 + idx, v1 * ww);
+                }
+            }
+        }
+    }
+}
+
 // Tile of TY x TZ pencils: TY = 4 (TY = 2 when the FP64 1024-point tile would not fit).
 template <typename T, int LOGN>
 struct FusedShape {
@@ -241,32 +278,20 @@ struct FusedShape {
     static constexpr int MINB = (sizeof(T) == 4 && (LOGN == 9 || LOGN == 8)) ? 2 : 1;
 };
 
-// One tile (tile_y, tile_z) of TY x TZ pencils of the slot blockIdx.y: particle ranges,
-// scatter, x transform, store of the kept x frequencies.  Every return is CTA-uniform.
-template <typename T, int LOGN>
-__device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int tile_y, int tile_z) {
+// Set-up of one tile (shared by the one- and two-slot tiles): the particles touching the
+// tile, as TZ+3 z rows of keys y0-2 .. y0+TY per source of slot `sl`, one or two contiguous
+// ranges each (the y window may wrap), and for fixed-point slots the largest 4 x 4 key-row
+// window count.  Lane l of warp 0 takes row l (source l / (TZ+3)); a warp scan places the
+// ranges.  Meanwhile the other warps clear `tile_elems` elements of the tiles and load the
+// twiddles.  NT: threads of the CTA.
+template <typename T, int LOGN, int NT>
+__device__ __forceinline__ void tile_setup(const FusedArgs<T>& a, const FusedSlot& sl, int y0, int z0, c2<T>* tw,
+                                           c2<T>* tiles, int tile_elems, int* r_begin, int* r_pref, int* r_src,
+                                           int& n_ranges, int (*rcount)[FusedShape<T, LOGN>::TY + 3], int& wmax) {
     using S = FusedShape<T, LOGN>;
-    constexpr int N = S::N, TY = S::TY, TZ = S::TZ, W = S::W, LD = S::LD;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int r_begin[S::MAXR], r_pref[S::MAXR + 1], r_src[S::MAXR];
-    __shared__ int n_ranges;
-    // particles per key row around the tile (fixed-point bound; rows of source 0)
-    __shared__ int rcount[TZ + 3][TY + 3];
-    __shared__ int wmax;
-    c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
-    c2<T>* tile = tw + N;
-    T* tilef = reinterpret_cast<T*>(tile);
+    constexpr int N = S::N, TY = S::TY, TZ = S::TZ;
     const int tid = threadIdx.x;
-    const int y0 = tile_y * TY;
-    const int z0 = tile_z * TZ;
-    const FusedSlot& sl = a.slots[blockIdx.y];
-    c2<T>* out = a.grids + (size_t)sl.grid * a.grid_stride + ((size_t)z0 * N + y0) * N;
-
-    // the particles touching the tile: TZ+3 z rows of keys y0-2 .. y0+TY per source,
-    // one or two contiguous ranges each (the y window may wrap).  Lane l of warp 0 takes
-    // row l (source l / (TZ+3)); a warp scan places the ranges.  Meanwhile the other warps
-    // clear the tile and load the twiddles.
-    if (S::THREADS < 64) {
+    if (NT < 64) {
         // tiny tiles (n <= 16): one thread finds the ranges, everybody clears the tile
         if (tid == 0) {
             int nr = 0, acc = 0;
@@ -294,8 +319,8 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int tile_y, in
             n_ranges = nr;
             wmax = acc;   // every particle of the tile: a looser but valid per-cell bound
         }
-        for (int i = tid; i < N; i += S::THREADS) tw[i] = a.tw[i];
-        for (int i = tid; i < N * LD; i += S::THREADS) tile[i] = mk<T>((T)0, (T)0);
+        for (int i = tid; i < N; i += NT) tw[i] = a.tw[i];
+        for (int i = tid; i < tile_elems; i += NT) tiles[i] = mk<T>((T)0, (T)0);
     } else if (tid < 32) {
         const int lane = tid;
         int bb[2] = {0, 0}, ee[2] = {0, 0}, m = 0, s_idx = 0;
@@ -359,9 +384,34 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int tile_y, in
             if (lane == 0) wmax = wsum;
         }
     } else {
-        for (int i = tid - 32; i < N; i += S::THREADS - 32) tw[i] = a.tw[i];
-        for (int i = tid - 32; i < N * LD; i += S::THREADS - 32) tile[i] = mk<T>((T)0, (T)0);
+        for (int i = tid - 32; i < N; i += NT - 32) tw[i] = a.tw[i];
+        for (int i = tid - 32; i < tile_elems; i += NT - 32) tiles[i] = mk<T>((T)0, (T)0);
     }
+}
+
+// One tile (tile_y, tile_z) of TY x TZ pencils of the slot blockIdx.y: particle ranges,
+// scatter, x transform, store of the kept x frequencies.  Every return is CTA-uniform.
+template <typename T, int LOGN>
+__device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int tile_y, int tile_z) {
+    using S = FusedShape<T, LOGN>;
+    constexpr int N = S::N, TY = S::TY, TZ = S::TZ, W = S::W, LD = S::LD;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int r_begin[S::MAXR], r_pref[S::MAXR + 1], r_src[S::MAXR];
+    __shared__ int n_ranges;
+    // particles per key row around the tile (fixed-point bound; rows of source 0)
+    __shared__ int rcount[TZ + 3][TY + 3];
+    __shared__ int wmax;
+    c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
+    c2<T>* tile = tw + N;
+    T* tilef = reinterpret_cast<T*>(tile);
+    const int tid = threadIdx.x;
+    const int y0 = tile_y * TY;
+    const int z0 = tile_z * TZ;
+    const FusedSlot& sl = a.slots[blockIdx.y];
+    c2<T>* out = a.grids + (size_t)sl.grid * a.grid_stride + ((size_t)z0 * N + y0) * N;
+
+    tile_setup<T, LOGN, S::THREADS>(a, sl, y0, z0, tw, tile, N * LD, r_begin, r_pref, r_src, n_ranges, rcount,
+                                    wmax);
     __syncthreads();
     const int nr = n_ranges;
     const int total = r_pref[nr];
@@ -536,6 +586,115 @@ void fused_geometry(int n, size_t elem_bytes, int* ty, int* tz, int* ipt, int* t
     *smem = (size_t)(n + n * (w + 1)) * 2 * elem_bytes;
 }
 
+// Two interlaced channel slots (2 blockIdx.y, 2 blockIdx.y + 1: single-source coefficient
+// rows of the same catalogue) in one CTA of 2 x THREADS threads: one set-up, every particle
+// visit computes its stencils once for both tiles; the halves of the CTA transform and store
+// one tile each.  The tiles use fixed point only when both slots' units pass the guard.
+template <typename T, int LOGN>
+__device__ __forceinline__ void fused_tile2(const FusedArgs<T>& a, int tile_y, int tile_z) {
+    using S = FusedShape<T, LOGN>;
+    constexpr int N = S::N, TY = S::TY, TZ = S::TZ, W = S::W, LD = S::LD;
+    constexpr int NT = 2 * S::THREADS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int r_begin[S::MAXR], r_pref[S::MAXR + 1], r_src[S::MAXR];
+    __shared__ int n_ranges;
+    __shared__ int rcount[TZ + 3][TY + 3];
+    __shared__ int wmax;
+    c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
+    c2<T>* tile0 = tw + N;
+    c2<T>* tile1 = tile0 + N * LD;
+    const int tid = threadIdx.x;
+    const int y0 = tile_y * TY, z0 = tile_z * TZ;
+    const FusedSlot& s0 = a.slots[2 * blockIdx.y];
+    const FusedSlot& s1 = a.slots[2 * blockIdx.y + 1];
+    tile_setup<T, LOGN, NT>(a, s0, y0, z0, tw, tile0, 2 * N * LD, r_begin, r_pref, r_src, n_ranges, rcount, wmax);
+    __syncthreads();
+    const int nr = n_ranges;
+    const int total = r_pref[nr];
+    const int half = tid / S::THREADS, th = tid - half * S::THREADS;
+    const FusedSlot& sh = half ? s1 : s0;
+    c2<T>* out = a.grids + (size_t)sh.grid * a.grid_stride + ((size_t)z0 * N + y0) * N;
+    const int nkept = a.nk_pos + 1 + a.nk_neg;
+    constexpr int LPL = S::THREADS / W;
+    const int cw = th / LPL;
+    if (total == 0) {
+        if (a.skip_empty) return;
+        bool write = true;
+        if (a.pmask) write = a.pmask[sh.src[0].cat * N + z0 + cw / TY] != 0;
+        if (write) {
+            for (int k = th & (LPL - 1); k < nkept; k += LPL) {
+                const int e = k <= a.nk_pos ? k : N - nkept + k;
+                out[((cw / TY) * N + (cw & (TY - 1))) * N + e] = mk<T>((T)0, (T)0);
+            }
+        }
+        return;
+    }
+    // fixed point as in fused_tile, with one unit per slot
+    bool fixed = sizeof(T) == 4;
+    float fs[2] = {1.f, 1.f}, fi[2] = {1.f, 1.f};
+    for (int q = 0; q < 2 && fixed; ++q) {
+        const FusedSlot& sq = q ? s1 : s0;
+        const float am = sq.amax_a[0], rms = sq.amax_a[1];
+        const float bound = (float)wmax * am;
+        if (bound == 0.f) continue;
+        if (bound * (1.f / 1073741824.f) <= rms * (1.f / 65536.f)) {
+            fs[q] = 1073741824.f / bound;
+            fi[q] = bound / 1073741824.f;
+        } else {
+            fixed = false;
+        }
+    }
+    const int P = a.scheme;
+    const PencilCat& cat = a.cat[s0.src[0].cat];
+    const T* su = static_cast<const T*>(cat.su);
+    const T* vals0 = static_cast<const T*>(s0.src[0].vals);
+    const T* vals1 = static_cast<const T*>(s1.src[0].vals);
+    const long long cap = cat.cap;
+    T* t0 = reinterpret_cast<T*>(tile0);
+    T* t1 = reinterpret_cast<T*>(tile1);
+    int r = 0;
+    for (int t = tid; t < total; t += NT) {
+        while (r + 1 < nr && r_pref[r + 1] <= t) ++r;
+        const int j = r_begin[r] + (t - r_pref[r]);
+        const T ux = su[j], uy = su[cap + j], uz = su[2 * cap + j];
+        T v0 = vals0[j], v1 = vals1[j];
+        if (fixed) {
+            v0 *= fs[0];
+            v1 *= fs[1];
+            scatter_two<T, true>(t0, t1, LD, N, P, ux, uy, uz, (T)0, y0, z0, TY, TZ, v0, v1, 0);
+            scatter_two<T, true>(t0, t1, LD, N, P, ux, uy, uz, (T)0.5, y0, z0, TY, TZ, v0, v1, 1);
+        } else {
+            scatter_two<T, false>(t0, t1, LD, N, P, ux, uy, uz, (T)0, y0, z0, TY, TZ, v0, v1, 0);
+            scatter_two<T, false>(t0, t1, LD, N, P, ux, uy, uz, (T)0.5, y0, z0, TY, TZ, v0, v1, 1);
+        }
+    }
+    __syncthreads();
+    c2<T>* tile = half ? tile1 : tile0;
+    if (fixed) {
+        T* tf = reinterpret_cast<T*>(tile);
+        const int* ti = reinterpret_cast<const int*>(tile);
+        const float inv = fi[half];
+        for (int i = th; i < 2 * N * LD; i += S::THREADS) tf[i] = (T)((float)ti[i] * inv);
+        __syncthreads();
+    }
+    fft_columns<T, LOGN, false, S::IPT, LD>(tile, th & (W - 1), th >> ilog2(W), tw);
+    for (int k = th & (LPL - 1); k < nkept; k += LPL) {
+        const int e = k <= a.nk_pos ? k : N - nkept + k;
+        out[((cw / TY) * N + (cw & (TY - 1))) * N + e] = tile[e * LD + cw];
+    }
+}
+
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(2 * FusedShape<T, LOGN>::THREADS, 1) k_assign_xfft2(FusedArgs<T> a) {
+    using S = FusedShape<T, LOGN>;
+    constexpr int NTY = S::N / S::TY;
+    const int total = *a.trow_count * NTY;
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        fused_tile2<T, LOGN>(a, t % NTY, a.trows[t / NTY]);
+        __syncthreads();
+    }
+}
+
 // Without a tile-row list one CTA per tile; with one (trows: z-tile rows that contain a
 // plane some particle reaches, *trow_count of them) a persistent grid walks those rows' tiles.
 template <typename T, int LOGN>
@@ -586,6 +745,20 @@ static cudaError_t launch_fused_n(const FusedArgs<T>& a, int n_tiles, cudaStream
     if (a.ty != S::TY || a.tz != S::TZ) return cudaErrorInvalidConfiguration;
     const size_t smem = (size_t)(S::N + S::N * S::LD) * sizeof(c2<T>);
     cudaFuncSetAttribute(k_assign_xfft<T, LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if constexpr (sizeof(T) == 4 && (LOGN == 8 || LOGN == 9)) {
+        if (a.dual) {
+            // two slots per CTA (FusedArgs::dual: even slot count, interlaced single-source
+            // coefficient slots, a tile-row list)
+            const size_t smem2 = (size_t)(S::N + 2 * S::N * S::LD) * sizeof(c2<T>);
+            cudaFuncSetAttribute(k_assign_xfft2<T, LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+            int dev = 0, sms = 152;
+            if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const int pairs = a.n_slots / 2;
+            const int g2 = std::max(1, std::min(n_tiles, 2 * sms / pairs));
+            k_assign_xfft2<T, LOGN><<<dim3(g2, pairs), 2 * S::THREADS, smem2, st>>>(a);
+            return cudaGetLastError();
+        }
+    }
     int grid = n_tiles;
     if (a.trows) {
         // persistent: about two resident waves over all slots
