@@ -49,6 +49,18 @@ def parse():
     return ap.parse_args()
 
 
+def replica_throughput(elapsed, steps: int, world: int, pg=None, device=None):
+    """Whole-job throughput of `world` independent replicas that each ran `steps` steps in
+    `elapsed` (any time unit): the slowest rank's time (max over ranks through `pg`) bounds
+    the job, and every rank's steps count.  Returns (units per elapsed unit, max elapsed)."""
+    if pg is not None and world > 1:
+        import torch
+        t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        elapsed = float(t.item())
+    return world * steps / elapsed, elapsed
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -362,12 +374,9 @@ def run_lpp(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    if pg:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    value, ms = replica_throughput(ms / 1000.0, args.steps, world, pg, dev)
+    ms *= 1000.0
     plan.set_timing(False)
-    value = world * args.steps / (ms / 1000.0)
     n_fields = plan.field_count()
 
     # dominant kernel and its roofline
@@ -411,12 +420,8 @@ def run_lpp(args):
             hplan.multipoles()
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        if pg:
-            t = torch.tensor([te], device=dev)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": world * args.steps / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
+        ev, te = replica_throughput(te, args.steps, world, pg, dev)
+        e2e = {"value": ev, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
         del hplan
 
     if rank != 0:
