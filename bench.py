@@ -365,8 +365,10 @@ def run_lpp(args):
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     stats = {k: {"ms": 0.0, "launches": 0, "bytes": 0.0} for k in L.KERNEL_KINDS}
+    launches = 0
     for _ in range(args.steps):
         est = plan.multipoles()
+        launches += plan.launch_count()
         for k, v in plan.kernel_stats().items():
             for f in ("ms", "launches", "bytes"):
                 stats[k][f] += v[f]
@@ -389,7 +391,6 @@ def run_lpp(args):
     kern = {k: {"ms_per_step": round(v["ms"] / args.steps, 3), "launches_per_step": v["launches"] // args.steps,
                 "gbs": round(v["bytes"] / (v["ms"] / 1000.0) / 1e9, 1) if v["ms"] > 0 else None}
             for k, v in stats.items()}
-    launches = sum(v["launches"] for v in stats.values())
 
     templates = None
     if rank == 0 and not args.no_surrogate:

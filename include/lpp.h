@@ -324,6 +324,13 @@ lpp_status lpp_plan_set_timing(lpp_plan_t plan, int enable);
 lpp_status lpp_plan_kernel_stats(lpp_plan_t plan, int kind, double* ms, long long* launches,
                                  double* bytes);
 
+/* Number of kernels the plan's last estimate enqueued on the device (the last
+ * lpp_multipoles call, or the last mock of a batch enqueued or captured on the plan): pencil sorts and scans, reach masks, coefficient and
+ * normalisation-sum kernels, fused assignment passes, y/z FFT passes and shell combines
+ * (memsets and copies excluded).  Counted with timing on or off.  launches: host output.
+ * LPP_ERR_INVALID_ARG for a null plan or pointer. */
+lpp_status lpp_plan_launch_count(lpp_plan_t plan, long long* launches);
+
 /* Density monopole P_dd^(0) of a periodic catalogue without any device allocation.
  * The paper has no counterpart: this entry point exists for callers that cannot call
  * cudaMalloc (code running inside another framework's memory pool or under a fixed

@@ -80,6 +80,7 @@ struct lpp_plan_s {
     Timer timer;
     std::string err;
     int n_sm = 152;
+    long long n_launch = 0;   // kernels launched by the last estimate
 };
 
 static lpp_status fail(lpp_plan_t p, lpp_status s, const std::string& msg) {
@@ -502,6 +503,8 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
     LPP_CUDA(cudaMemsetAsync(sums, 0, SUM_COUNT * sizeof(double), st));
     LPP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
     LPP_CUDA(cudaMemsetAsync(out, 0, (size_t)plan->out_rows * nb * 2 * sizeof(double), st));
+    long long& nl = plan->n_launch;
+    nl = 0;
 
     // 0. pencil sort of every catalogue (cell coordinates and weights in x-pencil key order)
     const long long caps[3] = {std::max<long long>(1, plan->d.max_shapes), std::max<long long>(1, plan->d.max_density),
@@ -516,6 +519,7 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
                                        (T*)(plan->ws + plan->off_su[role]),
                                        (T*)(plan->ws + plan->off_sw[role]), role == LPP_SHAPES ? perm : nullptr, err,
                                        st));
+        nl += c.count > 0 ? 5 : 3;
         if (tm) tm->end(KK_OTHER, st, (double)c.count * (plan->es * 8 + 12));
         return LPP_OK;
     };
@@ -526,6 +530,7 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
     LPP_CUDA(launch_plane_mask((const int*)(plan->ws + plan->off_koff[0]), (const int*)(plan->ws + plan->off_koff[1]),
                                (const int*)(plan->ws + plan->off_koff[2]), 1, plan->cat[LPP_DENSITY].set ? 1 : 0,
                                has_rand ? 1 : 0, n, pmask, st));
+    nl += 1;
     // the z-tile rows the fused passes visit: channel slots (shapes) and the partner slots
     int* trows = (int*)(plan->ws + plan->off_trows);
     int* tcount = trows + 512;
@@ -535,11 +540,13 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
     if (use_rows) {
         LPP_CUDA(launch_tile_rows(pmask, 1 << LPP_SHAPES, n, plan->ftz, trows, tcount, st));
         LPP_CUDA(launch_tile_rows(pmask, part_bits, n, plan->ftz, trows + 256, tcount + 1, st));
+        nl += 2;
     }
     unsigned char* plive = (unsigned char*)(plan->ws + plan->off_plive);
     LPP_CUDA(launch_pencil_live((const int*)(plan->ws + plan->off_koff[0]), (const int*)(plan->ws + plan->off_koff[1]),
                                 (const int*)(plan->ws + plan->off_koff[2]), 1, plan->cat[LPP_DENSITY].set ? 1 : 0,
                                 has_rand ? 1 : 0, n, plive, st));
+    nl += 1;
     // timing only: which planes are reached, for the byte counts of the skipping kernels
     // (one small synchronisation per estimate)
     std::vector<int> hmask;
@@ -626,29 +633,35 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
     if (sh.shape_kind != LPP_SHAPE_NONE) {
         if (tm) tm->begin(KK_COEFF, st);
         LPP_CUDA(launch_coeffs<T>(ca, st));
+        nl += sh.count > 0 ? 1 : 0;
         if (tm) tm->end(KK_COEFF, st, (double)sh.count * plan->es * (3 + 1 + 6 + plan->n_coeff_rows));
         if (!plan->fp64) {
             if (tm) tm->begin(KK_OTHER, st);
             LPP_CUDA(launch_rowstat((const float*)coeff, stride, sh.count, plan->n_coeff_rows, rmax,
                                     (double*)(plan->ws + plan->off_rsq), st));
+            nl += (sh.count > 0 && plan->n_coeff_rows > 0) ? 2 : 0;
             if (tm) tm->end(KK_OTHER, st, (double)sh.count * plan->n_coeff_rows * sizeof(float));
         }
     } else {
         if (tm) tm->begin(KK_OTHER, st);
         LPP_CUDA(launch_sums<T>((const T*)sh.w, nullptr, sh.count, sums, SUM_W_SHAPES, -1, -1, st));
+        nl += sh.count > 0 ? 1 : 0;
         if (tm) tm->end(KK_OTHER, st, (double)sh.count * plan->es);
     }
     if (tm) tm->begin(KK_OTHER, st);
     LPP_CUDA(launch_sums<T>((const T*)de.w, nullptr, de.count, sums, SUM_W_DENS, SUM_W2_DENS, -1, st));
+    nl += de.count > 0 ? 1 : 0;
     if (tm) tm->end(KK_OTHER, st, (double)de.count * plan->es);
     if (has_rand) {
         if (tm) tm->begin(KK_OTHER, st);
         LPP_CUDA(launch_sums<T>((const T*)ra.w, (const T*)ra.nbar, ra.count, sums, SUM_W_RAND, SUM_W2_RAND,
                                 SUM_NW2_RAND, st));
+        nl += ra.count > 0 ? 1 : 0;
         if (tm) tm->end(KK_OTHER, st, (double)ra.count * plan->es * 2);
     }
     if (tm) tm->begin(KK_OTHER, st);
     LPP_CUDA(launch_alpha(sums, has_rand ? 1 : 0, st));
+    nl += 1;
     if (tm) tm->end(KK_OTHER, st, 0.0);
 
     const FftGeom& geom = plan->geom;
@@ -710,6 +723,7 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
     auto assign_fused = [&](long long particles) -> lpp_status {
         if (tm) tm->begin(KK_ASSIGN, st);
         LPP_CUDA(launch_assign_xfft<T>(fa, st));
+        nl += fa.n_slots > 0 ? 1 : 0;
         if (tm) {
             // kept x pencils are stored on the planes the slot's particles reach
             double wb = 0.0;
@@ -778,12 +792,14 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         for (int i = 0; i < fa.n_slots; ++i) fl += pencil_frac(gp.gmask[fa.slots[i].grid]);
         gp.ylive_frac = fa.n_slots ? (float)(fl / fa.n_slots) : 1.0f;
         LPP_CUDA(fft_yz<T>(grids, pgrids, n, tw, gp, false, st, tm));
+        nl += 2;
         cb.partner_mode = 1;
         cb.has_d = plan->need_d;
         cb.has_g = plan->need_g;
         cb.n_ch = 0;
         if (tm) tm->begin(KK_PARTNER, st);
         LPP_CUDA(launch_combine<T>(cb, plan->n_sm, st));
+        nl += 1;
         if (tm) tm->end(KK_PARTNER, st, shell_modes * sizeof(c2<T>) * (pgrids + plan->n_partner));
     }
 
@@ -839,6 +855,7 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         LPP_CUDA(fft_yz<T>(grids, ngr, n, tw, gc, false, st, tm));
         if (tm) tm->begin(KK_COMBINE, st);
         LPP_CUDA(launch_combine<T>(cb, plan->n_sm, st));
+        nl += 3;
         if (tm) tm->end(KK_COMBINE, st, shell_modes * sizeof(c2<T>) * (ngr + (cb.has_d ? 1 : 0) + (cb.has_g ? 2 : 0)));
     }
 
@@ -1330,3 +1347,9 @@ extern "C" lpp_status lpp_batch_results(lpp_batch_t b, lpp_result* results) {
 }
 
 extern "C" const char* lpp_batch_last_error(lpp_batch_t b) { return b ? b->err.c_str() : "null batch"; }
+
+extern "C" lpp_status lpp_plan_launch_count(lpp_plan_t plan, long long* launches) {
+    if (!plan || !launches) return LPP_ERR_INVALID_ARG;
+    *launches = plan->n_launch;
+    return LPP_OK;
+}

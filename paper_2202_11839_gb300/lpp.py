@@ -105,6 +105,7 @@ EXPORTS = {
     "lpp_derive_eb": (C.c_int, [C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                 C.POINTER(C.c_double)]),
     "lpp_plan_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "lpp_plan_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
     "lpp_plan_kernel_stats": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                                         C.POINTER(C.c_double)]),
     "lpp_density_monopole_static": (C.c_int, [C.c_int, C.c_double, C.POINTER(C.c_double), C.c_int, C.c_int, C.c_int,
@@ -229,6 +230,12 @@ class Plan:
 
     def set_timing(self, on: bool = True):
         _check(self.lib, self.lib.lpp_plan_set_timing(self.h, int(on)), self.h)
+
+    def launch_count(self) -> int:
+        """Kernels the last estimate launched."""
+        v = C.c_longlong()
+        _check(self.lib, self.lib.lpp_plan_launch_count(self.h, C.byref(v)), self.h)
+        return v.value
 
     def kernel_stats(self) -> dict:
         out = {}
