@@ -1,11 +1,12 @@
 // Batched 3D complex FFT of n^3 grids as three pencil passes (x, y, z).
 //
-// Each CTA loads a tile of W pencils (n complex points each) into shared memory,
-// runs a mixed-radix Stockham FFT (radix 8 stages, one leading radix-2 or -4 stage)
-// with every thread holding 8 points per stage, and writes the pencils back in
-// place.  Pencils along y and z are loaded as rows of W consecutive x values, so
-// every global access is a contiguous W-element segment; x pencils are transposed
-// into the same column layout while loading.
+// Each CTA transforms a tile of W pencils (n complex points each) with a mixed-radix
+// Stockham FFT (radix 8 stages, one leading radix-2 or -4 stage), every thread holding
+// 8 points per stage, and writes the pencils back in place.  Pencils along y and z are
+// read as rows of W consecutive x values, so every global access is a contiguous
+// W-element segment; the first stage takes its operands straight from those rows and
+// the last stage stores straight to them, so shared memory holds only the stages in
+// between.  x pencils are transposed into the same column layout in shared memory.
 //
 // Passes can be pruned to the frequencies the shell binning needs: with a kept
 // range f in [-nk_neg, nk_pos] per axis, the x pass writes only kept x, the y pass
@@ -94,62 +95,40 @@ __global__ void __launch_bounds__(PassShape<LOGN>::THREADS, sizeof(T) == 4 ? (LO
                 if (g.gmask[blockIdx.y] & (1 << r)) hit |= g.pmask[r * N + z];
             if (!hit) return;   // nothing stored: the z pass reads zeros for this plane
         }
-        // y pencils that no particle of the grid's roles reaches are zero and not loaded
-        unsigned ylive = 0xffffffffu;
-        if (MODE == 1 && g.plive && g.gmask[blockIdx.y]) {
-            const int z = tile_id / g.ntx;
-            const int gm = g.gmask[blockIdx.y];
-            const int e0r = tid >> S::LOGW;
-            constexpr int ROWSr = S::THREADS / W;
-            ylive = 0u;
-#pragma unroll
-            for (int k = 0; k < S::PER; ++k) {
-                const int y = e0r + k * ROWSr;
-                int hit = 0;
-#pragma unroll
-                for (int r = 0; r < 3; ++r)
-                    if (gm & (1 << r)) hit |= __ldg(g.plive + (size_t)r * N * N + (size_t)z * N + y);
-                ylive |= (hit ? 1u : 0u) << k;
-            }
-        }
-        // rows e0 + k ROWS of W consecutive x values: one base pointer, compile-time strides
-        constexpr int ROWS = S::THREADS / W;
+        // Thread (c, u) owns pencil c (W consecutive x values per row: 128-byte segments in
+        // FP32) and butterfly slot u.  The first FFT stage loads its operands straight from
+        // the grid and the last stores its results straight back, so the tile holds only the
+        // intermediate stages.
+        const int c = tid & (W - 1), u = tid >> S::LOGW;
         constexpr unsigned ES = MODE == 1 ? (unsigned)N : (unsigned)N * N;
-        const int c = tid & (W - 1), e0 = tid >> S::LOGW;
-        c2<T>* gp = base + (size_t)e0 * ES + c;
-        c2<T>* sp = tile + e0 * LD + c;
-        // z pencils: 64-bit strides; two batches of loads keep the live registers under the cap
-        constexpr int KB = (MODE == 2 && S::PER > 8) ? 8 : S::PER;
-        static_assert(S::PER <= 32, "one liveness bit per loaded row");
-        // z pencils: entries on planes no particle reaches are zero and are not loaded
+        c2<T>* gp = base + c;
+        static_assert(S::PER == 8 * S::IPT && S::PER <= 32, "one liveness bit per operand");
+        // operands on rows that no particle of the grid's roles reaches (y pencils of this z
+        // plane for the y pass, z planes for the z pass) are zero and not loaded
         unsigned live = 0xffffffffu;
-        if (MODE == 2 && g.pmask && g.gmask[blockIdx.y]) {
-            const int gm = g.gmask[blockIdx.y];
+        const int gm = g.gmask[blockIdx.y];
+        if (gm && (MODE == 1 ? g.plive != nullptr : g.pmask != nullptr)) {
+            const int z = tile_id / g.ntx;   // the y pass's plane
             live = 0u;
 #pragma unroll
-            for (int k = 0; k < S::PER; ++k) {
-                const int z = e0 + k * ROWS;
+            for (int b = 0; b < S::PER; ++b) {
+                const int e = lead_row<LOGN, S::IPT>(u, b);
                 int hit = 0;
 #pragma unroll
-                for (int r = 0; r < 3; ++r)
-                    if (gm & (1 << r)) hit |= __ldg(g.pmask + r * N + z);
-                live |= (hit ? 1u : 0u) << k;
+                for (int r = 0; r < 3; ++r) {
+                    if (gm & (1 << r))
+                        hit |= MODE == 1 ? __ldg(g.plive + (size_t)r * N * N + (size_t)z * N + e)
+                                         : __ldg(g.pmask + r * N + e);
+                }
+                live |= (hit ? 1u : 0u) << b;
             }
         }
-#pragma unroll 1
-        for (int k0 = 0; k0 < S::PER; k0 += KB) {
-#pragma unroll
-            for (int k = k0; k < k0 + KB; ++k) {
-                c2<T> v = mk<T>((T)0, (T)0);
-                if ((live >> k) & (ylive >> k) & 1u) v = gp[(size_t)k * ROWS * ES];
-                sp[k * ROWS * LD] = v;
-            }
-        }
-        __syncthreads();
-        fft_columns<T, LOGN, INV, S::IPT, LD>(tile, tid & (W - 1), tid >> S::LOGW, tw);
-#pragma unroll
-        for (int k = 0; k < S::PER; ++k)
-            if (kept(e0 + k * ROWS, N, g.nk_pos, g.nk_neg)) gp[(size_t)k * ROWS * ES] = sp[k * ROWS * LD];
+        fft_columns_io<T, LOGN, INV, S::IPT, LD>(
+            tile, c, u, tw,
+            [&](int b, int e) { return ((live >> b) & 1u) ? gp[(size_t)e * ES] : mk<T>((T)0, (T)0); },
+            [&](int e, c2<T> v) {
+                if (kept(e, N, g.nk_pos, g.nk_neg)) gp[(size_t)e * ES] = v;
+            });
     }
 }
 

@@ -130,6 +130,117 @@ __device__ __forceinline__ void fft_columns(c2<T>* tile, int c, int u, const c2<
     }
 }
 
+// ---- stages with their operands outside the tile ----------------------------------------
+// Radix of the leading stage for N = 2^LOGN (2 or 4 when LOGN is not a multiple of 3).
+template <int LOGN>
+struct LeadRadix {
+    static constexpr int R = LOGN % 3 == 1 ? 2 : (LOGN % 3 == 2 ? 4 : 8);
+};
+
+// Point of the thread's pencil that operand b (= s 8 + q R + r) of the leading stage
+// reads: butterfly slot u + s US + q N/8, leg r.
+template <int LOGN, int IPT>
+__device__ __forceinline__ int lead_row(int u, int b) {
+    constexpr int N = 1 << LOGN, R = LeadRadix<LOGN>::R, US = N / (8 * IPT);
+    const int s = b >> 3, q = (b & 7) / R, r = (b & 7) % R;
+    return u + s * US + q * (N / 8) + r * (N / R);
+}
+
+// Leading stage (NS = 1, no twiddles) with operand b of point e from load(b, e); results
+// to the tile.  INPLACE: load reads the tile itself (a barrier separates the reads from
+// the writes).  Ends with a barrier.
+template <typename T, int LOGN, bool INV, int IPT, int LD, bool INPLACE, class Load>
+__device__ __forceinline__ void lead_stage(c2<T>* tile, int c, int u, Load&& load) {
+    constexpr int N = 1 << LOGN, R = LeadRadix<LOGN>::R, Q = 8 / R, US = N / (8 * IPT);
+    c2<T> v[IPT][8];
+#pragma unroll
+    for (int s = 0; s < IPT; ++s) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[s][k] = load(s * 8 + k, lead_row<LOGN, IPT>(u, s * 8 + k));
+    }
+    if (INPLACE) __syncthreads();
+#pragma unroll
+    for (int s = 0; s < IPT; ++s) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int j = u + s * US + q * (N / 8);
+            if (R == 8) dft8<T, INV>(v[s] + q * R);
+            else if (R == 4) dft4<T, INV>(v[s] + q * R);
+            else dft2<T, INV>(v[s] + q * R);
+            c2<T>* dst = tile + j * R * LD + c;
+#pragma unroll
+            for (int r = 0; r < R; ++r) dst[r * LD] = v[s][q * R + r];
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T, int N, bool INV, int IPT, int LD, int NS, int NS_END>
+__device__ __forceinline__ void radix8_until(c2<T>* tile, int c, int u, const c2<T>* tw) {
+    if constexpr (NS < NS_END) {
+        stockham_stage<T, N, 8, INV, IPT, LD, NS>(tile, c, u, tw);
+        radix8_until<T, N, INV, IPT, LD, NS * 8, NS_END>(tile, c, u, tw);
+    }
+}
+
+// Last radix-8 stage (NS = N/8) from the tile, results to store(e, value): the butterfly
+// at slot j writes points j + r N/8.  No barrier at the end.
+template <typename T, int N, bool INV, int IPT, int LD, class Store>
+__device__ __forceinline__ void last_stage(const c2<T>* tile, int c, int u, const c2<T>* tw, Store&& store) {
+    constexpr int US = N / (8 * IPT);
+    c2<T> v[IPT][8];
+    const c2<T>* src = tile + u * LD + c;
+#pragma unroll
+    for (int s = 0; s < IPT; ++s) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[s][r] = src[(s * US + r * (N / 8)) * LD];
+    }
+#pragma unroll
+    for (int s = 0; s < IPT; ++s) {
+        const int j = u + s * US;
+#pragma unroll
+        for (int r = 1; r < 8; ++r) {
+            c2<T> w = tw[j * r];
+            if (INV) w.y = -w.y;
+            v[s][r] = cmul<T>(v[s][r], w);
+        }
+        dft8<T, INV>(v[s]);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) store(j + r * (N / 8), v[s][r]);
+    }
+}
+
+// fft_columns with the input read by load(b, e) (b as in lead_row) inside the first stage
+// and the output handed to store(e, value) by the last: the tile holds only the
+// intermediate stages, so a pass moves each point through shared memory twice (not four
+// times) for N = 512.  The caller reuses the tile only after a barrier.
+template <typename T, int LOGN, bool INV, int IPT, int LD, class Load, class Store>
+__device__ __forceinline__ void fft_columns_io(c2<T>* tile, int c, int u, const c2<T>* tw, Load&& load,
+                                               Store&& store) {
+    constexpr int N = 1 << LOGN;
+    if constexpr (N == 8) {
+        c2<T> v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = load(k, k);
+        dft8<T, INV>(v);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) store(k, v[k]);
+    } else {
+        lead_stage<T, LOGN, INV, IPT, LD, false>(tile, c, u, load);
+        radix8_until<T, N, INV, IPT, LD, LeadRadix<LOGN>::R, N / 8>(tile, c, u, tw);
+        last_stage<T, N, INV, IPT, LD>(tile, c, u, tw, store);
+    }
+}
+
+// fft_columns whose first stage reads its operands through load(b, e) from the tile itself
+// (a conversion of the stored values fused into that stage); the result stays in the tile.
+template <typename T, int LOGN, bool INV, int IPT, int LD, class Load>
+__device__ __forceinline__ void fft_columns_in(c2<T>* tile, int c, int u, const c2<T>* tw, Load&& load) {
+    constexpr int N = 1 << LOGN;
+    lead_stage<T, LOGN, INV, IPT, LD, true>(tile, c, u, load);
+    radix8_until<T, N, INV, IPT, LD, LeadRadix<LOGN>::R, N>(tile, c, u, tw);
+}
+
 __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
 
 // Shape of the pencil passes for n = 2^LOGN: W pencils per CTA (W n / 8 <= 1024 butterfly

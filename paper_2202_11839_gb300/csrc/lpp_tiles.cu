@@ -389,6 +389,25 @@ __device__ __forceinline__ void tile_setup(const FusedArgs<T>& a, const FusedSlo
     }
 }
 
+// Forward x transform of the tile's pencils after the scatter.  A fixed-point tile is
+// converted back to floating point (value = integer x unit) inside the first FFT stage.
+// fixed is CTA-uniform.
+template <typename T, int LOGN>
+__device__ __forceinline__ void x_transform(c2<T>* tile, int c, int u, const c2<T>* tw, bool fixed, float unit) {
+    using S = FusedShape<T, LOGN>;
+    if constexpr (sizeof(T) == 4) {
+        if (fixed) {
+            const int2* ti = reinterpret_cast<const int2*>(tile) + c;
+            fft_columns_in<T, LOGN, false, S::IPT, S::LD>(tile, c, u, tw, [&](int, int e) {
+                const int2 q = ti[e * S::LD];
+                return mk<T>((T)((float)q.x * unit), (T)((float)q.y * unit));
+            });
+            return;
+        }
+    }
+    fft_columns<T, LOGN, false, S::IPT, S::LD>(tile, c, u, tw);
+}
+
 // One tile (tile_y, tile_z) of TY x TZ pencils of the slot blockIdx.y: particle ranges,
 // scatter, x transform, store of the kept x frequencies.  Every return is CTA-uniform.
 template <typename T, int LOGN>
@@ -504,13 +523,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int tile_y, in
         }
     }
     __syncthreads();
-    if (fixed) {
-        // fixed point back to floating point before the transform
-        const int* ti = reinterpret_cast<const int*>(tilef);
-        for (int i = tid; i < 2 * N * LD; i += S::THREADS) tilef[i] = (T)((float)ti[i] * finv);
-        __syncthreads();
-    }
-    fft_columns<T, LOGN, false, S::IPT, LD>(tile, tid & (W - 1), tid >> ilog2(W), tw);
+    x_transform<T, LOGN>(tile, tid & (W - 1), tid >> ilog2(W), tw, fixed, finv);
     for (int k = tid & (LPL - 1); k < nkept; k += LPL) {
         const int e = k <= a.nk_pos ? k : N - nkept + k;
         out[((cw / TY) * N + (cw & (TY - 1))) * N + e] = tile[e * LD + cw];
@@ -670,14 +683,7 @@ __device__ __forceinline__ void fused_tile2(const FusedArgs<T>& a, int tile_y, i
     }
     __syncthreads();
     c2<T>* tile = half ? tile1 : tile0;
-    if (fixed) {
-        T* tf = reinterpret_cast<T*>(tile);
-        const int* ti = reinterpret_cast<const int*>(tile);
-        const float inv = fi[half];
-        for (int i = th; i < 2 * N * LD; i += S::THREADS) tf[i] = (T)((float)ti[i] * inv);
-        __syncthreads();
-    }
-    fft_columns<T, LOGN, false, S::IPT, LD>(tile, th & (W - 1), th >> ilog2(W), tw);
+    x_transform<T, LOGN>(tile, th & (W - 1), th >> ilog2(W), tw, fixed, fi[half]);
     for (int k = th & (LPL - 1); k < nkept; k += LPL) {
         const int e = k <= a.nk_pos ? k : N - nkept + k;
         out[((cw / TY) * N + (cw & (TY - 1))) * N + e] = tile[e * LD + cw];
