@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--data", type=int, default=1_500_000)
     ap.add_argument("--randoms", type=int, default=15_000_000)
     ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--moment-mask", type=int, default=-1,
+                    help="bit mask of moment slots (default: all ten); smaller cases for profiling")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
@@ -345,8 +347,9 @@ def run_lpp(args):
     shp, rnd = wl.shapes, wl.randoms
     tt = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
     d_pos, d_shape, d_rpos, d_rnbar = tt(shp.pos), tt(shp.shape), tt(rnd.pos), tt(rnd.nbar)
+    moments = L.LPP_WANT_ALL if args.moment_mask < 0 else args.moment_mask
     common = dict(origin=wl.origin, observer=wl.observer, pole=wl.pole, scheme=L.LPP_TSC, interlace=True,
-                  compensate=True, precision=L.LPP_FP32, moments=L.LPP_WANT_ALL, max_shapes=shp.count,
+                  compensate=True, precision=L.LPP_FP32, moments=moments, max_shapes=shp.count,
                   max_randoms=rnd.count, batch=args.batch)
     plan = L.Plan(wl.n, wl.box, wl.k_edges, **common)
     plan.assign(L.LPP_SHAPES, d_pos, None, None, d_shape, L.LPP_SHAPE_TENSOR6)

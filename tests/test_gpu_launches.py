@@ -1,17 +1,28 @@
 """lpp_plan_launch_count against the kernels the CUDA profiling interface records for one
 estimate (torch.profiler's CUPTI activity trace), so the launch count the benchmark reports
-is the library's real one."""
-import numpy as np
-import pytest
+is the library's real one.  The profiling runs in a fresh interpreter: an activity trace
+taken after other CUDA work in a long test process may come back empty."""
+import json
+import os
+import subprocess
+import sys
 
-from tests.parity_util import default_edges, make_case
+import pytest
 
 pytestmark = pytest.mark.gpu
 
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
-def _plan(L, cat, n, interlace, n_rand):
-    import torch
+SCRIPT = r"""
+import json, sys
+import numpy as np, torch
+from torch.profiler import ProfilerActivity, profile
+from paper_2202_11839_gb300 import lpp as L
+from tests.parity_util import default_edges, make_case
+
+def plan_for(n, interlace, n_rand):
     box = 300.0
+    cat = make_case("tensor", n, 4000, 11, n_rand=n_rand, dtype=np.float32)
     plan = L.Plan(n, box, default_edges(n, box), observer=(150.0, 150.0, -900.0), scheme=L.LPP_TSC,
                   interlace=interlace, precision=L.LPP_FP32, moments=L.LPP_WANT_ALL,
                   max_shapes=cat["pos"].shape[1], max_randoms=n_rand)
@@ -23,36 +34,35 @@ def _plan(L, cat, n, interlace, n_rand):
         plan.assign(L.LPP_RANDOMS, keep[3], keep[4], keep[5])
     return plan, keep
 
+plans = [plan_for(32, True, 3000), plan_for(64, False, 0)]
+for p, _ in plans:
+    p.multipoles()
+torch.cuda.synchronize()
+with profile(activities=[ProfilerActivity.CPU, ProfilerActivity.CUDA]) as prof:
+    for p, _ in plans:
+        p.multipoles()
+    torch.cuda.synchronize()
+names = [e.name for e in prof.events() if e.device_type == torch.autograd.DeviceType.CUDA]
+kernels = [n for n in names if "memcpy" not in n.lower() and "memset" not in n.lower()]
+counts = [p.launch_count() for p, _ in plans]
+timed = []
+for p, _ in plans:
+    p.set_timing(True)
+    p.multipoles()
+    timed.append(p.launch_count())
+print(json.dumps({"counts": counts, "timed": timed, "kernels": len(kernels), "names": sorted(set(kernels))}))
+"""
+
 
 def test_launch_count_matches_profiled_kernels():
     """Two plans (32^3 interlaced with randoms, 64^3 plain) in one profiler session: the
-    device kernels recorded equal the sum of the two reported counts."""
-    import torch
-    from torch.profiler import ProfilerActivity, profile
-
-    from paper_2202_11839_gb300 import lpp as L
-    plans, keep = [], []
-    for n, interlace, n_rand in ((32, True, 3000), (64, False, 0)):
-        cat = make_case("tensor", n, 4000, 11, n_rand=n_rand, dtype=np.float32)
-        p, k = _plan(L, cat, n, interlace, n_rand)
-        p.multipoles()
-        plans.append(p)
-        keep.append(k)
-    torch.cuda.synchronize()
-    with profile(activities=[ProfilerActivity.CPU, ProfilerActivity.CUDA]) as prof:
-        for p in plans:
-            p.multipoles()
-        torch.cuda.synchronize()
-    kernels = [e for e in prof.events() if e.device_type == torch.autograd.DeviceType.CUDA
-               and "memcpy" not in e.name.lower() and "memset" not in e.name.lower()]
-    if not kernels:
+    device kernels recorded equal the sum of the two reported counts; timing on or off
+    launches the same kernels."""
+    r = subprocess.run([sys.executable, "-c", SCRIPT], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    assert min(d["counts"]) > 0
+    assert d["timed"] == d["counts"]
+    if d["kernels"] == 0:
         pytest.skip("the profiler recorded no device activity")
-    counts = [p.launch_count() for p in plans]
-    assert min(counts) > 0
-    assert sum(counts) == len(kernels), (counts, sorted({e.name for e in kernels}))
-    # timing on or off launches the same kernels
-    for p, c in zip(plans, counts):
-        p.set_timing(True)
-        p.multipoles()
-        assert p.launch_count() == c
-        p.close()
+    assert sum(d["counts"]) == d["kernels"], d
