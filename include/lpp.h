@@ -190,6 +190,11 @@ lpp_status lpp_batch_launch(lpp_batch_t batch, void* stream);
  * lpp_multipoles); returns the first failing mock's status (e.g. LPP_ERR_DOMAIN). */
 lpp_status lpp_batch_results(lpp_batch_t batch, lpp_result* results);
 const char* lpp_batch_last_error(lpp_batch_t batch);
+/* Kernels of the batch: *counted = the sum of the mocks' lpp_plan_launch_count figures
+ * when the batch was last enqueued or captured; *graph_kernels = the kernel nodes of the
+ * captured CUDA graph as the CUDA runtime lists them (-1 without a graph).  Host outputs.
+ * LPP_ERR_INVALID_ARG for a null argument, LPP_ERR_CUDA if the graph cannot be read. */
+lpp_status lpp_batch_launch_count(lpp_batch_t batch, long long* counted, long long* graph_kernels);
 
 /* ------------------------------------------------------------------ templates
  * Window-convolved theory templates (Sec. 3.2, Eqs. window_convolution_X_hankel and

@@ -1173,6 +1173,7 @@ struct lpp_batch_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool launched = false;
+    long long n_launch = 0;                  // kernels the mocks' estimates enqueued
     std::string err;
 };
 
@@ -1191,6 +1192,7 @@ static lpp_status batch_fail(lpp_batch_t b, lpp_status s, const std::string& m) 
 static lpp_status batch_enqueue(lpp_batch_t b, cudaStream_t root) {
     LPP_BCUDA(cudaEventRecord(b->start, root));
     for (size_t p = 0; p < b->plans.size(); ++p) LPP_BCUDA(cudaStreamWaitEvent(b->streams[p], b->start, 0));
+    b->n_launch = 0;
     for (size_t j = 0; j < b->plan_of.size(); ++j) {
         const int pi = b->plan_of[j];
         lpp_plan_t plan = b->plans[pi];
@@ -1205,6 +1207,7 @@ static lpp_status batch_enqueue(lpp_batch_t b, cudaStream_t root) {
         plan->stream = keep;
         plan->timer.enabled = timing;
         if (s != LPP_OK) return batch_fail(b, s, "mock " + std::to_string(j) + ": " + plan->err);
+        b->n_launch += plan->n_launch;
     }
     for (size_t p = 0; p < b->plans.size(); ++p) {
         LPP_BCUDA(cudaEventRecord(b->done[p], b->streams[p]));
@@ -1351,5 +1354,25 @@ extern "C" const char* lpp_batch_last_error(lpp_batch_t b) { return b ? b->err.c
 extern "C" lpp_status lpp_plan_launch_count(lpp_plan_t plan, long long* launches) {
     if (!plan || !launches) return LPP_ERR_INVALID_ARG;
     *launches = plan->n_launch;
+    return LPP_OK;
+}
+
+extern "C" lpp_status lpp_batch_launch_count(lpp_batch_t b, long long* counted, long long* graph_kernels) {
+    if (!b || !counted || !graph_kernels) return LPP_ERR_INVALID_ARG;
+    *counted = b->n_launch;
+    *graph_kernels = -1;
+    if (b->graph) {
+        size_t num = 0;
+        LPP_BCUDA(cudaGraphGetNodes(b->graph, nullptr, &num));
+        std::vector<cudaGraphNode_t> nodes(num);
+        if (num) LPP_BCUDA(cudaGraphGetNodes(b->graph, nodes.data(), &num));
+        long long k = 0;
+        for (size_t i = 0; i < num; ++i) {
+            cudaGraphNodeType t;
+            LPP_BCUDA(cudaGraphNodeGetType(nodes[i], &t));
+            if (t == cudaGraphNodeTypeKernel) ++k;
+        }
+        *graph_kernels = k;
+    }
     return LPP_OK;
 }

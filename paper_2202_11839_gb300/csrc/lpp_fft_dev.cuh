@@ -210,6 +210,35 @@ __device__ __forceinline__ void last_stage(const c2<T>* tile, int c, int u, cons
     }
 }
 
+// Last radix-8 stage (NS = N/8) with one warp per pencil: lane l of the warp for pencil c
+// takes the butterflies at slots j = l + 32 s (s < IPT), so the points j + r N/8 that it
+// hands to store(e, value) are consecutive across the warp (a coalesced store along the
+// pencil).  twr holds each leg's twiddles by slot, twr[(r - 1) N/8 + j] = w^(j r), so the
+// lanes read consecutive words.  No barrier at the end.
+template <typename T, int N, bool INV, int IPT, int LD, class Store>
+__device__ __forceinline__ void last_stage_warp(const c2<T>* tile, int c, int l, const c2<T>* twr, Store&& store) {
+    static_assert(N / 8 == 32 * IPT, "one warp covers the N/8 butterfly slots of a pencil");
+    c2<T> v[IPT][8];
+#pragma unroll
+    for (int s = 0; s < IPT; ++s) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[s][r] = tile[(l + 32 * s + r * (N / 8)) * LD + c];
+    }
+#pragma unroll
+    for (int s = 0; s < IPT; ++s) {
+        const int j = l + 32 * s;
+#pragma unroll
+        for (int r = 1; r < 8; ++r) {
+            c2<T> w = twr[(r - 1) * (N / 8) + j];
+            if (INV) w.y = -w.y;
+            v[s][r] = cmul<T>(v[s][r], w);
+        }
+        dft8<T, INV>(v[s]);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) store(j + r * (N / 8), v[s][r]);
+    }
+}
+
 // fft_columns with the input read by load(b, e) (b as in lead_row) inside the first stage
 // and the output handed to store(e, value) by the last: the tile holds only the
 // intermediate stages, so a pass moves each point through shared memory twice (not four

@@ -276,6 +276,11 @@ struct FusedShape {
     // resident CTAs per SM the register budget is sized for (shared memory allows 3 at
     // n = 512 in FP32)
     static constexpr int MINB = (sizeof(T) == 4 && (LOGN == 9 || LOGN == 8)) ? 2 : 1;
+    // the last x stage runs one warp per pencil and stores straight to the grid when a
+    // warp's 32 lanes cover the N/8 butterfly slots (N >= 256); it reads the per-leg
+    // twiddle table of TWR entries after the tiles
+    static constexpr bool WARP_OUT = (N / 8 == 32 * IPT) && (THREADS == 32 * W);
+    static constexpr int TWR = WARP_OUT ? 7 * (N / 8) : 0;
 };
 
 // Set-up of one tile (shared by the one- and two-slot tiles): the particles touching the
@@ -286,8 +291,9 @@ struct FusedShape {
 // twiddles.  NT: threads of the CTA.
 template <typename T, int LOGN, int NT>
 __device__ __forceinline__ void tile_setup(const FusedArgs<T>& a, const FusedSlot& sl, int y0, int z0, c2<T>* tw,
-                                           c2<T>* tiles, int tile_elems, int* r_begin, int* r_pref, int* r_src,
-                                           int& n_ranges, int (*rcount)[FusedShape<T, LOGN>::TY + 3], int& wmax) {
+                                           c2<T>* twr, c2<T>* tiles, int tile_elems, int* r_begin, int* r_pref,
+                                           int* r_src, int& n_ranges, int (*rcount)[FusedShape<T, LOGN>::TY + 3],
+                                           int& wmax) {
     using S = FusedShape<T, LOGN>;
     constexpr int N = S::N, TY = S::TY, TZ = S::TZ;
     const int tid = threadIdx.x;
@@ -385,27 +391,57 @@ __device__ __forceinline__ void tile_setup(const FusedArgs<T>& a, const FusedSlo
         }
     } else {
         for (int i = tid - 32; i < N; i += NT - 32) tw[i] = a.tw[i];
+        if constexpr (S::TWR > 0) {
+            for (int i = tid - 32; i < S::TWR; i += NT - 32) {
+                const int r = i / (N / 8) + 1, j = i - (r - 1) * (N / 8);
+                twr[i] = a.tw[j * r];
+            }
+        }
         for (int i = tid - 32; i < tile_elems; i += NT - 32) tiles[i] = mk<T>((T)0, (T)0);
     }
 }
 
-// Forward x transform of the tile's pencils after the scatter.  A fixed-point tile is
-// converted back to floating point (value = integer x unit) inside the first FFT stage.
-// fixed is CTA-uniform.
+// Forward x transform of the tile's pencils after the scatter, and the store of the kept x
+// frequencies to the grid (out: the tile's first pencil; pencil c = lz TY + ly at
+// out + (lz n + ly) n).  A fixed-point tile is converted back to floating point (value =
+// integer x unit) inside the first FFT stage.  t: the thread's index among the S::THREADS
+// that transform this tile; fixed is CTA-uniform.
 template <typename T, int LOGN>
-__device__ __forceinline__ void x_transform(c2<T>* tile, int c, int u, const c2<T>* tw, bool fixed, float unit) {
+__device__ __forceinline__ void x_transform(c2<T>* tile, int t, const c2<T>* tw, const c2<T>* twr, bool fixed,
+                                            float unit, c2<T>* out, int nk_pos, int nk_neg) {
     using S = FusedShape<T, LOGN>;
+    constexpr int N = S::N, W = S::W, LD = S::LD, IPT = S::IPT, TY = S::TY, R0 = LeadRadix<LOGN>::R;
+    const int c = t & (W - 1), u = t >> ilog2(W);
+    bool converted = false;
     if constexpr (sizeof(T) == 4) {
         if (fixed) {
             const int2* ti = reinterpret_cast<const int2*>(tile) + c;
-            fft_columns_in<T, LOGN, false, S::IPT, S::LD>(tile, c, u, tw, [&](int, int e) {
-                const int2 q = ti[e * S::LD];
+            lead_stage<T, LOGN, false, IPT, LD, true>(tile, c, u, [&](int, int e) {
+                const int2 q = ti[e * LD];
                 return mk<T>((T)((float)q.x * unit), (T)((float)q.y * unit));
             });
-            return;
+            converted = true;
         }
     }
-    fft_columns<T, LOGN, false, S::IPT, S::LD>(tile, c, u, tw);
+    if (!converted) stockham_stage<T, N, R0, false, IPT, LD, 1>(tile, c, u, tw);
+    if constexpr (S::WARP_OUT) {
+        radix8_until<T, N, false, IPT, LD, R0, N / 8>(tile, c, u, tw);
+        const int pc = t >> 5;
+        c2<T>* po = out + ((size_t)(pc / TY) * N + (pc & (TY - 1))) * N;
+        last_stage_warp<T, N, false, IPT, LD>(tile, pc, t & 31, twr, [&](int e, c2<T> v) {
+            if (kept(e, N, nk_pos, nk_neg)) po[e] = v;
+        });
+    } else {
+        radix8_until<T, N, false, IPT, LD, R0, N>(tile, c, u, tw);
+        // LPL consecutive threads store one pencil (coalesced along x)
+        constexpr int LPL = S::THREADS / W;
+        const int cw = t / LPL;
+        const int nkept = nk_pos + 1 + nk_neg;
+        for (int k = t & (LPL - 1); k < nkept; k += LPL) {
+            const int e = k <= nk_pos ? k : N - nkept + k;
+            out[((cw / TY) * N + (cw & (TY - 1))) * N + e] = tile[e * LD + cw];
+        }
+    }
 }
 
 // One tile (tile_y, tile_z) of TY x TZ pencils of the slot blockIdx.y: particle ranges,
@@ -422,6 +458,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int tile_y, in
     __shared__ int wmax;
     c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
     c2<T>* tile = tw + N;
+    c2<T>* twr = tile + N * LD;
     T* tilef = reinterpret_cast<T*>(tile);
     const int tid = threadIdx.x;
     const int y0 = tile_y * TY;
@@ -429,7 +466,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int tile_y, in
     const FusedSlot& sl = a.slots[blockIdx.y];
     c2<T>* out = a.grids + (size_t)sl.grid * a.grid_stride + ((size_t)z0 * N + y0) * N;
 
-    tile_setup<T, LOGN, S::THREADS>(a, sl, y0, z0, tw, tile, N * LD, r_begin, r_pref, r_src, n_ranges, rcount,
+    tile_setup<T, LOGN, S::THREADS>(a, sl, y0, z0, tw, twr, tile, N * LD, r_begin, r_pref, r_src, n_ranges, rcount,
                                     wmax);
     __syncthreads();
     const int nr = n_ranges;
@@ -523,11 +560,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int tile_y, in
         }
     }
     __syncthreads();
-    x_transform<T, LOGN>(tile, tid & (W - 1), tid >> ilog2(W), tw, fixed, finv);
-    for (int k = tid & (LPL - 1); k < nkept; k += LPL) {
-        const int e = k <= a.nk_pos ? k : N - nkept + k;
-        out[((cw / TY) * N + (cw & (TY - 1))) * N + e] = tile[e * LD + cw];
-    }
+    x_transform<T, LOGN>(tile, tid, tw, twr, fixed, finv, out, a.nk_pos, a.nk_neg);
 }
 
 __global__ void k_plane_mask(const int* __restrict__ off0, const int* __restrict__ off1, const int* __restrict__ off2,
@@ -596,7 +629,8 @@ void fused_geometry(int n, size_t elem_bytes, int* ty, int* tz, int* ipt, int* t
     const int t1 = w * n / 8;
     *ipt = t1 <= 512 ? 1 : (t1 <= 1024 ? 2 : 4);
     *threads = t1 / *ipt;
-    *smem = (size_t)(n + n * (w + 1)) * 2 * elem_bytes;
+    const bool warp_out = n / 8 == 32 * *ipt && *threads == 32 * w;
+    *smem = (size_t)(n + n * (w + 1) + (warp_out ? 7 * (n / 8) : 0)) * 2 * elem_bytes;
 }
 
 // Two interlaced channel slots (2 blockIdx.y, 2 blockIdx.y + 1: single-source coefficient
@@ -616,11 +650,13 @@ __device__ __forceinline__ void fused_tile2(const FusedArgs<T>& a, int tile_y, i
     c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
     c2<T>* tile0 = tw + N;
     c2<T>* tile1 = tile0 + N * LD;
+    c2<T>* twr = tile1 + N * LD;
     const int tid = threadIdx.x;
     const int y0 = tile_y * TY, z0 = tile_z * TZ;
     const FusedSlot& s0 = a.slots[2 * blockIdx.y];
     const FusedSlot& s1 = a.slots[2 * blockIdx.y + 1];
-    tile_setup<T, LOGN, NT>(a, s0, y0, z0, tw, tile0, 2 * N * LD, r_begin, r_pref, r_src, n_ranges, rcount, wmax);
+    tile_setup<T, LOGN, NT>(a, s0, y0, z0, tw, twr, tile0, 2 * N * LD, r_begin, r_pref, r_src, n_ranges, rcount,
+                            wmax);
     __syncthreads();
     const int nr = n_ranges;
     const int total = r_pref[nr];
@@ -683,11 +719,7 @@ __device__ __forceinline__ void fused_tile2(const FusedArgs<T>& a, int tile_y, i
     }
     __syncthreads();
     c2<T>* tile = half ? tile1 : tile0;
-    x_transform<T, LOGN>(tile, th & (W - 1), th >> ilog2(W), tw, fixed, fi[half]);
-    for (int k = th & (LPL - 1); k < nkept; k += LPL) {
-        const int e = k <= a.nk_pos ? k : N - nkept + k;
-        out[((cw / TY) * N + (cw & (TY - 1))) * N + e] = tile[e * LD + cw];
-    }
+    x_transform<T, LOGN>(tile, th, tw, twr, fixed, fi[half], out, a.nk_pos, a.nk_neg);
 }
 
 template <typename T, int LOGN>
@@ -749,13 +781,13 @@ template <typename T, int LOGN>
 static cudaError_t launch_fused_n(const FusedArgs<T>& a, int n_tiles, cudaStream_t st) {
     using S = FusedShape<T, LOGN>;
     if (a.ty != S::TY || a.tz != S::TZ) return cudaErrorInvalidConfiguration;
-    const size_t smem = (size_t)(S::N + S::N * S::LD) * sizeof(c2<T>);
+    const size_t smem = (size_t)(S::N + S::N * S::LD + S::TWR) * sizeof(c2<T>);
     cudaFuncSetAttribute(k_assign_xfft<T, LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if constexpr (sizeof(T) == 4 && (LOGN == 8 || LOGN == 9)) {
         if (a.dual) {
             // two slots per CTA (FusedArgs::dual: even slot count, interlaced single-source
             // coefficient slots, a tile-row list)
-            const size_t smem2 = (size_t)(S::N + 2 * S::N * S::LD) * sizeof(c2<T>);
+            const size_t smem2 = (size_t)(S::N + 2 * S::N * S::LD + S::TWR) * sizeof(c2<T>);
             cudaFuncSetAttribute(k_assign_xfft2<T, LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
             int dev = 0, sms = 152;
             if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

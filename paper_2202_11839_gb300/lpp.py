@@ -68,6 +68,7 @@ EXPORTS = {
     "lpp_batch_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lpp_batch_results": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lpp_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "lpp_batch_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "lpp_plan_destroy": (None, [C.c_void_p]),
     "lpp_plan_workspace_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "lpp_plan_set_workspace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
@@ -591,6 +592,12 @@ class Batch:
             out.append(Estimate(p[..., 0] + 1j * p[..., 1], raw[..., 0] + 1j * raw[..., 1], km, nm, r.norm_auto,
                                 r.norm_cross, r.norm_dd, r.shot_plus, r.shot_dd, r.alpha))
         return out
+
+    def launch_count(self):
+        """(kernels the mocks' estimates enqueued, kernel nodes of the captured graph or -1)."""
+        a, b = C.c_longlong(), C.c_longlong()
+        self._check(self.lib.lpp_batch_launch_count(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def close(self):
         if getattr(self, "h", None):

@@ -66,3 +66,22 @@ def test_launch_count_matches_profiled_kernels():
     if d["kernels"] == 0:
         pytest.skip("the profiler recorded no device activity")
     assert sum(d["counts"]) == d["kernels"], d
+
+
+def test_launch_count_matches_graph_kernel_nodes():
+    """Three mocks on two plans captured into one CUDA graph: the kernel nodes the CUDA
+    runtime lists in the graph equal the sum of the counts the plans reported while the
+    batch was captured; a second plain (uncaptured) batch counts the same."""
+    from paper_2202_11839_gb300 import batch as B
+    mocks = B.make_mocks(3, (20_000, 60_000), (32, 64), n_base=2, n_field=32)
+    tuning = {32: B.Tuning(32, 4), 64: B.Tuning(64, 8)}
+    run = B.BatchRun(mocks, tuning, use_graph=True)
+    counted, nodes = run.batch.launch_count()
+    assert counted > 0 and nodes == counted
+    run.run()
+    run.close()
+    plain = B.BatchRun(mocks, tuning, use_graph=False)
+    plain.run()
+    counted2, nodes2 = plain.batch.launch_count()
+    assert nodes2 == -1 and counted2 == counted
+    plain.close()
