@@ -71,6 +71,7 @@ struct lpp_plan_s {
     size_t off_rsq = 0;                  // [n_coeff_rows] FP64 sums of squares
     size_t off_trows = 0;                // [2][256] z-tile rows to visit, then [2] counts
     size_t off_plive = 0;                // [3][n*n] bytes: x pencils reached per role
+    size_t off_tranges = 0;              // per-tile range records of the two-slot fused passes
     int fty = 4, ftz = 4;
     int n_partner = 0;
     int out_rows = 0;
@@ -82,6 +83,12 @@ struct lpp_plan_s {
     int n_sm = 152;
     long long n_launch = 0;   // kernels launched by the last estimate
 };
+
+// FP32 interlaced grids of 256^3 or 512^3: channel batches with an even slot count run the
+// two-slot fused kernel (with per-tile range records)
+static bool two_slot_grid(lpp_plan_t p) {
+    return !p->fp64 && p->d.interlace && (p->d.n == 256 || p->d.n == 512) && p->d.n / p->ftz <= 256;
+}
 
 static lpp_status fail(lpp_plan_t p, lpp_status s, const std::string& msg) {
     if (p) p->err = msg;
@@ -300,6 +307,7 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
     plan->off_rsq = take((size_t)std::max(1, plan->n_coeff_rows) * sizeof(double));
     plan->off_trows = take((2 * 256 + 2) * sizeof(int));
     plan->off_plive = take((size_t)3 * n * n);
+    plan->off_tranges = take(two_slot_grid(plan) ? tile_range_bytes(n, plan->fty, plan->ftz) : sizeof(int));
     plan->off_wout = take((size_t)kWindowChannels * 256 * 2 * sizeof(double));
     plan->off_wthr = take(257 * sizeof(int));
     plan->off_partner = take((size_t)std::max(1, plan->n_partner) * n3 * cs);
@@ -806,6 +814,25 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
     // 3. channel fields, a batch of grids at a time
     const int per_grid = il ? 1 : 2;
     cb.partner_mode = 0;
+    // range records of the shape tiles, shared by every two-slot channel launch
+    int* tranges = nullptr;
+    bool any_dual = false;
+    for (int c0 = 0; c0 < n_ch; c0 += plan->batch_ch) any_dual |= (std::min(n_ch, c0 + plan->batch_ch) - c0) % 2 == 0;
+    if (two_slot_grid(plan) && use_rows && any_dual) {
+        tranges = (int*)(plan->ws + plan->off_tranges);
+        FusedArgs<T> fr = fa;
+        FusedSlot fs{};
+        fs.n_src = 1;
+        fs.src[0] = FusedSrc{LPP_SHAPES, nullptr, 0};
+        fr.slots[0] = fs;
+        fr.n_slots = 1;
+        fr.trows = trows;
+        fr.trow_count = tcount;
+        if (tm) tm->begin(KK_OTHER, st);
+        LPP_CUDA(launch_tile_ranges<T>(fr, tranges, st));
+        nl += 1;
+        if (tm) tm->end(KK_OTHER, st, (double)tile_range_bytes(n, plan->fty, plan->ftz) * tile_frac(1 << LPP_SHAPES));
+    }
     for (int c0 = 0; c0 < n_ch; c0 += plan->batch_ch) {
         const int c1 = std::min(n_ch, c0 + plan->batch_ch);
         const int nch = c1 - c0;
@@ -842,9 +869,11 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         }
         fa.trows = use_rows ? trows : nullptr;
         fa.trow_count = use_rows ? tcount : nullptr;
-        fa.dual = (!plan->fp64 && il && use_rows && (n == 256 || n == 512) && fa.n_slots % 2 == 0) ? 1 : 0;
+        fa.dual = (tranges && fa.n_slots % 2 == 0) ? 1 : 0;
+        fa.tranges = fa.dual ? tranges : nullptr;
         { lpp_status s0 = assign_fused(sh.count); if (s0 != LPP_OK) return s0; }
         fa.dual = 0;
+        fa.tranges = nullptr;
         FftGeom gc = geom;
         gc.pmask = pmask;
         gc.q_max = plan->thr[nb];

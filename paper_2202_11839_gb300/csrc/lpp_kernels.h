@@ -218,6 +218,7 @@ struct FusedArgs {
     const int* trow_count;
     int skip_empty;                      // empty tiles store nothing (the y pass fills their zeros)
     int dual;                            // FP32 n = 256/512: two slots per CTA (see k_assign_xfft2)
+    const int* tranges;                  // two-slot launches: per-tile range records, or null
 };
 
 void fused_geometry(int n, size_t elem_bytes, int* ty, int* tz, int* ipt, int* threads, size_t* smem);
@@ -239,6 +240,12 @@ cudaError_t launch_pencil_sort(const T* pos, const T* w, long long count, long l
                                T* su, T* sw, int* perm, int* err, cudaStream_t st);
 template <typename T>
 cudaError_t launch_assign_xfft(const FusedArgs<T>& a, cudaStream_t st);
+// Range records (particle ranges and fixed-point bound) of every tile of the two-slot
+// persistent enumeration over a.trows, for the sources of a.slots[0]; FP32, n = 256 or 512.
+// out: tile_range_bytes(n, ty, tz) bytes.  One launch.
+template <typename T>
+cudaError_t launch_tile_ranges(const FusedArgs<T>& a, int* out, cudaStream_t st);
+size_t tile_range_bytes(int n, int ty, int tz);
 
 // --------------------------------------------------------------------- combine
 struct CombineChan {

@@ -283,12 +283,82 @@ struct FusedShape {
     static constexpr int TWR = WARP_OUT ? 7 * (N / 8) : 0;
 };
 
-// Set-up of one tile (shared by the one- and two-slot tiles): the particles touching the
-// tile, as TZ+3 z rows of keys y0-2 .. y0+TY per source of slot `sl`, one or two contiguous
-// ranges each (the y window may wrap), and for fixed-point slots the largest 4 x 4 key-row
-// window count.  Lane l of warp 0 takes row l (source l / (TZ+3)); a warp scan places the
-// ranges.  Meanwhile the other warps clear `tile_elems` elements of the tiles and load the
-// twiddles.  NT: threads of the CTA.
+// The particle ranges of the tile at (y0, z0) for the sources of slot `sl`, found by one
+// warp (all 32 lanes): TZ+3 z rows of keys y0-2 .. y0+TY per source, one or two contiguous
+// ranges each (the y window may wrap).  Lane l takes row l (source l / (TZ+3)); a warp scan
+// places the ranges.  With want_wmax, also the largest 4 x 4 key-row window count of source
+// 0 (the fixed-point bound).  rcount: the warp's scratch.
+template <typename T, int LOGN>
+__device__ __forceinline__ void warp_ranges(const FusedArgs<T>& a, const FusedSlot& sl, int y0, int z0, int lane,
+                                            int* r_begin, int* r_pref, int* r_src, int& n_ranges,
+                                            int (*rcount)[FusedShape<T, LOGN>::TY + 3], int& wmax, bool want_wmax) {
+    using S = FusedShape<T, LOGN>;
+    constexpr int N = S::N, TY = S::TY, TZ = S::TZ;
+    int bb[2] = {0, 0}, ee[2] = {0, 0}, m = 0, s_idx = 0;
+    if (lane < sl.n_src * (TZ + 3)) {
+        s_idx = lane / (TZ + 3);
+        const int dz = lane - s_idx * (TZ + 3);
+        const int* off = a.cat[sl.src[s_idx].cat].off;
+        const int zr = (z0 - 2 + dz) & (N - 1);
+        const int ylo = y0 - 2, yhi = y0 + TY;   // inclusive
+        bb[m] = off[zr * N + (ylo < 0 ? 0 : ylo)];
+        ee[m++] = off[zr * N + (yhi >= N ? N - 1 : yhi) + 1];
+        if (ylo < 0) { bb[m] = off[zr * N + N + ylo]; ee[m++] = off[zr * N + N]; }
+        if (yhi >= N) { bb[m] = off[zr * N]; ee[m++] = off[zr * N + (yhi - N) + 1]; }
+    }
+    int nr_l = 0, cnt_l = 0;
+    for (int q = 0; q < m; ++q)
+        if (ee[q] > bb[q]) { ++nr_l; cnt_l += ee[q] - bb[q]; }
+    int nr_inc = nr_l, cnt_inc = cnt_l;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int a1 = __shfl_up_sync(0xffffffffu, nr_inc, d);
+        const int a2 = __shfl_up_sync(0xffffffffu, cnt_inc, d);
+        if (lane >= d) { nr_inc += a1; cnt_inc += a2; }
+    }
+    int nr = nr_inc - nr_l, acc = cnt_inc - cnt_l;
+    for (int q = 0; q < m; ++q) {
+        if (ee[q] <= bb[q]) continue;
+        r_begin[nr] = bb[q];
+        r_src[nr] = s_idx;
+        r_pref[nr] = acc;
+        acc += ee[q] - bb[q];
+        ++nr;
+    }
+    if (lane == 31) {
+        r_pref[nr_inc] = cnt_inc;
+        n_ranges = nr_inc;
+    }
+    if (want_wmax) {
+        // a cell (y, z) of the tile receives only from the key rows y-2..y+1, z-2..z+1:
+        // the largest such 4 x 4 window sum bounds the contributions of any one cell
+        if (lane < TZ + 3) {
+            const int* off = a.cat[sl.src[0].cat].off;
+            const int zr = (z0 - 2 + lane) & (N - 1);
+#pragma unroll
+            for (int dy = 0; dy < TY + 3; ++dy) {
+                const int yr = (y0 - 2 + dy) & (N - 1);
+                rcount[lane][dy] = off[zr * N + yr + 1] - off[zr * N + yr];
+            }
+        }
+        __syncwarp();
+        int wsum = 0;
+        if (lane < TY * TZ) {
+            const int ly = lane % TY, lz = lane / TY;   // cell (y0 + ly, z0 + lz): rows ly..ly+3
+#pragma unroll
+            for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+                for (int b2 = 0; b2 < 4; ++b2) wsum += rcount[lz + a2][ly + b2];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wsum = max(wsum, __shfl_down_sync(0xffffffffu, wsum, o));
+        if (lane == 0) wmax = wsum;
+    }
+}
+
+// Set-up of one tile (shared by the one- and two-slot tiles): warp 0 finds the particle
+// ranges (warp_ranges; the fixed-point bound for fixed-point slots) while the other warps
+// clear `tile_elems` elements of the tiles and load the twiddles.  NT: threads of the CTA.
 template <typename T, int LOGN, int NT>
 __device__ __forceinline__ void tile_setup(const FusedArgs<T>& a, const FusedSlot& sl, int y0, int z0, c2<T>* tw,
                                            c2<T>* twr, c2<T>* tiles, int tile_elems, int* r_begin, int* r_pref,
@@ -328,67 +398,8 @@ __device__ __forceinline__ void tile_setup(const FusedArgs<T>& a, const FusedSlo
         for (int i = tid; i < N; i += NT) tw[i] = a.tw[i];
         for (int i = tid; i < tile_elems; i += NT) tiles[i] = mk<T>((T)0, (T)0);
     } else if (tid < 32) {
-        const int lane = tid;
-        int bb[2] = {0, 0}, ee[2] = {0, 0}, m = 0, s_idx = 0;
-        if (lane < sl.n_src * (TZ + 3)) {
-            s_idx = lane / (TZ + 3);
-            const int dz = lane - s_idx * (TZ + 3);
-            const int* off = a.cat[sl.src[s_idx].cat].off;
-            const int zr = (z0 - 2 + dz) & (N - 1);
-            const int ylo = y0 - 2, yhi = y0 + TY;   // inclusive
-            bb[m] = off[zr * N + (ylo < 0 ? 0 : ylo)];
-            ee[m++] = off[zr * N + (yhi >= N ? N - 1 : yhi) + 1];
-            if (ylo < 0) { bb[m] = off[zr * N + N + ylo]; ee[m++] = off[zr * N + N]; }
-            if (yhi >= N) { bb[m] = off[zr * N]; ee[m++] = off[zr * N + (yhi - N) + 1]; }
-        }
-        int nr_l = 0, cnt_l = 0;
-        for (int q = 0; q < m; ++q)
-            if (ee[q] > bb[q]) { ++nr_l; cnt_l += ee[q] - bb[q]; }
-        int nr_inc = nr_l, cnt_inc = cnt_l;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int a1 = __shfl_up_sync(0xffffffffu, nr_inc, d);
-            const int a2 = __shfl_up_sync(0xffffffffu, cnt_inc, d);
-            if (lane >= d) { nr_inc += a1; cnt_inc += a2; }
-        }
-        int nr = nr_inc - nr_l, acc = cnt_inc - cnt_l;
-        for (int q = 0; q < m; ++q) {
-            if (ee[q] <= bb[q]) continue;
-            r_begin[nr] = bb[q];
-            r_src[nr] = s_idx;
-            r_pref[nr] = acc;
-            acc += ee[q] - bb[q];
-            ++nr;
-        }
-        if (lane == 31) {
-            r_pref[nr_inc] = cnt_inc;
-            n_ranges = nr_inc;
-        }
-        if (sl.amax_a != nullptr) {
-            // a cell (y, z) of the tile receives only from the key rows y-2..y+1, z-2..z+1:
-            // the largest such 4 x 4 window sum bounds the contributions of any one cell
-            if (lane < TZ + 3) {
-                const int* off = a.cat[sl.src[0].cat].off;
-                const int zr = (z0 - 2 + lane) & (N - 1);
-#pragma unroll
-                for (int dy = 0; dy < TY + 3; ++dy) {
-                    const int yr = (y0 - 2 + dy) & (N - 1);
-                    rcount[lane][dy] = off[zr * N + yr + 1] - off[zr * N + yr];
-                }
-            }
-            __syncwarp();
-            int wsum = 0;
-            if (lane < TY * TZ) {
-                const int ly = lane % TY, lz = lane / TY;   // cell (y0 + ly, z0 + lz): rows ly..ly+3
-#pragma unroll
-                for (int a2 = 0; a2 < 4; ++a2)
-#pragma unroll
-                    for (int b2 = 0; b2 < 4; ++b2) wsum += rcount[lz + a2][ly + b2];
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) wsum = max(wsum, __shfl_down_sync(0xffffffffu, wsum, o));
-            if (lane == 0) wmax = wsum;
-        }
+        warp_ranges<T, LOGN>(a, sl, y0, z0, tid, r_begin, r_pref, r_src, n_ranges, rcount, wmax,
+                             sl.amax_a != nullptr);
     } else {
         for (int i = tid - 32; i < N; i += NT - 32) tw[i] = a.tw[i];
         if constexpr (S::TWR > 0) {
@@ -633,20 +644,42 @@ void fused_geometry(int n, size_t elem_bytes, int* ty, int* tz, int* ipt, int* t
     *smem = (size_t)(n + n * (w + 1) + (warp_out ? 7 * (n / 8) : 0)) * 2 * elem_bytes;
 }
 
+// Tile range records (k_tile_ranges): per tile of the persistent enumeration, kRec ints:
+// [0] range count, [1] fixed-point bound wmax, [kRecBegin..) first particle of each range,
+// [kRecPref..) running particle count before each range (and the total), [kRecSrc..) source.
+constexpr int kRec = 96, kRecBegin = 2, kRecPref = 32, kRecSrc = 64;
+
+// Tiles of a two-slot launch: twiddles and cleared tiles only (the ranges come from a record).
+template <typename T, int LOGN, int NT>
+__device__ __forceinline__ void tile_clear(const FusedArgs<T>& a, c2<T>* tw, c2<T>* twr, c2<T>* tiles,
+                                           int tile_elems) {
+    using S = FusedShape<T, LOGN>;
+    constexpr int N = S::N;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < N; i += NT) tw[i] = a.tw[i];
+    if constexpr (S::TWR > 0) {
+        for (int i = tid; i < S::TWR; i += NT) {
+            const int r = i / (N / 8) + 1, j = i - (r - 1) * (N / 8);
+            twr[i] = a.tw[j * r];
+        }
+    }
+    for (int i = tid; i < tile_elems; i += NT) tiles[i] = mk<T>((T)0, (T)0);
+}
+
 // Two interlaced channel slots (2 blockIdx.y, 2 blockIdx.y + 1: single-source coefficient
 // rows of the same catalogue) in one CTA of 2 x THREADS threads: one set-up, every particle
 // visit computes its stencils once for both tiles; the halves of the CTA transform and store
 // one tile each.  The tiles use fixed point only when both slots' units pass the guard.
 template <typename T, int LOGN>
-__device__ __forceinline__ void fused_tile2(const FusedArgs<T>& a, int tile_y, int tile_z) {
+__device__ __forceinline__ void fused_tile2(const FusedArgs<T>& a, int tile_y, int tile_z, const int* rec) {
     using S = FusedShape<T, LOGN>;
     constexpr int N = S::N, TY = S::TY, TZ = S::TZ, W = S::W, LD = S::LD;
     constexpr int NT = 2 * S::THREADS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int r_begin[S::MAXR], r_pref[S::MAXR + 1], r_src[S::MAXR];
-    __shared__ int n_ranges;
+    __shared__ int r_begin_s[S::MAXR], r_pref_s[S::MAXR + 1], r_src_s[S::MAXR];
+    __shared__ int n_ranges_s;
     __shared__ int rcount[TZ + 3][TY + 3];
-    __shared__ int wmax;
+    __shared__ int wmax_s;
     c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
     c2<T>* tile0 = tw + N;
     c2<T>* tile1 = tile0 + N * LD;
@@ -655,10 +688,17 @@ __device__ __forceinline__ void fused_tile2(const FusedArgs<T>& a, int tile_y, i
     const int y0 = tile_y * TY, z0 = tile_z * TZ;
     const FusedSlot& s0 = a.slots[2 * blockIdx.y];
     const FusedSlot& s1 = a.slots[2 * blockIdx.y + 1];
-    tile_setup<T, LOGN, NT>(a, s0, y0, z0, tw, twr, tile0, 2 * N * LD, r_begin, r_pref, r_src, n_ranges, rcount,
-                            wmax);
+    if (rec) {
+        tile_clear<T, LOGN, NT>(a, tw, twr, tile0, 2 * N * LD);
+    } else {
+        tile_setup<T, LOGN, NT>(a, s0, y0, z0, tw, twr, tile0, 2 * N * LD, r_begin_s, r_pref_s, r_src_s,
+                                n_ranges_s, rcount, wmax_s);
+    }
     __syncthreads();
-    const int nr = n_ranges;
+    const int* r_begin = rec ? rec + kRecBegin : r_begin_s;
+    const int* r_pref = rec ? rec + kRecPref : r_pref_s;
+    const int nr = rec ? rec[0] : n_ranges_s;
+    const int wmax = rec ? rec[1] : wmax_s;
     const int total = r_pref[nr];
     const int half = tid / S::THREADS, th = tid - half * S::THREADS;
     const FusedSlot& sh = half ? s1 : s0;
@@ -722,14 +762,66 @@ __device__ __forceinline__ void fused_tile2(const FusedArgs<T>& a, int tile_y, i
     x_transform<T, LOGN>(tile, th, tw, twr, fixed, fi[half], out, a.nk_pos, a.nk_neg);
 }
 
+// With range records (a.tranges) warp 0 loads the next tile's record into registers while
+// the CTA works on the current tile and stores it into the other record buffer at the end.
 template <typename T, int LOGN>
 __global__ void __launch_bounds__(2 * FusedShape<T, LOGN>::THREADS, 1) k_assign_xfft2(FusedArgs<T> a) {
     using S = FusedShape<T, LOGN>;
+    static_assert(S::MAXR <= kRecPref - kRecBegin && S::MAXR + 1 <= kRecSrc - kRecPref && S::MAXR <= kRec - kRecSrc,
+                  "range record layout");
     constexpr int NTY = S::N / S::TY;
+    __shared__ int recs[2][kRec];
     const int total = *a.trow_count * NTY;
+    const int tid = threadIdx.x;
+    if (a.tranges == nullptr) {
+        for (int t = blockIdx.x; t < total; t += gridDim.x) {
+            fused_tile2<T, LOGN>(a, t % NTY, a.trows[t / NTY], nullptr);
+            __syncthreads();
+        }
+        return;
+    }
+    if (tid < 32 && (int)blockIdx.x < total) {
+#pragma unroll
+        for (int k = 0; k < kRec / 32; ++k) recs[0][tid + 32 * k] = a.tranges[(size_t)blockIdx.x * kRec + tid + 32 * k];
+    }
+    __syncthreads();
+    int buf = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
-        fused_tile2<T, LOGN>(a, t % NTY, a.trows[t / NTY]);
+        const int tn = t + gridDim.x;
+        int pre[kRec / 32];
+        if (tid < 32 && tn < total) {
+#pragma unroll
+            for (int k = 0; k < kRec / 32; ++k) pre[k] = a.tranges[(size_t)tn * kRec + tid + 32 * k];
+        }
+        fused_tile2<T, LOGN>(a, t % NTY, a.trows[t / NTY], recs[buf]);
+        if (tid < 32 && tn < total) {
+#pragma unroll
+            for (int k = 0; k < kRec / 32; ++k) recs[buf ^ 1][tid + 32 * k] = pre[k];
+        }
         __syncthreads();
+        buf ^= 1;
+    }
+}
+
+// Range records of every tile of the persistent enumeration (tile t: y index t % (n/TY),
+// z-tile row trows[t / (n/TY)]) for the sources of slots[0], with the fixed-point bound:
+// one warp per tile, 8 per CTA.
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(256) k_tile_ranges(FusedArgs<T> a, int* __restrict__ out) {
+    using S = FusedShape<T, LOGN>;
+    constexpr int NTY = S::N / S::TY;
+    __shared__ int rec[8][kRec];
+    __shared__ int rcount[8][S::TZ + 3][S::TY + 3];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int total = *a.trow_count * NTY;
+    for (int t = blockIdx.x * 8 + w; t < total; t += gridDim.x * 8) {
+        const int y0 = (t % NTY) * S::TY, z0 = a.trows[t / NTY] * S::TZ;
+        warp_ranges<T, LOGN>(a, a.slots[0], y0, z0, lane, rec[w] + kRecBegin, rec[w] + kRecPref,
+                             rec[w] + kRecSrc, rec[w][0], rcount[w], rec[w][1], true);
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < kRec / 32; ++k) out[(size_t)t * kRec + lane + 32 * k] = rec[w][lane + 32 * k];
+        __syncwarp();
     }
 }
 
@@ -770,6 +862,23 @@ __global__ void __launch_bounds__(256) k_tile_rows(const int* __restrict__ pmask
     if (live) rows[base + __popc(b & ((1u << lane) - 1u))] = r;
     if (r == 255) *count = base + __popc(b);
 }
+
+template <typename T>
+cudaError_t launch_tile_ranges(const FusedArgs<T>& a, int* out, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (a.trows == nullptr || a.trow_count == nullptr) return cudaErrorInvalidValue;
+        if (a.n == 256 || a.n == 512) {
+            const int tiles = (a.n / a.ty) * (a.n / a.tz);
+            const int blocks = std::max(1, std::min((tiles + 7) / 8, 152 * 8));
+            if (a.n == 256) k_tile_ranges<T, 8><<<blocks, 256, 0, st>>>(a, out);
+            else k_tile_ranges<T, 9><<<blocks, 256, 0, st>>>(a, out);
+            return cudaGetLastError();
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+size_t tile_range_bytes(int n, int ty, int tz) { return (size_t)(n / ty) * (n / tz) * kRec * sizeof(int); }
 
 cudaError_t launch_tile_rows(const int* pmask, int bits, int n, int tz, int* rows, int* count, cudaStream_t st) {
     if (n / tz > 256) return cudaErrorInvalidValue;
@@ -832,6 +941,8 @@ template cudaError_t launch_pencil_sort<float>(const float*, const float*, long 
 template cudaError_t launch_pencil_sort<double>(const double*, const double*, long long, long long, int, double,
                                                 const double*, int*, int*, int*, int*, int*, double*, double*, int*, int*,
                                                 cudaStream_t);
+template cudaError_t launch_tile_ranges<float>(const FusedArgs<float>&, int*, cudaStream_t);
+template cudaError_t launch_tile_ranges<double>(const FusedArgs<double>&, int*, cudaStream_t);
 template cudaError_t launch_assign_xfft<float>(const FusedArgs<float>&, cudaStream_t);
 template cudaError_t launch_assign_xfft<double>(const FusedArgs<double>&, cudaStream_t);
 
