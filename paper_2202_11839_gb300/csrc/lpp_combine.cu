@@ -64,6 +64,61 @@ __device__ __forceinline__ void field_at(const c2<T>* g, int sub, int interlace,
     field_of<T>(g[c.im], g[c.ip], sub, interlace, c, Fm, Fp);
 }
 
+// ylm_poly_scaled(L, +-M, x, y, z) with L and M known at compile time: the same recurrence
+// with constant coefficients and no loops; use_im selects the sine part (n < 0).
+template <typename T, int L, int M>
+__device__ __forceinline__ T ylm_fixed(T x, T y, T z, bool use_im) {
+    T qmm = (T)1;
+#pragma unroll
+    for (int i = 1; i <= M; ++i) qmm *= (T)(2 * i - 1);
+    T q = qmm;
+    if constexpr (L > M) {
+        T q0 = qmm, q1 = (T)(2 * M + 1) * z * qmm;
+#pragma unroll
+        for (int l = M + 2; l <= L; ++l) {
+            const T q2 = (T)(2 * l - 1) * z * q1 - (T)((l + M - 1) * (l - M - 1)) * q0;
+            q0 = q1;
+            q1 = q2;
+        }
+        q = q1;
+    }
+    if constexpr (M == 0) {
+        return q;
+    } else {
+        T re = x, im = y;
+#pragma unroll
+        for (int i = 1; i < M; ++i) {
+            const T t = re * x - im * y;
+            im = re * y + im * x;
+            re = t;
+        }
+        return q * (use_im ? im : re);
+    }
+}
+
+// The channel's harmonic (warp-uniform L, n): the estimators' even degrees up to 8 by a
+// compile-time case, anything else by the general recurrence.
+template <typename T>
+__device__ __forceinline__ T ylm_channel(int L, int n, T x, T y, T z) {
+    const int m = n < 0 ? -n : n;
+    const bool use_im = n < 0;
+    switch (L * 16 + m) {
+#define LPP_YCASE(LL, MM) \
+    case LL * 16 + MM:    \
+        return ylm_fixed<T, LL, MM>(x, y, z, use_im);
+        LPP_YCASE(0, 0)
+        LPP_YCASE(2, 0) LPP_YCASE(2, 1) LPP_YCASE(2, 2)
+        LPP_YCASE(4, 0) LPP_YCASE(4, 1) LPP_YCASE(4, 2) LPP_YCASE(4, 3) LPP_YCASE(4, 4)
+        LPP_YCASE(6, 0) LPP_YCASE(6, 1) LPP_YCASE(6, 2) LPP_YCASE(6, 3) LPP_YCASE(6, 4) LPP_YCASE(6, 5)
+        LPP_YCASE(6, 6)
+        LPP_YCASE(8, 0) LPP_YCASE(8, 1) LPP_YCASE(8, 2) LPP_YCASE(8, 3) LPP_YCASE(8, 4) LPP_YCASE(8, 5)
+        LPP_YCASE(8, 6) LPP_YCASE(8, 7) LPP_YCASE(8, 8)
+#undef LPP_YCASE
+        default:
+            return ylm_poly_scaled<T>(L, n, x, y, z);
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(1024) k_combine(CombineArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -243,12 +298,12 @@ __global__ void __launch_bounds__(1024) k_combine(CombineArgs<T> a) {
                                 Pp = mk<T>(G1p.x + s * G2p.y, -G1p.y + s * G2p.x);
                             }
                             const T yn = (T)ch.ynorm;
-                            const T ym = yn * ylm_poly_scaled<T>(ch.L, ch.n, kx, ky, kz);
+                            const T ym = yn * ylm_channel<T>(ch.L, ch.n, kx, ky, kz);
                             c2<T> t = cscale<T>(cmul<T>(Fm, Pm), ym);
                             if (!c.self) {
                                 const T yp2 = (mirror_neg && (ch.L & 1) == 0)
                                                   ? ym
-                                                  : yn * ylm_poly_scaled<T>(ch.L, ch.n, kxp, kyp, kzp);
+                                                  : yn * ylm_channel<T>(ch.L, ch.n, kxp, kyp, kzp);
                                 t = cadd<T>(t, cscale<T>(cmul<T>(Fp, Pp), yp2));
                             }
                             tre = t.x;
