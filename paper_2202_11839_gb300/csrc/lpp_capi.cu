@@ -72,6 +72,7 @@ struct lpp_plan_s {
     size_t off_trows = 0;                // [2][256] z-tile rows to visit, then [2] counts
     size_t off_plive = 0;                // [3][n*n] bytes: x pencils reached per role
     size_t off_tranges = 0;              // per-tile range records of the two-slot fused passes
+    size_t off_work = 0;                 // item counter of the dynamically scheduled fused passes
     int fty = 4, ftz = 4;
     int n_partner = 0;
     int out_rows = 0;
@@ -308,6 +309,7 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
     plan->off_trows = take((2 * 256 + 2) * sizeof(int));
     plan->off_plive = take((size_t)3 * n * n);
     plan->off_tranges = take(two_slot_grid(plan) ? tile_range_bytes(n, plan->fty, plan->ftz) : sizeof(int));
+    plan->off_work = take(sizeof(int));
     plan->off_wout = take((size_t)kWindowChannels * 256 * 2 * sizeof(double));
     plan->off_wthr = take(257 * sizeof(int));
     plan->off_partner = take((size_t)std::max(1, plan->n_partner) * n3 * cs);
@@ -728,7 +730,11 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         for (int q = 0; q < f.n_src; ++q) bits |= 1 << f.src[q].cat;
         return bits;
     };
+    int* work = (int*)(plan->ws + plan->off_work);
     auto assign_fused = [&](long long particles) -> lpp_status {
+        // one-slot passes over a tile-row list take (slot, tile) items dynamically
+        fa.work = (!fa.dual && fa.trows) ? work : nullptr;
+        if (fa.work) LPP_CUDA(cudaMemsetAsync(work, 0, sizeof(int), st));
         if (tm) tm->begin(KK_ASSIGN, st);
         LPP_CUDA(launch_assign_xfft<T>(fa, st));
         nl += fa.n_slots > 0 ? 1 : 0;
@@ -785,6 +791,15 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         }
         fa.trows = use_rows ? trows + 256 : nullptr;
         fa.trow_count = use_rows ? tcount + 1 : nullptr;
+        // the slot with the most particles (D with the randoms) first: its tiles are the
+        // first items of the dynamic schedule
+        auto weight = [&](const FusedSlot& f) {
+            long long w = 0;
+            for (int q = 0; q < f.n_src; ++q) w += plan->cat[f.src[q].cat].count;
+            return w;
+        };
+        std::stable_sort(fa.slots, fa.slots + fa.n_slots,
+                         [&](const FusedSlot& x, const FusedSlot& y) { return weight(x) > weight(y); });
         { lpp_status s0 = assign_fused(parts); if (s0 != LPP_OK) return s0; }
         FftGeom gp = geom;
         gp.pmask = pmask;

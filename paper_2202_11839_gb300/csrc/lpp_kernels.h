@@ -219,6 +219,8 @@ struct FusedArgs {
     int skip_empty;                      // empty tiles store nothing (the y pass fills their zeros)
     int dual;                            // FP32 n = 256/512: two slots per CTA (see k_assign_xfft2)
     const int* tranges;                  // two-slot launches: per-tile range records, or null
+    int* work;                           // one-slot launches over trows: item counter, zeroed
+                                         // before the launch (dynamic schedule), or null
 };
 
 void fused_geometry(int n, size_t elem_bytes, int* ty, int* tz, int* ipt, int* threads, size_t* smem);

@@ -455,10 +455,10 @@ __device__ __forceinline__ void x_transform(c2<T>* tile, int t, const c2<T>* tw,
     }
 }
 
-// One tile (tile_y, tile_z) of TY x TZ pencils of the slot blockIdx.y: particle ranges,
+// One tile (tile_y, tile_z) of TY x TZ pencils of slot `slot`: particle ranges,
 // scatter, x transform, store of the kept x frequencies.  Every return is CTA-uniform.
 template <typename T, int LOGN>
-__device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int tile_y, int tile_z) {
+__device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int slot, int tile_y, int tile_z) {
     using S = FusedShape<T, LOGN>;
     constexpr int N = S::N, TY = S::TY, TZ = S::TZ, W = S::W, LD = S::LD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -474,7 +474,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int tile_y, in
     const int tid = threadIdx.x;
     const int y0 = tile_y * TY;
     const int z0 = tile_z * TZ;
-    const FusedSlot& sl = a.slots[blockIdx.y];
+    const FusedSlot& sl = a.slots[slot];
     c2<T>* out = a.grids + (size_t)sl.grid * a.grid_stride + ((size_t)z0 * N + y0) * N;
 
     tile_setup<T, LOGN, S::THREADS>(a, sl, y0, z0, tw, twr, tile, N * LD, r_begin, r_pref, r_src, n_ranges, rcount,
@@ -833,12 +833,28 @@ k_assign_xfft(FusedArgs<T> a) {
     using S = FusedShape<T, LOGN>;
     constexpr int NTY = S::N / S::TY;
     if (a.trows == nullptr) {
-        fused_tile<T, LOGN>(a, blockIdx.x % NTY, blockIdx.x / NTY);
+        fused_tile<T, LOGN>(a, blockIdx.y, blockIdx.x % NTY, blockIdx.x / NTY);
         return;
     }
     const int total = *a.trow_count * NTY;
+    if (a.work) {
+        // dynamic: every CTA takes the next (slot, tile) item, slot-major, until none is left
+        // (slots of very different particle counts share the SMs evenly)
+        __shared__ int item;
+        const int items = total * a.n_slots;
+        for (;;) {
+            if (threadIdx.x == 0) item = atomicAdd(a.work, 1);
+            __syncthreads();
+            const int it = item;
+            if (it >= items) break;
+            const int sl = it / total, t = it - sl * total;
+            fused_tile<T, LOGN>(a, sl, t % NTY, a.trows[t / NTY]);
+            __syncthreads();   // the tile's shared memory and `item` are reused by the next one
+        }
+        return;
+    }
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
-        fused_tile<T, LOGN>(a, t % NTY, a.trows[t / NTY]);
+        fused_tile<T, LOGN>(a, blockIdx.y, t % NTY, a.trows[t / NTY]);
         __syncthreads();   // the tile's shared memory is reused by the next one
     }
 }
@@ -906,15 +922,21 @@ static cudaError_t launch_fused_n(const FusedArgs<T>& a, int n_tiles, cudaStream
             return cudaGetLastError();
         }
     }
-    int grid = n_tiles;
+    int grid = n_tiles, slots_y = a.n_slots;
     if (a.trows) {
-        // persistent: about two resident waves over all slots
+        // persistent: about two resident waves over all slots (dynamic: one resident wave
+        // that takes items until none is left)
         int dev = 0, sms = 152;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int per_sm = std::max(1, (int)((227 * 1024) / (smem + 1024)));
-        grid = std::max(1, std::min(n_tiles, 2 * sms * per_sm / std::max(1, a.n_slots)));
+        if (a.work) {
+            grid = std::max(1, std::min(n_tiles * a.n_slots, sms * per_sm));
+            slots_y = 1;
+        } else {
+            grid = std::max(1, std::min(n_tiles, 2 * sms * per_sm / std::max(1, a.n_slots)));
+        }
     }
-    k_assign_xfft<T, LOGN><<<dim3(grid, a.n_slots), S::THREADS, smem, st>>>(a);
+    k_assign_xfft<T, LOGN><<<dim3(grid, slots_y), S::THREADS, smem, st>>>(a);
     return cudaGetLastError();
 }
 

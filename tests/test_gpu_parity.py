@@ -188,15 +188,18 @@ def test_on_node_512_matches_direct_sum(L):
         assert np.max(np.abs(got - want) / (np.abs(want) + ref_scale)) < TOL32, (kind, Lm)
 
 
-def test_fp32_interlaced_256_matches_fp64(L):
+@pytest.mark.parametrize("cross_b", [True, False])
+def test_fp32_interlaced_256_matches_fp64(L, cross_b):
     """256^3, TSC + interlacing, catalogue confined in y and z: the FP32 path (two slots per
     CTA, fixed-point tiles, skipped planes, pencils and columns) against the FP64 path (one
     slot per CTA, float atomics), which matches the oracle to 1e-10 on the small grids above;
-    1e-5 of the per-bin scale |P| + sqrt(P_+^(0) P_dd^(0))."""
+    1e-5 of the per-bin scale |P| + sqrt(P_+^(0) P_dd^(0)).  With the B-mode cross parts
+    there are 160 channels (20 batches of 8); without, 133, so the last batch has 5 grids and
+    runs the one-slot kernel on the dynamic (slot, tile) schedule."""
     n, box = 256, 1000.0
     cat = U.make_case("box256", n, count=120_000, seed=21, box=box, dtype=np.float64, yslab=(0.2, 0.6),
                       zslab=(0.35, 0.7))
-    cfg = _cfg(n, box, scheme=3, interlace=True, frac=0.5, nb=12)
+    cfg = _cfg(n, box, scheme=3, interlace=True, frac=0.5, nb=12, cross_b=cross_b)
     g64 = U.run_gpu(cfg, cat, L.LPP_FP64)
     c32 = {k: v.astype(np.float32) for k, v in cat.items()}
     g32 = U.run_gpu(cfg, c32, L.LPP_FP32)
