@@ -239,6 +239,91 @@ __device__ __forceinline__ void last_stage_warp(const c2<T>* tile, int c, int l,
     }
 }
 
+// FFT of one pencil (column c of the tile; N = 64 R1 points, R1 = 4 or 8) by the 32 lanes
+// of one warp, with __syncwarp between the passes and no block barrier.  With
+// n = n0 + 8 n1 + 64 n2 and k = k0 + R1 k1 + 8 R1 k2:
+//   pass 1: y1[m, k0] = w^(m k0) DFT_R1 over n2 of x[m + 64 n2]   (m = n0 + 8 n1)
+//   pass 2: y2[n0, k0, k1] = w^(R1 n0 k1) DFT_8 over n1 of y1[n0 + 8 n1, k0]
+//   pass 3: X[k0 + R1 k1 + 8 R1 k2] = DFT_8 over n0 of y2[n0, k0, k1]
+// y1 sits at row 64 k0 + (m + 8 k0) % 64 and y2 at row 8 R1 n0 + (k0 + R1 k1 + 2 n0) % (8 R1),
+// so that with an odd LD the 16 lanes of every half-warp access 16 different bank pairs in
+// each pass.  load(e): point e of the input; store(k, value): output k (consecutive lanes
+// store consecutive k).  t1[(k0 - 1) 64 + m] = w^(m k0) and t2[(k1 - 1) 8 + n0] = w^(R1 n0 k1)
+// (forward twiddles; conjugated for INV).
+template <typename T, int LOGN, bool INV, int LD, class Load, class Store>
+__device__ __forceinline__ void fft_pencil_warp(c2<T>* tile, int c, int lane, const c2<T>* t1, const c2<T>* t2,
+                                                Load&& load, Store&& store) {
+    constexpr int N = 1 << LOGN, R1 = N / 64, Q = 8 * R1, B = R1 / 4;
+    static_assert(R1 == 4 || R1 == 8, "N = 256 or 512");
+    c2<T>* col = tile + c;
+    {
+        c2<T> v[2][R1];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int n2 = 0; n2 < R1; ++n2) v[h][n2] = load(lane + 32 * h + 64 * n2);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int m = lane + 32 * h;
+            if (R1 == 8) dft8<T, INV>(v[h]);
+            else dft4<T, INV>(v[h]);
+#pragma unroll
+            for (int k0 = 1; k0 < R1; ++k0) {
+                c2<T> w = t1[(k0 - 1) * 64 + m];
+                if (INV) w.y = -w.y;
+                v[h][k0] = cmul<T>(v[h][k0], w);
+            }
+#pragma unroll
+            for (int k0 = 0; k0 < R1; ++k0) col[(64 * k0 + ((m + 8 * k0) & 63)) * LD] = v[h][k0];
+        }
+        __syncwarp();
+    }
+    c2<T> v[B][8];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int m2 = lane + 32 * b, n0 = m2 & 7, k0 = m2 >> 3;
+#pragma unroll
+        for (int n1 = 0; n1 < 8; ++n1) v[b][n1] = col[(64 * k0 + ((n0 + 8 * n1 + 8 * k0) & 63)) * LD];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int m2 = lane + 32 * b, n0 = m2 & 7, k0 = m2 >> 3;
+        dft8<T, INV>(v[b]);
+#pragma unroll
+        for (int k1 = 1; k1 < 8; ++k1) {
+            c2<T> w = t2[(k1 - 1) * 8 + n0];
+            if (INV) w.y = -w.y;
+            v[b][k1] = cmul<T>(v[b][k1], w);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 8; ++k1) col[(Q * n0 + ((k0 + R1 * k1 + 2 * n0) & (Q - 1))) * LD] = v[b][k1];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int q = lane + 32 * b;
+#pragma unroll
+        for (int n0 = 0; n0 < 8; ++n0) v[b][n0] = col[(Q * n0 + ((q + 2 * n0) & (Q - 1))) * LD];
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int q = lane + 32 * b;
+        dft8<T, INV>(v[b]);
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) store(q + Q * k2, v[b][k2]);
+    }
+}
+
+// Entries of the twiddle tables t1, t2 of fft_pencil_warp for N = 2^LOGN (t2 follows t1).
+template <int LOGN>
+struct PencilWarpTw {
+    static constexpr int R1 = (1 << LOGN) / 64;
+    static constexpr int T1 = (R1 - 1) * 64, T2 = 56, SIZE = T1 + T2;
+};
+
 // fft_columns with the input read by load(b, e) (b as in lead_row) inside the first stage
 // and the output handed to store(e, value) by the last: the tile holds only the
 // intermediate stages, so a pass moves each point through shared memory twice (not four

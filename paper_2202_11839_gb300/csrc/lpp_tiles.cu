@@ -280,8 +280,36 @@ struct FusedShape {
     // warp's 32 lanes cover the N/8 butterfly slots (N >= 256); it reads the per-leg
     // twiddle table of TWR entries after the tiles
     static constexpr bool WARP_OUT = (N / 8 == 32 * IPT) && (THREADS == 32 * W);
-    static constexpr int TWR = WARP_OUT ? 7 * (N / 8) : 0;
+    // n = 256, 512: the whole x transform of a pencil by one warp (fft_pencil_warp), with
+    // its twiddle tables in the TWR entries
+    static constexpr bool WARP_FFT = WARP_OUT && (N == 256 || N == 512);
+    static constexpr int TWR = WARP_FFT ? PencilWarpTw<LOGN>::SIZE : (WARP_OUT ? 7 * (N / 8) : 0);
 };
+
+// The per-leg twiddles after the tiles: fft_pencil_warp's t1, t2 (WARP_FFT), else the last
+// stage's twr[(r - 1) N/8 + j] = w^(j r).  Threads `first`, first + step, ... fill them.
+template <typename T, int LOGN>
+__device__ __forceinline__ void fill_twr(const c2<T>* tw, c2<T>* twr, int first, int step) {
+    using S = FusedShape<T, LOGN>;
+    constexpr int N = S::N;
+    if constexpr (S::WARP_FFT) {
+        using P = PencilWarpTw<LOGN>;
+        for (int i = first; i < P::SIZE; i += step) {
+            if (i < P::T1) {
+                const int k0 = i / 64 + 1, m = i - (k0 - 1) * 64;
+                twr[i] = tw[m * k0];
+            } else {
+                const int k1 = (i - P::T1) / 8 + 1, n0 = (i - P::T1) - (k1 - 1) * 8;
+                twr[i] = tw[P::R1 * n0 * k1];
+            }
+        }
+    } else if constexpr (S::TWR > 0) {
+        for (int i = first; i < S::TWR; i += step) {
+            const int r = i / (N / 8) + 1, j = i - (r - 1) * (N / 8);
+            twr[i] = tw[j * r];
+        }
+    }
+}
 
 // The particle ranges of the tile at (y0, z0) for the sources of slot `sl`, found by one
 // warp (all 32 lanes): TZ+3 z rows of keys y0-2 .. y0+TY per source, one or two contiguous
@@ -402,12 +430,7 @@ __device__ __forceinline__ void tile_setup(const FusedArgs<T>& a, const FusedSlo
                              sl.amax_a != nullptr);
     } else {
         for (int i = tid - 32; i < N; i += NT - 32) tw[i] = a.tw[i];
-        if constexpr (S::TWR > 0) {
-            for (int i = tid - 32; i < S::TWR; i += NT - 32) {
-                const int r = i / (N / 8) + 1, j = i - (r - 1) * (N / 8);
-                twr[i] = a.tw[j * r];
-            }
-        }
+        fill_twr<T, LOGN>(a.tw, twr, tid - 32, NT - 32);
         for (int i = tid - 32; i < tile_elems; i += NT - 32) tiles[i] = mk<T>((T)0, (T)0);
     }
 }
@@ -422,35 +445,58 @@ __device__ __forceinline__ void x_transform(c2<T>* tile, int t, const c2<T>* tw,
                                             float unit, c2<T>* out, int nk_pos, int nk_neg) {
     using S = FusedShape<T, LOGN>;
     constexpr int N = S::N, W = S::W, LD = S::LD, IPT = S::IPT, TY = S::TY, R0 = LeadRadix<LOGN>::R;
-    const int c = t & (W - 1), u = t >> ilog2(W);
-    bool converted = false;
-    if constexpr (sizeof(T) == 4) {
-        if (fixed) {
-            const int2* ti = reinterpret_cast<const int2*>(tile) + c;
-            lead_stage<T, LOGN, false, IPT, LD, true>(tile, c, u, [&](int, int e) {
-                const int2 q = ti[e * LD];
-                return mk<T>((T)((float)q.x * unit), (T)((float)q.y * unit));
-            });
-            converted = true;
-        }
-    }
-    if (!converted) stockham_stage<T, N, R0, false, IPT, LD, 1>(tile, c, u, tw);
-    if constexpr (S::WARP_OUT) {
-        radix8_until<T, N, false, IPT, LD, R0, N / 8>(tile, c, u, tw);
-        const int pc = t >> 5;
+    if constexpr (S::WARP_FFT) {
+        // one warp per pencil
+        const int pc = t >> 5, lane = t & 31;
         c2<T>* po = out + ((size_t)(pc / TY) * N + (pc & (TY - 1))) * N;
-        last_stage_warp<T, N, false, IPT, LD>(tile, pc, t & 31, twr, [&](int e, c2<T> v) {
+        auto store = [&](int e, c2<T> v) {
             if (kept(e, N, nk_pos, nk_neg)) po[e] = v;
-        });
+        };
+        constexpr int T1 = PencilWarpTw<LOGN>::T1;
+        if constexpr (sizeof(T) == 4) {
+            if (fixed) {
+                const int2* ti = reinterpret_cast<const int2*>(tile) + pc;
+                fft_pencil_warp<T, LOGN, false, LD>(tile, pc, lane, twr, twr + T1, [&](int e) {
+                    const int2 q = ti[e * LD];
+                    return mk<T>((T)((float)q.x * unit), (T)((float)q.y * unit));
+                }, store);
+                return;
+            }
+        }
+        const c2<T>* col = tile + pc;
+        fft_pencil_warp<T, LOGN, false, LD>(tile, pc, lane, twr, twr + T1, [&](int e) { return col[e * LD]; },
+                                            store);
     } else {
-        radix8_until<T, N, false, IPT, LD, R0, N>(tile, c, u, tw);
-        // LPL consecutive threads store one pencil (coalesced along x)
-        constexpr int LPL = S::THREADS / W;
-        const int cw = t / LPL;
-        const int nkept = nk_pos + 1 + nk_neg;
-        for (int k = t & (LPL - 1); k < nkept; k += LPL) {
-            const int e = k <= nk_pos ? k : N - nkept + k;
-            out[((cw / TY) * N + (cw & (TY - 1))) * N + e] = tile[e * LD + cw];
+        const int c = t & (W - 1), u = t >> ilog2(W);
+        bool converted = false;
+        if constexpr (sizeof(T) == 4) {
+            if (fixed) {
+                const int2* ti = reinterpret_cast<const int2*>(tile) + c;
+                lead_stage<T, LOGN, false, IPT, LD, true>(tile, c, u, [&](int, int e) {
+                    const int2 q = ti[e * LD];
+                    return mk<T>((T)((float)q.x * unit), (T)((float)q.y * unit));
+                });
+                converted = true;
+            }
+        }
+        if (!converted) stockham_stage<T, N, R0, false, IPT, LD, 1>(tile, c, u, tw);
+        if constexpr (S::WARP_OUT) {
+            radix8_until<T, N, false, IPT, LD, R0, N / 8>(tile, c, u, tw);
+            const int pc = t >> 5;
+            c2<T>* po = out + ((size_t)(pc / TY) * N + (pc & (TY - 1))) * N;
+            last_stage_warp<T, N, false, IPT, LD>(tile, pc, t & 31, twr, [&](int e, c2<T> v) {
+                if (kept(e, N, nk_pos, nk_neg)) po[e] = v;
+            });
+        } else {
+            radix8_until<T, N, false, IPT, LD, R0, N>(tile, c, u, tw);
+            // LPL consecutive threads store one pencil (coalesced along x)
+            constexpr int LPL = S::THREADS / W;
+            const int cw = t / LPL;
+            const int nkept = nk_pos + 1 + nk_neg;
+            for (int k = t & (LPL - 1); k < nkept; k += LPL) {
+                const int e = k <= nk_pos ? k : N - nkept + k;
+                out[((cw / TY) * N + (cw & (TY - 1))) * N + e] = tile[e * LD + cw];
+            }
         }
     }
 }
@@ -641,7 +687,9 @@ void fused_geometry(int n, size_t elem_bytes, int* ty, int* tz, int* ipt, int* t
     *ipt = t1 <= 512 ? 1 : (t1 <= 1024 ? 2 : 4);
     *threads = t1 / *ipt;
     const bool warp_out = n / 8 == 32 * *ipt && *threads == 32 * w;
-    *smem = (size_t)(n + n * (w + 1) + (warp_out ? 7 * (n / 8) : 0)) * 2 * elem_bytes;
+    const bool warp_fft = warp_out && (n == 256 || n == 512);
+    const int twr = warp_fft ? (n / 64 - 1) * 64 + 56 : (warp_out ? 7 * (n / 8) : 0);
+    *smem = (size_t)(n + n * (w + 1) + twr) * 2 * elem_bytes;
 }
 
 // Tile range records (k_tile_ranges): per tile of the persistent enumeration, kRec ints:
@@ -657,12 +705,7 @@ __device__ __forceinline__ void tile_clear(const FusedArgs<T>& a, c2<T>* tw, c2<
     constexpr int N = S::N;
     const int tid = threadIdx.x;
     for (int i = tid; i < N; i += NT) tw[i] = a.tw[i];
-    if constexpr (S::TWR > 0) {
-        for (int i = tid; i < S::TWR; i += NT) {
-            const int r = i / (N / 8) + 1, j = i - (r - 1) * (N / 8);
-            twr[i] = a.tw[j * r];
-        }
-    }
+    fill_twr<T, LOGN>(a.tw, twr, tid, NT);
     for (int i = tid; i < tile_elems; i += NT) tiles[i] = mk<T>((T)0, (T)0);
 }
 
