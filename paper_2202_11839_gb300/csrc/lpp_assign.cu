@@ -16,13 +16,6 @@
 
 namespace lpp {
 
-template <typename T>
-__device__ __forceinline__ T horner(const T* c, int nc, T x) {
-    T r = (T)0;
-    for (int i = nc - 1; i >= 0; --i) r = r * x + c[i];
-    return r;
-}
-
 // Sky frame about the pole p: e_phi = unit(p x xhat), e_theta = e_phi x xhat.
 template <typename T>
 __device__ __forceinline__ void sky_frame(const T xh[3], const double pole[3], T et[3], T ep[3], int* err) {
@@ -43,31 +36,70 @@ __device__ __forceinline__ void sky_frame(const T xh[3], const double pole[3], T
     et[2] = ep[0] * xh[1] - ep[1] * xh[0];
 }
 
-// sm: the block's shared copy of the quadrature directions, tables and polynomials (in the
-// order of coeff_smem_words)
+// Shared-memory layout of the quadrature for degree L = 2 (q + 1): directions as [S][4]
+// (x, y, z, 0) and the table transposed to [S][NHP] (NHP = 2L + 1 rounded up to a multiple
+// of 4), so that a quadrature point reads its direction and its 2L + 1 table entries in
+// 16-byte words; every thread of a block reads the same entries at the same time
+// (broadcast).  The blocks of L = 2, 4, 6, 8 follow one another, then the polynomials.
+__host__ __device__ constexpr int quad_nhp(int q) { return (2 * (2 * (q + 1)) + 1 + 3) & ~3; }
+
+template <typename T>
+__host__ __device__ inline int quad_block_words(const CoeffArgs<T>& a, int q) { return a.quad_S[q] * (4 + quad_nhp(q)); }
+
+// sm: the block's shared copy of the quadrature directions, tables and polynomials
 template <typename T, int L, bool HAS_IM>
 __device__ __forceinline__ void project_group(const CoeffArgs<T>& a, const CoeffGroup& g, long long i, T wgt,
                                               T gre, T gim, const T et[3], const T ep[3], const T xh[3],
                                               const T* sm) {
     constexpr int NH = 2 * L + 1;
     constexpr int q = L / 2 - 1;
+    constexpr int NHP = quad_nhp(q);
     int o = 0;
 #pragma unroll
-    for (int qq = 0; qq < q; ++qq) o += a.quad_S[qq] * (3 + 2 * (2 * (qq + 1)) + 1);
+    for (int qq = 0; qq < q; ++qq) o += quad_block_words(a, qq);
     const int S = a.quad_S[q];
     const T* dirs = sm + o;
-    const T* tab = dirs + 3 * S;
+    const T* tab = dirs + 4 * S;
     int op = 0;
 #pragma unroll
-    for (int qq = 0; qq < 4; ++qq) op += a.quad_S[qq] * (3 + 2 * (2 * (qq + 1)) + 1);
+    for (int qq = 0; qq < 4; ++qq) op += quad_block_words(a, qq);
     const T* poly = sm + op + g.poly;
+    // the kernel polynomial in registers, zero-padded to 8 coefficients (the leading zeros
+    // leave Horner's scheme exact)
+    T pc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) pc[k] = k < g.npoly ? poly[k] : (T)0;
     T accr[NH], acci[NH];
 #pragma unroll
     for (int n = 0; n < NH; ++n) { accr[n] = (T)0; acci[n] = (T)0; }
     for (int s = 0; s < S; ++s) {
-        const T kx = dirs[3 * s], ky = dirs[3 * s + 1], kz = dirs[3 * s + 2];
+        T kx, ky, kz;
+        T t[NHP];
+        if constexpr (sizeof(T) == 4) {
+            const float4 d = reinterpret_cast<const float4*>(dirs)[s];
+            kx = d.x;
+            ky = d.y;
+            kz = d.z;
+            const float4* tv = reinterpret_cast<const float4*>(tab + s * NHP);
+#pragma unroll
+            for (int j = 0; j < NHP / 4; ++j) {
+                const float4 v = tv[j];
+                t[4 * j] = v.x;
+                t[4 * j + 1] = v.y;
+                t[4 * j + 2] = v.z;
+                t[4 * j + 3] = v.w;
+            }
+        } else {
+            kx = dirs[4 * s];
+            ky = dirs[4 * s + 1];
+            kz = dirs[4 * s + 2];
+#pragma unroll
+            for (int n = 0; n < NH; ++n) t[n] = tab[s * NHP + n];
+        }
         const T mu = kx * xh[0] + ky * xh[1] + kz * xh[2];
-        const T pm = horner(poly, g.npoly, mu);
+        T pm = (T)0;
+#pragma unroll
+        for (int k = 7; k >= 0; --k) pm = pm * mu + pc[k];
         T kre, kim;
         if (g.kind == KIND_PLUS) {
             kre = gre * pm;
@@ -77,9 +109,9 @@ __device__ __forceinline__ void project_group(const CoeffArgs<T>& a, const Coeff
             const T cb = kx * ep[0] + ky * ep[1] + kz * ep[2];
             T zr = ca * ca - cb * cb, zi = (T)-2 * ca * cb;  // (a - i b)^2
             if (g.kind == KIND_MINUS) {
-                const T t = zr * zr - zi * zi;
+                const T tt = zr * zr - zi * zi;
                 zi = (T)2 * zr * zi;
-                zr = t;
+                zr = tt;
             }
             zr *= pm;
             zi *= pm;
@@ -88,9 +120,8 @@ __device__ __forceinline__ void project_group(const CoeffArgs<T>& a, const Coeff
         }
 #pragma unroll
         for (int n = 0; n < NH; ++n) {
-            const T t = tab[n * S + s];
-            accr[n] += t * kre;
-            if (HAS_IM) acci[n] += t * kim;
+            accr[n] += t[n] * kre;
+            if (HAS_IM) acci[n] += t[n] * kim;
         }
     }
 #pragma unroll
@@ -137,12 +168,12 @@ __device__ __forceinline__ void block_add(double v, double* dst) {
     }
 }
 
-// Shared-memory words for the quadrature directions and tables (L = 2, 4, 6, 8) and the
-// polynomials: every thread of a block reads the same entry at the same time (broadcast).
+// Shared-memory words for the quadrature directions and tables (L = 2, 4, 6, 8, laid out as
+// in project_group) and the polynomials.
 template <typename T>
 __host__ __device__ inline int coeff_smem_words(const CoeffArgs<T>& a) {
     int w = a.n_polys;
-    for (int q = 0; q < 4; ++q) w += a.quad_S[q] * (3 + 2 * (2 * (q + 1)) + 1);
+    for (int q = 0; q < 4; ++q) w += quad_block_words(a, q);
     return w;
 }
 
@@ -153,11 +184,16 @@ __global__ void __launch_bounds__(256) k_coeffs(CoeffArgs<T> a) {
     {
         int o = 0;
         for (int q = 0; q < 4; ++q) {
-            const int S = a.quad_S[q], nh = 2 * (2 * (q + 1)) + 1;
-            for (int i = threadIdx.x; i < 3 * S; i += blockDim.x) sm[o + i] = a.quad_dirs[q][i];
-            o += 3 * S;
-            for (int i = threadIdx.x; i < nh * S; i += blockDim.x) sm[o + i] = a.quad_tab[q][i];
-            o += nh * S;
+            const int S = a.quad_S[q], nh = 2 * (2 * (q + 1)) + 1, nhp = quad_nhp(q);
+            // directions [S][3] -> [S][4]; table [nh][S] -> [S][nhp] (zero padding)
+            for (int i = threadIdx.x; i < 4 * S; i += blockDim.x)
+                sm[o + i] = (i & 3) < 3 ? a.quad_dirs[q][(i >> 2) * 3 + (i & 3)] : (T)0;
+            o += 4 * S;
+            for (int i = threadIdx.x; i < nhp * S; i += blockDim.x) {
+                const int si = i / nhp, n = i - si * nhp;
+                sm[o + i] = n < nh ? a.quad_tab[q][n * S + si] : (T)0;
+            }
+            o += nhp * S;
         }
         for (int i = threadIdx.x; i < a.n_polys; i += blockDim.x) sm[o + i] = a.polys[i];
         __syncthreads();
