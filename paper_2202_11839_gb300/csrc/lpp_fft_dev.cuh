@@ -346,15 +346,6 @@ __device__ __forceinline__ void fft_columns_io(c2<T>* tile, int c, int u, const 
     }
 }
 
-// fft_columns whose first stage reads its operands through load(b, e) from the tile itself
-// (a conversion of the stored values fused into that stage); the result stays in the tile.
-template <typename T, int LOGN, bool INV, int IPT, int LD, class Load>
-__device__ __forceinline__ void fft_columns_in(c2<T>* tile, int c, int u, const c2<T>* tw, Load&& load) {
-    constexpr int N = 1 << LOGN;
-    lead_stage<T, LOGN, INV, IPT, LD, true>(tile, c, u, load);
-    radix8_until<T, N, INV, IPT, LD, LeadRadix<LOGN>::R, N>(tile, c, u, tw);
-}
-
 __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
 
 // Shape of the pencil passes for n = 2^LOGN: W pencils per CTA (W n / 8 <= 1024 butterfly
