@@ -256,8 +256,11 @@ __global__ void __launch_bounds__(1024) k_combine(CombineArgs<T> a) {
             // the mirror is exactly -k unless an index sits at the Nyquist frequency; then an
             // even-degree harmonic takes the same value at both members of the pair
             const bool mirror_neg = (fxp == -fx) && (fyp == -fy) && (fzp == -fz);
+            // a warp none of whose lanes owns a mode pair (rows near the last shell) has
+            // nothing to add: it skips the channels (warp-uniform)
+            const bool warp_live = __any_sync(0xffffffffu, own_pair);
             const SegMask segm = seg_mask(bin);
-            const int n_slots = (a.n_ch + a.per_grid - 1) / a.per_grid;
+            const int n_slots = warp_live ? (a.n_ch + a.per_grid - 1) / a.per_grid : 0;
             // four slots at a time: their packed values at m and -m are loaded together
             for (int s0 = 0; s0 < n_slots; s0 += 4) {
                 c2<T> zm[4], zp[4];
