@@ -301,7 +301,7 @@ lpp_status lpp_surrogate_encode(lpp_surrogate_t net, const double* params, int n
 lpp_status lpp_surrogate_predict(lpp_surrogate_t net, const double* params, int n, float* out, void* stream);
 
 /* Gaussian (disconnected, mode-counting) error bars of the derived multipoles, the unit in
- * which the template emulator is trained and judged.  The paper gives no covariance; this
+ * which the template emulator is trained and checked.  The paper gives no covariance; this
  * is the standard isotropic-Gaussian reading: a shell with N_k = V (k_hi^3 - k_lo^3) / (6 pi^2)
  * Fourier modes (both k and -k counted) and multipole l has
  *   sigma^2(gE_l)    = (2l+1) [(P_gg + N_g)(P_EE + N_e) + P_gE^2] / N_k,

@@ -23,7 +23,7 @@ Lm_L/(1-mu^2)^(m/2) is a polynomial in mu = k.x, expanded here into products of
 Cartesian components of k and x (Sec. 3.1.2: "Cartesian components"), so each
 needed field is a plain FFT of gamma * (tensor component) * (monomial of x).
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
 * sky frame: e_phi = unit(p x xhat), e_theta = e_phi x xhat for a plan pole p
   (the spherical frame about p; the paper's S(d) matrix is the case p = z);
 * galaxies enter as weighted Dirac deltas, gridded by CIC/TSC (optionally with

@@ -19,7 +19,7 @@ the Mellin transform of j_l,
 
     int_0^inf x^(s-1) j_l(x) dx = 2^(s-2) sqrt(pi) Gamma((l+s)/2) / Gamma((3+l-s)/2).
 
-Readings where the paper is silent (listed in the design doc): 2048 log-spaced k in [1e-4, 10],
+Readings where the paper is silent: 2048 log-spaced k in [1e-4, 10],
 zero padding to 4096, k_0 r_0 = exp(-(N-1) Delta), biases q = 1.5 (inverse) and 0.5
 (forward), the Nyquist coefficient replaced by its real part; the input spectrum tapered
 to zero over the lowest and highest 10% of the log-k range by t - sin(2 pi t)/(2 pi) (a

@@ -1,6 +1,6 @@
 """Template emulator: the surrogate network (lpp_surrogate_*) trained on window-convolved
 templates from the FFTLog path (lpp_convolve_template_eb), which stays its fallback and its
-judge.
+accuracy reference.
 
 Emulated quantity: the Legendre multipoles gE_0,2, EE_0,2,4 and BB_0,2,4 of the window-
 convolved template (Sec. 3.2, Eq. window_convolution_X_hankel; Sec. 2.4 for E/B) at 40
@@ -167,7 +167,7 @@ class Emulator:
 
     # -------------------------------------------------------------------- judging
     def plain(self, params):
-        """The FFTLog path's curves in error-bar units (the fallback and the judge)."""
+        """The FFTLog path's curves in error-bar units (the fallback and the accuracy reference)."""
         _, eb = self.t.derived(params, ref=None, sigma=self.sigma_dev)
         return eb
 

@@ -209,7 +209,7 @@ def test_targets_decode_back_to_the_template():
 
 
 def test_emulator_accuracy_and_speed():
-    """Train on 20k Latin-hypercube templates from the FFTLog path; judge on 2k held-out
+    """Train on 20k Latin-hypercube templates from the FFTLog path; evaluate on 2k held-out
     parameter sets in units of the Gaussian error bar.  The trained network beats its
     interpolated baseline by a wide margin and is much faster than the FFTLog path."""
     import torch
