@@ -697,16 +697,26 @@ void fused_geometry(int n, size_t elem_bytes, int* ty, int* tz, int* ipt, int* t
 // [kRecPref..) running particle count before each range (and the total), [kRecSrc..) source.
 constexpr int kRec = 96, kRecBegin = 2, kRecPref = 32, kRecSrc = 64;
 
-// Tiles of a two-slot launch: twiddles and cleared tiles only (the ranges come from a record).
+// Tiles of a two-slot launch with range records: cleared tiles only (16-byte stores; the
+// ranges come from a record and the kernel loads the twiddles once, before its tile loop).
 template <typename T, int LOGN, int NT>
-__device__ __forceinline__ void tile_clear(const FusedArgs<T>& a, c2<T>* tw, c2<T>* twr, c2<T>* tiles,
-                                           int tile_elems) {
+__device__ __forceinline__ void tile_clear(c2<T>* tiles, int tile_elems) {
+    static_assert(sizeof(c2<T>) == 8 || sizeof(c2<T>) == 16, "complex float or double");
+    float4* t4 = reinterpret_cast<float4*>(tiles);
+    const int n4 = tile_elems * (int)sizeof(c2<T>) / 16;   // tile_elems even for complex float
+    for (int i = threadIdx.x; i < n4; i += NT) t4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Twiddles of a tile's x transform in shared memory: the N-entry table (unless every pencil
+// is transformed by fft_pencil_warp, which reads only the per-leg tables) and the per-leg
+// tables after the tiles.
+template <typename T, int LOGN, int NT>
+__device__ __forceinline__ void load_twiddles(const FusedArgs<T>& a, c2<T>* tw, c2<T>* twr) {
     using S = FusedShape<T, LOGN>;
-    constexpr int N = S::N;
-    const int tid = threadIdx.x;
-    for (int i = tid; i < N; i += NT) tw[i] = a.tw[i];
-    fill_twr<T, LOGN>(a.tw, twr, tid, NT);
-    for (int i = tid; i < tile_elems; i += NT) tiles[i] = mk<T>((T)0, (T)0);
+    if constexpr (!S::WARP_FFT) {
+        for (int i = threadIdx.x; i < S::N; i += NT) tw[i] = a.tw[i];
+    }
+    fill_twr<T, LOGN>(a.tw, twr, threadIdx.x, NT);
 }
 
 // Two interlaced channel slots (2 blockIdx.y, 2 blockIdx.y + 1: single-source coefficient
@@ -732,7 +742,7 @@ __device__ __forceinline__ void fused_tile2(const FusedArgs<T>& a, int tile_y, i
     const FusedSlot& s0 = a.slots[2 * blockIdx.y];
     const FusedSlot& s1 = a.slots[2 * blockIdx.y + 1];
     if (rec) {
-        tile_clear<T, LOGN, NT>(a, tw, twr, tile0, 2 * N * LD);
+        tile_clear<T, LOGN, NT>(tile0, 2 * N * LD);
     } else {
         tile_setup<T, LOGN, NT>(a, s0, y0, z0, tw, twr, tile0, 2 * N * LD, r_begin_s, r_pref_s, r_src_s,
                                 n_ranges_s, rcount, wmax_s);
@@ -826,6 +836,11 @@ __global__ void __launch_bounds__(2 * FusedShape<T, LOGN>::THREADS, 1) k_assign_
     if (tid < 32 && (int)blockIdx.x < total) {
 #pragma unroll
         for (int k = 0; k < kRec / 32; ++k) recs[0][tid + 32 * k] = a.tranges[(size_t)blockIdx.x * kRec + tid + 32 * k];
+    }
+    {
+        extern __shared__ __align__(16) unsigned char smem_raw[];
+        c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
+        load_twiddles<T, LOGN, 2 * S::THREADS>(a, tw, tw + S::N + 2 * S::N * S::LD);
     }
     __syncthreads();
     int buf = 0;
