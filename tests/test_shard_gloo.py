@@ -1,0 +1,117 @@
+"""Moment-slot sharding of one estimate (paper_2202_11839_gb300/shard.py): the partition
+covers every requested slot once and balances the ranks, and two gloo ranks that each hold
+an estimate of their own slots end up with the whole estimate.  Each rank's estimate comes
+from the FP64 oracle on a small catalogue (its rows outside the rank's slots must not
+leak into the result)."""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _sh():
+    sys.path.insert(0, ROOT)
+    from paper_2202_11839_gb300 import lpp as L
+    from paper_2202_11839_gb300 import shard as SH
+    return L, SH
+
+
+@pytest.mark.parametrize("extra", [0, 1 << 10])
+@pytest.mark.parametrize("moments", [0x3FF, 0x3FE, (1 << 5) | (1 << 9), 1 << 4])
+def test_partition_covers_each_slot_once_and_balances(moments, extra):
+    L, SH = _sh()
+    want = moments | extra
+    cross_b = bool(extra)
+    weight = {s: SH.slot_channels(s, cross_b) + 1 for s in range(10)}
+    for world in range(1, 13):
+        masks = SH.partition(want, world)
+        assert len(masks) == world
+        slots = [s for m in masks for s in range(10) if m & (1 << s)]
+        assert sorted(slots) == [s for s in range(10) if moments & (1 << s)]
+        for m in masks:
+            assert (m & L.LPP_WANT_CROSS_B) == (extra if m else 0)
+        loads = [sum(weight[s] for s in range(10) if m & (1 << s)) for m in masks]
+        assert max(loads) - min(loads) <= max(weight[s] for s in slots)
+
+
+def test_slot_channels_match_the_plan_tables():
+    L, SH = _sh()
+    # 133 channels for the ten slots without the B-mode cross parts, 160 with
+    assert sum(SH.slot_channels(s, False) for s in range(10)) == 133
+    assert sum(SH.slot_channels(s, True) for s in range(10)) == 160
+
+
+def _oracle_estimate():
+    sys.path.insert(0, ROOT)
+    from tests import parity_util as U
+    cfg = dict(n=16, box=300.0, observer=(150.0, 150.0, -800.0), scheme=3, interlace=True,
+               k_edges=U.default_edges(16, 300.0))
+    cat = U.make_case("shard", 16, count=1200, seed=7, n_rand=2500)
+    return U.run_oracle(cfg, cat)
+
+
+def test_single_process_gather_is_the_identity():
+    L, SH = _sh()
+    ref = _oracle_estimate()
+    out = SH.gather(ref, L.LPP_WANT_ALL)
+    np.testing.assert_array_equal(out.p, ref.p)
+    np.testing.assert_array_equal(out.raw, ref.raw)
+    np.testing.assert_array_equal(out.n_modes, ref.n_modes)
+    assert out.norm_auto == ref.norm_auto and out.shot_plus == ref.shot_plus
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, moments, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    L, SH = _sh()
+    ref = _oracle_estimate()
+    mask = SH.partition(moments, world)[rank]
+    mine = None
+    if mask:
+        # the rank's own estimate: the oracle's rows of its slots, garbage elsewhere (which
+        # gather must drop)
+        mine = L.Estimate(ref.p.copy(), ref.raw.copy(), ref.k_mean, ref.n_modes, ref.norm_auto, ref.norm_cross,
+                          ref.norm_dd, ref.shot_plus, ref.shot_dd, ref.alpha)
+        for s in range(10):
+            if not mask & (1 << s):
+                mine.p[s] = 1e30 * (rank + 1)
+                mine.raw[s] = -1e30
+    out = SH.gather(mine, mask, dist, "cpu")
+    want = ref.p.copy()
+    for s in range(10):
+        if not moments & (1 << s):
+            want[s] = 0
+    q.put((rank, mask, np.array_equal(out.p, want), np.array_equal(out.n_modes, ref.n_modes),
+           out.norm_auto == ref.norm_auto and out.alpha == ref.alpha))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("moments", [0x3FF, (1 << 5) | (1 << 9)])
+def test_two_gloo_ranks_gather_the_whole_estimate(moments):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    world = 2 if moments == 0x3FF else 3        # the second case leaves one rank without a slot
+    procs = [ctx.Process(target=_rank, args=(r, world, port, moments, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=300) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert any(mask == 0 for _, mask, *_ in out) == (world == 3)
+    for rank, mask, p_ok, n_ok, meta_ok in out:
+        assert p_ok and n_ok and meta_ok, rank
