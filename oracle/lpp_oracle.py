@@ -484,6 +484,78 @@ def derived_eb(p: np.ndarray):
     return ge, 0.5 * (plus + mm), 0.5 * (plus - mm)
 
 
+# ------------------------------------------------------------ density multipoles
+@dataclass
+class DensityResult:
+    ells: tuple
+    p: np.ndarray          # (len(ells), nb) complex, normalised (shot noise on l = 0 only)
+    raw: np.ndarray        # (len(ells), nb) complex, shell means before normalisation
+    n_modes: np.ndarray
+    k_mean: np.ndarray
+    norm: float
+    shot: float
+
+
+def density_ell_field(plan: Plan, mg: ModeGrid, pos, w, ell: int) -> np.ndarray:
+    """delta^(l)(k) = FT[w L_l(khat . xhat)] of one catalogue (Eq. delta_ell, endpoint line of
+    sight xhat toward each galaxy, or the plan's global n for the GPP form Eq. gpp_dens),
+    with L_l(khat . xhat) expanded into Cartesian products of khat and xhat as for the
+    tensor moments (one FFT per monomial of xhat)."""
+    pos = np.asarray(pos, dtype=np.float64)
+    xl = line_of_sight(pos, plan.observer)
+    if plan.los_est_global:
+        ng = np.asarray(plan.los_global, dtype=np.float64)
+        xl = np.broadcast_to(ng / np.linalg.norm(ng), xl.shape).copy()
+    ft = FieldTransformer(pos, plan.n, plan.box, plan.origin, plan.scheme, plan.interlace, plan.compensate, mg)
+    return xi_contracted(ft, mg, np.asarray(w, dtype=np.float64), np.ones(pos.shape[1]), 0, legendre_coeffs(ell), xl)
+
+
+def density_multipoles(plan: Plan, dens_pos, dens_w=None, rand_pos=None, rand_w=None, rand_nbar=None,
+                       ells=(0, 2, 4)) -> DensityResult:
+    """Yamamoto (LPP) multipoles of the galaxy density (Eq. lpp_dens_app):
+        P^(l)(k) = (2l+1) < delta^(l)(k) delta(-k) >_shell / I  -  [l = 0] N,
+    delta = data - alpha randoms, each catalogue's delta^(l) from its own lines of sight;
+    I and the shot noise N as for the density monopole slot of `multipoles`."""
+    n, box = plan.n, plan.box
+    mg = ModeGrid(n, box)
+    edges = np.asarray(plan.k_edges, dtype=np.float64)
+    b, nb = _bins(mg, edges)
+    n_modes = np.bincount(b.ravel(), minlength=nb + 1)[:nb].astype(np.int64)
+    ksum = np.bincount(b.ravel(), weights=mg.kmag.ravel(), minlength=nb + 1)[:nb]
+    k_mean = np.where(n_modes > 0, ksum / np.maximum(n_modes, 1), 0.0)
+    dp = np.asarray(dens_pos, dtype=np.float64)
+    wd = np.ones(dp.shape[1]) if dens_w is None else np.asarray(dens_w, dtype=np.float64)
+    if rand_pos is not None:
+        rp = np.asarray(rand_pos, dtype=np.float64)
+        wr = np.ones(rp.shape[1]) if rand_w is None else np.asarray(rand_w, dtype=np.float64)
+        nbr = np.ones(rp.shape[1]) if rand_nbar is None else np.asarray(rand_nbar, dtype=np.float64)
+        alpha = wd.sum() / wr.sum()
+        norm = alpha * np.sum(nbr * wr * wr)
+        shot_num = np.sum(wd * wd) + alpha * alpha * np.sum(wr * wr)
+    else:
+        alpha, norm, shot_num = 0.0, wd.sum() ** 2 / box ** 3, np.sum(wd * wd)
+    if plan.norm_override > 0:
+        norm = plan.norm_override
+    shot = shot_num / norm if plan.subtract_shot else 0.0
+
+    def field_of(ell):
+        f = density_ell_field(plan, mg, dp, wd, ell)
+        if rand_pos is not None:
+            f = f - alpha * density_ell_field(plan, mg, rp, wr, ell)
+        return f
+
+    delta = field_of(0)
+    nm = np.maximum(n_modes, 1)
+    raw = np.zeros((len(ells), nb), dtype=np.complex128)
+    p = np.zeros_like(raw)
+    for i, ell in enumerate(ells):
+        f = delta if ell == 0 else field_of(ell)
+        raw[i] = (2 * ell + 1) * _shell_sum(f * np.conj(delta), b, nb) / nm
+        p[i] = raw[i] / norm - (shot if ell == 0 else 0.0)
+        p[i] = np.where(n_modes > 0, p[i], 0.0)
+    return DensityResult(tuple(ells), p, raw, n_modes, k_mean, norm, shot)
+
+
 # --------------------------------------------------------------- direct sums (pins)
 def direct_kernel(kind: str, L: int, khat: np.ndarray, xhat, etheta, ephi, gamma):
     """K_X(khat; x, gamma) evaluated directly (no Cartesian expansion), shape (nk, np).
