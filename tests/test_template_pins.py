@@ -124,3 +124,46 @@ def test_gaussian_sigma_against_monte_carlo():
         est = (2 * ell + 1) * np.mean((a * np.conj(b)).real * eval_legendre(ell, mu), axis=1)
         got = est.std()
         assert abs(got / want[c] - 1.0) < 0.04, (c, got, want[c])
+
+
+def _bbks_published(k, gamma, tilt):
+    """Bardeen, Bond, Kaiser & Szalay (1986), Eq. G3: T(q) = ln(1 + 2.34 q)/(2.34 q)
+    [1 + 3.89 q + (16.1 q)^2 + (5.46 q)^3 + (6.71 q)^4]^(-1/4), q = k / Gamma; P = k^(1+tilt) T^2."""
+    q = k / gamma
+    t = math.log(1.0 + 2.34 * q) / (2.34 * q) * (1.0 + 3.89 * q + (16.1 * q) ** 2 + (5.46 * q) ** 3
+                                                 + (6.71 * q) ** 4) ** -0.25
+    return k ** (1.0 + tilt) * t * t
+
+
+@pytest.mark.parametrize("params", [(1.0, 1.5, 0.8, 0.0, 0.2, 1.0), (0.3, 2.2, 0.65, -0.15, 0.12, 1.0),
+                                    (2.5, 1.1, 0.97, 0.18, 0.29, 0.6)])
+def test_linear_pk_sigma8_normalisation(params):
+    """sigma_8^2 = int dk/k k^3 P(k) W_TH(8k)^2 / (2 pi^2) with the top hat W(x) = 3 (sin x - x cos x)/x^3.
+
+    The oracle's P(k) must be the published BBKS shape times one constant (checked at every
+    tenth grid point), and the integral, done here by adaptive quadrature over the input range
+    [1e-4, 10] of the oracle's reading, must equal the requested sigma_8^2 to 1e-8.  Over
+    (0, inf) the truncated range costs under 1e-5.  A wrong 2 pi^2, top-hat factor or BBKS
+    coefficient fails this test."""
+    from scipy.integrate import quad
+    k, r, delta = T.log_grid()
+    pk = T.linear_pk(params)
+    gam, tilt, s8 = params[4], params[3], params[2]
+    ratio = np.array([pk[i] / _bbks_published(k[i], gam, tilt) for i in range(0, T.N_IN, 10)])
+    norm = ratio[0]
+    assert np.max(np.abs(ratio / norm - 1.0)) < 1e-12
+    assert np.all(pk[T.N_IN:] == 0.0)
+
+    def w_th(x):
+        return 3.0 * (math.sin(x) - x * math.cos(x)) / x ** 3
+
+    def f(lk):
+        kk = math.exp(lk)
+        return kk ** 3 * norm * _bbks_published(kk, gam, tilt) * w_th(8.0 * kk) ** 2 / (2.0 * math.pi ** 2)
+
+    edges = np.log(np.geomspace(T.K_MIN, T.K_MAX, 200))
+    s2 = sum(quad(f, a, b, epsabs=0.0, epsrel=1e-13, limit=200)[0] for a, b in zip(edges[:-1], edges[1:]))
+    assert s2 == pytest.approx(s8 * s8, rel=1e-8)
+    tail = quad(f, math.log(T.K_MAX), math.log(1e3), epsabs=0.0, epsrel=1e-10, limit=4000)[0] + \
+        quad(f, math.log(1e-9), math.log(T.K_MIN), epsabs=0.0, epsrel=1e-10)[0]
+    assert tail < 1e-5 * s8 * s8
