@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP32-vs-FP64 error of the timed estimate")
+    ap.add_argument("--shard", action="store_true",
+                    help="time one estimate split by moment slot over the ranks (strong scaling)")
     ap.add_argument("--batch-mocks", type=int, default=64)
     return ap.parse_args()
 
@@ -140,61 +143,87 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle timing
-def oracle_sample(wl, nfields_estimate: int, ns: int = 128):
-    """Time the oracle on a bounded sample of the workload and scale to one estimate.
-
-    Sample: one Cartesian field transform of the oracle (TSC, both interlaced sub-grids,
-    two FFTs, window deconvolution) on an ns^3 grid over the same box for the first
-    count * (ns/n)^3 shape galaxies, i.e. the same galaxies per cell.  The FFT part is
-    scaled by (n/ns)^3 log(n^3)/log(ns^3), the assignment part by the particle ratio, to
-    one transform of the full catalogue on the n^3 grid; an estimate is nfields_estimate
-    such transforms plus one of the randoms.  Returns (estimates/s, seconds, description).
-    """
+def _oracle_slot_task(task):
+    """One moment slot of the oracle's estimate (a pool task): returns its seconds."""
+    cfg, cat, moments = task
     from oracle import lpp_oracle as O
-    shp = wl.shapes
-    ratio = (wl.n / ns) ** 3
-    m = max(1, int(shp.count / ratio))
-    pos = shp.pos[:, :m].astype(np.float64)
-    vals = np.asarray(shp.shape[0, :m], dtype=np.float64)
+    plan = O.Plan(n=cfg["n"], box=cfg["box"], origin=cfg["origin"], observer=cfg["observer"], pole=cfg["pole"],
+                  scheme=3, interlace=True, k_edges=cfg["k_edges"], cross_b=True, moments=moments)
     t0 = time.perf_counter()
-    mg = O.ModeGrid(ns, wl.box)
-    st0 = O.assignment_stencil(pos, ns, wl.box, wl.origin, wl.scheme, 0.0)
-    st1 = O.assignment_stencil(pos, ns, wl.box, wl.origin, wl.scheme, 0.5)
-    g0 = O.grid_from_stencil(st0, vals, ns)
-    g1 = O.grid_from_stencil(st1, vals, ns)
-    t1 = time.perf_counter()
-    inv_w = 1.0 / O.window_compensation(mg, wl.scheme)
-    phase = np.exp(-1j * math.pi * (mg.nx + mg.ny + mg.nz) / ns)
-    f = 0.5 * (np.fft.fftn(g0) + phase * np.fft.fftn(g1)) * inv_w
-    t2 = time.perf_counter()
-    del f
-    t_assign = (t1 - t0) / m                                        # per particle
-    t_fft = (t2 - t1) * ratio * math.log(wl.n ** 3) / math.log(ns ** 3)
-    n_rand = wl.randoms.count if wl.randoms is not None else 0
-    t_field = t_fft + t_assign * shp.count
-    t_est = nfields_estimate * t_field + (t_fft + t_assign * n_rand)
-    work = t2 - t0
-    desc = (f"one oracle field transform on a {ns}^3 grid with {m} of {shp.count} shape galaxies "
-            f"({work:.2f} s), scaled to {wl.n}^3 and the full catalogue, times {nfields_estimate} Cartesian "
-            f"field transforms plus one of the {n_rand} randoms (numpy/pocketfft, 1 thread)")
-    return 1.0 / t_est, work, desc
+    O.multipoles(plan, cat["pos"], None, cat["shape"], None, None, None, cat["rpos"], None, cat["rnbar"])
+    return time.perf_counter() - t0
 
 
-def oracle_field_count():
-    """Cartesian field transforms the oracle performs per estimate (all moments, cross E+B)."""
-    from oracle import lpp_oracle as O
-    sym2, sym4 = len(O.sym_index_sets(2)), len(O.sym_index_sets(4))
-    cnt = 0
-    for L in (2, 4, 6):
-        q = O.reduced_assoc_legendre(2, L)
-        cnt += sym2 * sum(len(O.monomials(p)) for p, c in enumerate(q) if c != 0)
-    for l in (0, 2, 4):
-        q = O.legendre_coeffs(l)
-        cnt += sum(len(O.monomials(p)) for p, c in enumerate(q) if c != 0)
-    for L in (4, 6, 8):
-        q = O.reduced_assoc_legendre(4, L)
-        cnt += sym4 * sum(len(O.monomials(p)) for p, c in enumerate(q) if c != 0)
-    return cnt + 3   # gamma, gamma* and the density partner
+class OracleTimer:
+    """The FP64 oracle as it stands, timed on the host cores on a bounded sample of the workload.
+
+    Sample: one complete oracle estimate (all ten moment slots, cross E and B parts, TSC +
+    interlacing, the randoms) on an ns^3 grid over the same box, with the first
+    count (ns/n)^3 shape galaxies and randoms (the same particles per cell).  The oracle's
+    cost is dominated by its field transforms, so the time is scaled to the n^3 grid by
+    (n/ns)^3 log(n^3)/log(ns^3) (an extrapolation, stated in the sample text).  With
+    workers > 1 the ten slots run as separate processes of a spawn pool (each recomputes the
+    partner fields, as the oracle does for one slot) and the wall time of the whole set is
+    taken; the pool is created before any GPU work and warmed before timing."""
+
+    def __init__(self, wl, ns: int = 64, workers: int = 1):
+        import multiprocessing as mp
+        self.wl, self.ns = wl, ns
+        ratio = (wl.n / ns) ** 3
+        shp, rnd = wl.shapes, wl.randoms
+        m, mr = max(1, int(shp.count / ratio)), max(1, int(rnd.count / ratio)) if rnd is not None else 0
+        self.counts = (m, mr)
+        self.cat = dict(pos=shp.pos[:, :m].astype(np.float64), shape=shp.shape[:, :m].astype(np.float64),
+                        rpos=rnd.pos[:, :mr].astype(np.float64), rnbar=rnd.nbar[:mr].astype(np.float64))
+        self.cfg = dict(n=ns, box=wl.box, origin=wl.origin, observer=wl.observer, pole=wl.pole,
+                        k_edges=np.asarray(wl.k_edges))
+        self.scale = ratio * math.log(wl.n ** 3) / math.log(ns ** 3)
+        self.workers = max(1, min(workers, 10))
+        self.pool = None
+        if self.workers > 1:
+            self.pool = mp.get_context("spawn").Pool(self.workers)
+            self.pool.map(abs, range(self.workers))   # start the workers before timing
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+            self.pool = None
+
+    def sample(self):
+        """One timed sample: (estimates/s scaled to the workload, wall seconds, description)."""
+        from oracle import lpp_oracle as O
+        t0 = time.perf_counter()
+        if self.pool is None:
+            _oracle_slot_task((self.cfg, self.cat, tuple(O.MOMENTS)))
+        else:
+            self.pool.map(_oracle_slot_task, [(self.cfg, self.cat, (mom,)) for mom in O.MOMENTS], chunksize=1)
+        wall = time.perf_counter() - t0
+        wl = self.wl
+        desc = (f"one complete oracle estimate (ten slots, cross E+B, TSC+interlacing) on a {self.ns}^3 grid over "
+                f"the same box with {self.counts[0]} of {wl.shapes.count} shape galaxies and {self.counts[1]} of "
+                f"{wl.randoms.count} randoms ({wall:.2f} s wall on {self.workers} process"
+                f"{'es, one per moment slot' if self.workers > 1 else ''}), extrapolated to {wl.n}^3 by "
+                f"(n/ns)^3 log(n^3)/log(ns^3) = {self.scale:.0f} (numpy/pocketfft, one thread per process)")
+        return 1.0 / (wall * self.scale), wall, desc
+
+
+def cpu_baseline_leg(wl, steps: int = 1):
+    """The oracle on all host cores (nproc, moment-parallel) and on one core."""
+    nproc = os.cpu_count() or 1
+    out = {}
+    for key, workers in (("all", nproc), ("one", 1)):
+        tmr = OracleTimer(wl, workers=workers)
+        vals, desc = [], ""
+        for _ in range(steps):
+            v, _, desc = tmr.sample()
+            vals.append(v)
+        tmr.close()
+        out[key] = {"value": statistics.median(vals), "cores": tmr.workers, "sample": desc}
+    a, o = out["all"], out["one"]
+    return {"value": a["value"], "unit": UNIT, "cores": a["cores"], "nproc": nproc, "kind": "oracle",
+            "sample": a["sample"], "single_core": {"value": o["value"], "unit": UNIT, "cores": 1,
+                                                   "sample": o["sample"]}}
 
 
 def run_reference(args):
@@ -202,13 +231,14 @@ def run_reference(args):
     if rank != 0:
         return
     wl = workload(args, seed=0)
-    nf = oracle_field_count()
-    vals, works, desc = [], [], ""
+    nproc = os.cpu_count() or 1
+    tmr = OracleTimer(wl, workers=nproc)
+    vals, desc = [], ""
     for i in range(args.warmup + args.steps):
-        v, w, desc = oracle_sample(wl, nf)
+        v, w, desc = tmr.sample()
         if i >= args.warmup:
             vals.append(v)
-            works.append(w)
+    tmr.close()
     v = statistics.median(vals)
     out = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
@@ -216,7 +246,8 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name, "n": wl.n, "box": wl.box, "shape_galaxies": wl.shapes.count,
                    "randoms": wl.randoms.count if wl.randoms is not None else 0, "scheme": "tsc", "interlace": True},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": tmr.workers, "nproc": nproc, "kind": "oracle",
+                         "sample": desc},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -306,14 +337,8 @@ def batch_leg(args, dev, steps: int):
         ref = p64.multipoles()
         del p64
         torch.cuda.empty_cache()
-        # per bin: |P| + sqrt(P_+^(0) P_dd^(0)) before shot-noise subtraction (the error scale
-        # of the parity tests), max over bins
-        pp = np.abs(ref.raw[4].real) / max(ref.norm_auto, 1e-300)
-        pd = np.abs(ref.raw[0].real) / max(ref.norm_dd, 1e-300)
-        sc = np.abs(ref.p) + np.sqrt(pp * pd)[None, :]
-        sc = np.where(sc > 0, sc, 1.0)
-        e = (np.abs(res[j].p - ref.p) / sc).max(axis=1)
-        errs[f"{n}^3"] = {f"{k}{l}": float(v) for (k, l), v in zip(MOMENT_NAMES, e)}
+        e = slot_errors(res[j].p, ref)
+        errs[f"{n}^3"] = {f"{k}{l}": float(v) for (k, l), v in zip(MOMENT_NAMES[:10], e)}
     counts = [m.count for m in mocks]
     out = {"value": len(mocks) * steps / (ms / 1000.0), "unit": "estimates/s", "mocks": len(mocks),
            "grids": {f"{n}^3": sum(1 for m in mocks if m.n == n) for n in grids},
@@ -330,7 +355,45 @@ def batch_leg(args, dev, steps: int):
 
 
 MOMENT_NAMES = [("dd", 0), ("cross", 2), ("cross", 4), ("cross", 6), ("plus", 0), ("plus", 2), ("plus", 4),
-                ("minus", 4), ("minus", 6), ("minus", 8)]
+                ("minus", 4), ("minus", 6), ("minus", 8), ("dd", 2), ("dd", 4)]
+
+
+def slot_errors(p, ref):
+    """Per moment slot: max over shells of |p - ref.p| / (|ref.p| + sqrt(P_+^(0) P_dd^(0))), the
+    monopoles taken before shot-noise subtraction (the error scale of the parity tests)."""
+    pp = np.abs(ref.raw[4].real) / max(ref.norm_auto, 1e-300)
+    pd = np.abs(ref.raw[0].real) / max(ref.norm_dd, 1e-300)
+    sc = np.abs(ref.p) + np.sqrt(pp * pd)[None, :]
+    sc = np.where(sc > 0, sc, 1.0)
+    return (np.abs(p - ref.p) / sc).max(axis=1)
+
+
+def precision_leg(wl, est, common, dev):
+    """The timed FP32 estimate against the FP64 path on the same catalogues (positions, shapes
+    and n-bar of the FP32 run, widened): per moment slot, the largest error over the shells
+    in units of the parity tests' scale.  The FP64 path matches the FP64 oracle to 1e-10 in
+    the tests, and the FP32 path of this grid and configuration is compared with the oracle
+    directly at 512^3 (tests/test_gpu_survey_fullsize.py)."""
+    import torch
+
+    from paper_2202_11839_gb300 import lpp as L
+    shp, rnd = wl.shapes, wl.randoms
+    td = lambda a: torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float32), dtype=np.float64)).to(dev)
+    c64 = dict(common, precision=L.LPP_FP64, batch=0)
+    t0 = time.perf_counter()
+    p64 = L.Plan(wl.n, wl.box, wl.k_edges, **c64)
+    pos, shape, rpos, rnbar = td(shp.pos), td(shp.shape), td(rnd.pos), td(rnd.nbar)
+    p64.assign(L.LPP_SHAPES, pos, None, None, shape, L.LPP_SHAPE_TENSOR6)
+    p64.assign(L.LPP_RANDOMS, rpos, None, rnbar)
+    ref = p64.multipoles()
+    p64.close()
+    del p64, pos, shape, rpos, rnbar
+    torch.cuda.empty_cache()
+    e = slot_errors(est.p, ref)
+    return {"error_vs_fp64": {f"{k}{l}": float(v) for (k, l), v in zip(MOMENT_NAMES, e)
+                              if common["moments"] & (1 << MOMENT_NAMES.index((k, l)))},
+            "scale": "|P_fp64| + sqrt(P_+^(0) P_dd^(0)) per shell, max over the shells",
+            "fp64_estimate_s": time.perf_counter() - t0}
 
 
 def run_lpp(args):
@@ -401,6 +464,9 @@ def run_lpp(args):
     templates = None
     if rank == 0 and not args.no_surrogate:
         templates = template_leg(plan, est, wl, dev)
+    precision = None
+    if rank == 0 and not args.no_fp64:
+        precision = precision_leg(wl, est, common, dev)
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -440,8 +506,7 @@ def run_lpp(args):
         batched = batch_leg(args, dev, max(1, min(args.steps, 3)))
     cpu = None
     if world == 1 and not args.no_cpu:
-        v, work, desc = oracle_sample(wl, oracle_field_count())
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        cpu = cpu_baseline_leg(wl)
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
@@ -466,9 +531,79 @@ def run_lpp(args):
         "clocks": clk,
         "kernels": kern,
         "templates": templates,
+        "precision": precision,
         "batched": batched,
     }
     print(json.dumps(out), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def run_shard(args):
+    """One estimate of the survey workload split by moment slot over the ranks (every rank
+    recomputes the partner fields, computes its slots' channels, then one sum all-reduce of
+    the FP64 rows and one max all-reduce of the shell data over NCCL): strong scaling, one
+    estimate per step for the whole job."""
+    import torch
+
+    from paper_2202_11839_gb300 import lpp as L
+    from paper_2202_11839_gb300 import shard as SH
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    L.load_library()
+    wl = workload(args, seed=0)
+    shp, rnd = wl.shapes, wl.randoms
+    tt = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    d_pos, d_shape, d_rpos, d_rnbar = tt(shp.pos), tt(shp.shape), tt(rnd.pos), tt(rnd.nbar)
+    moments = L.LPP_WANT_ALL if args.moment_mask < 0 else args.moment_mask
+    mask = SH.partition(moments, world)[rank]
+    plan = None
+    if mask:
+        plan = L.Plan(wl.n, wl.box, wl.k_edges, origin=wl.origin, observer=wl.observer, pole=wl.pole,
+                      scheme=L.LPP_TSC, interlace=True, precision=L.LPP_FP32, moments=mask, max_shapes=shp.count,
+                      max_randoms=rnd.count, batch=args.batch)
+        plan.assign(L.LPP_SHAPES, d_pos, None, None, d_shape, L.LPP_SHAPE_TENSOR6)
+        plan.assign(L.LPP_RANDOMS, d_rpos, None, d_rnbar)
+
+    def step():
+        est = plan.multipoles() if plan is not None else None
+        return SH.gather(est, mask, pg, dev)
+
+    for _ in range(args.warmup):
+        out = step()
+    assert np.all(np.isfinite(out.p)), "non-finite estimate"
+    clocks = ClockSampler(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        out = step()
+    torch.cuda.synchronize()
+    elapsed = time.perf_counter() - t0
+    clk = clocks.stop()
+    if pg:
+        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        elapsed = float(t.item())
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": args.steps / elapsed, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "n": wl.n, "shape_galaxies": shp.count, "randoms": rnd.count,
+                       "parallelism": f"moment-slot shards x{world}", "masks": SH.partition(moments, world),
+                       "l2": "inputs larger than L2 (each grid 1 GiB)"},
+            "timing": "host wall clock around the steps, a device synchronisation on both sides (the gather "
+                      "copies the rows to the host every step)",
+            "clocks": clk}), flush=True)
     if pg:
         pg.destroy_process_group()
 
@@ -477,6 +612,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.shard:
+        run_shard(args)
     else:
         run_lpp(args)
 

@@ -9,7 +9,7 @@
  *   cross  P^(L)_gd, L = 2,4,6   Sec. 3.1.2, Eqs. lpp_estimator_cross_Xiij, def_of_Xiij
  *   plus   P^(l)_+,  l = 0,2,4   Eq. lpp_estimator_auto_+ (Appendix B)
  *   minus  P^(L)_-,  L = 4,6,8   Eqs. lpp_estimator_auto_-, def_of_Xiijkl (Appendix B)
- *   density monopole P^(0)_dd    Eq. lpp_dens_app with l = 0
+ *   density   P^(l)_dd, l = 0,2,4 Sec. 3.1.1, Eqs. lpp_dens_app, delta_ell
  *
  * The shear of each galaxy is gamma = e_ij(x) s_ij (Eq. gamma_def), with
  * e_ij = e+_i e+_j and e+ = (e_theta + i e_phi)/sqrt(2) (Eqs. def_of_eij_+2,
@@ -59,18 +59,27 @@ enum { LPP_SHAPES = 0, LPP_DENSITY = 1, LPP_RANDOMS = 2 };
 /* shape inputs */
 enum { LPP_SHAPE_NONE = 0, LPP_SHAPE_GAMMA12 = 1, LPP_SHAPE_TENSOR6 = 2 };
 
-/* Moment slots of every output array, in this order. */
-#define LPP_N_MOMENTS 10
+/* Moment slots of every output array, in this order.  Slots 10 and 11 are the density
+ * quadrupole and hexadecapole P^(2,4)_dd of Eq. lpp_dens_app (Yamamoto form: each
+ * catalogue's delta^(l) with its own endpoint lines of sight, Eq. delta_ell). */
+#define LPP_N_MOMENTS 12
 enum {
     LPP_MOM_DD0 = 0,
     LPP_MOM_CROSS2 = 1, LPP_MOM_CROSS4 = 2, LPP_MOM_CROSS6 = 3,
     LPP_MOM_PLUS0 = 4, LPP_MOM_PLUS2 = 5, LPP_MOM_PLUS4 = 6,
-    LPP_MOM_MINUS4 = 7, LPP_MOM_MINUS6 = 8, LPP_MOM_MINUS8 = 9
+    LPP_MOM_MINUS4 = 7, LPP_MOM_MINUS6 = 8, LPP_MOM_MINUS8 = 9,
+    LPP_MOM_DD2 = 10, LPP_MOM_DD4 = 11
 };
-/* bitmask of requested moments: bit i enables slot i; LPP_WANT_CROSS_B adds the
- * B (imaginary) part of the cross moments, which costs 2L+1 extra fields per L. */
+/* bitmask of requested moments: bit i enables slot i.  LPP_WANT_ALL is the ten slots of
+ * the density monopole and the tensor estimators; LPP_WANT_DENSITY adds the density
+ * quadrupole and hexadecapole (2l+1 fields each, from the density catalogue and the
+ * randoms).  LPP_WANT_CROSS_B adds the B (imaginary) part of the cross moments, which
+ * costs 2L+1 extra fields per L. */
 #define LPP_WANT_ALL 0x3FFu
-#define LPP_WANT_CROSS_B (1u << 10)
+#define LPP_WANT_DD2 (1u << LPP_MOM_DD2)
+#define LPP_WANT_DD4 (1u << LPP_MOM_DD4)
+#define LPP_WANT_DENSITY (LPP_WANT_DD2 | LPP_WANT_DD4)
+#define LPP_WANT_CROSS_B (1u << 16)
 
 typedef struct lpp_plan_s* lpp_plan_t;
 
@@ -122,7 +131,17 @@ typedef struct {
     double alpha;         /* out: sum w_density / sum w_randoms (0 without randoms)           */
 } lpp_result;
 
-/* Create a plan from a descriptor; validates sizes and flags on the host only. */
+/* Create a plan from a descriptor; validates sizes and flags on the host only.  The plan
+ * fixes what every estimate of it computes (Sec. 3.1.2): the grid of Eq. lpp_estimator_cross_Xiij
+ * (n^3 nodes over the box, CIC/TSC assignment, optional interlacing and window deconvolution),
+ * the |k| shells of the multipoles (Eq. multipole_cross_def), the requested moments and, from
+ * them, the real harmonic fields (2L+1 per moment order and projected part, because each
+ * kernel of Eqs. def_of_Xiij, def_of_Xiijkl and lpp_estimator_auto_+ is a pure degree-L
+ * spherical harmonic in khat), the sky frame of Eq. gamma_def about `pole`, and the line of
+ * sight of the projection and of the estimator (cases (a)-(c) of Sec. 4.2).
+ * Errors: LPP_ERR_UNSUPPORTED for a grid that is not a power of two in [8, 1024],
+ * LPP_ERR_INVALID_ARG for any other bad field (shells, scheme, precision, moments, a zero
+ * pole or global line of sight).  On success *plan is owned by the caller (lpp_plan_destroy). */
 lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* plan);
 void lpp_plan_destroy(lpp_plan_t plan);
 
@@ -136,10 +155,17 @@ lpp_status lpp_plan_set_stream(lpp_plan_t plan, void* stream);
 /* Number of real k-space fields one estimate transforms (channels plus partners). */
 lpp_status lpp_plan_field_count(lpp_plan_t plan, int* n_fields);
 
-/* Attach a catalogue to a role.  Device pointers are referenced (they must stay valid
- * until lpp_multipoles returns); host pointers are copied into the workspace on the
- * plan's stream.  LPP_SHAPES is required; LPP_DENSITY defaults to the shapes'
- * positions and weights; LPP_RANDOMS is optional (none = periodic box). */
+/* Attach a catalogue to a role: the galaxies whose shapes form gamma (Eq. gamma_def) and
+ * the shear field of Eq. lpp_estimator_cross_Xiij (LPP_SHAPES), the density tracer delta
+ * (LPP_DENSITY), or the randoms that describe the survey window (LPP_RANDOMS; delta = data -
+ * alpha randoms, Sec. 4.3).  Device pointers are referenced (they must stay valid until
+ * lpp_multipoles returns); host pointers are copied into the workspace on the plan's
+ * stream.  LPP_SHAPES is required; LPP_DENSITY defaults to the shapes' positions and
+ * weights; LPP_RANDOMS is optional (none = periodic box).  Errors: LPP_ERR_INVALID_ARG for a
+ * count above the role's capacity, a null pointer, a bad shape kind or missing shapes that
+ * the requested moments need, host memory on a plan without staging; LPP_ERR_NOT_READY for
+ * host memory before the workspace is set.  Positions are checked against the box during
+ * lpp_multipoles (LPP_ERR_DOMAIN). */
 lpp_status lpp_assign(lpp_plan_t plan, int role, const lpp_particles* particles);
 /* Forget a role's catalogue (e.g. to run a periodic estimate after a survey one). */
 lpp_status lpp_clear(lpp_plan_t plan, int role);
@@ -147,6 +173,12 @@ lpp_status lpp_clear(lpp_plan_t plan, int role);
 /* Run the estimator (Secs. 3.1.1-3.1.2): sky frames and shears, harmonic weights,
  * CIC/TSC assignment with optional interlacing, 3D FFTs, k-space contraction with
  * the partner field and FP64 shell sums; then normalise and subtract shot noise.
+ * Density multipoles (slots 10, 11): P^(l)_dd = (2l+1) < delta^(l)(k) delta(-k) > / I_dd
+ * with delta^(l) = FT[w L_l(khat . xhat)] of the density catalogue minus alpha times that
+ * of the randoms, computed through the addition theorem L_l(khat . xhat) =
+ * 4 pi / (2l+1) sum_n Y_ln(khat) Y_ln(xhat) as 2l+1 real fields FT[w Y_ln(xhat)]; no shot
+ * noise for l > 0 (its shell average of L_l vanishes).  With los_est = GLOBAL the plan's
+ * global line of sight replaces xhat (Eq. gpp_dens).
  * Synchronises the plan's stream.  Returns LPP_ERR_DOMAIN if a particle was outside
  * the box, at the observer, or on the frame pole. */
 lpp_status lpp_multipoles(lpp_plan_t plan, lpp_result* result);
@@ -165,7 +197,10 @@ lpp_status lpp_window_Q(lpp_plan_t plan, int n_s, const double* s_edges, double*
                         long long* n_points, double* norm);
 
 /* ------------------------------------------------------------------ batches of catalogues
- * Many catalogues (mocks) through a set of plans in one launch.  plans[0..n_plans) are
+ * Many catalogues (mocks) through a set of plans in one launch: the estimator of Secs.
+ * 3.1.1-3.1.2 (each mock exactly as lpp_multipoles would compute it on its plan) over many
+ * realisations, as in the validation of Sec. 4 (1000 realisations of the tidal field, Sec.
+ * 4.1, whose mean Secs. 4.2-4.3 compare between estimators and with the template).  plans[0..n_plans) are
  * distinct plans with their workspaces set (they may differ in grid size and bins); mock j
  * runs on plans[plan_of[j]] with the device catalogues shapes[j] (shape kind GAMMA12 or
  * TENSOR6) and randoms[j] (randoms == NULL or randoms[j].count == 0: periodic box).  Mocks
@@ -199,7 +234,9 @@ lpp_status lpp_batch_launch_count(lpp_batch_t batch, long long* counted, long lo
 /* ------------------------------------------------------------------ templates
  * Window-convolved theory templates (Sec. 3.2, Eqs. window_convolution_X_hankel and
  * def_of_Q_llp; Appendix D): for every parameter set (A, b_g, sigma_8, tilt, Gamma,
- * shot-noise scale) the ten native moment slots (the estimator's order)
+ * shot-noise scale) the twelve native moment slots (the estimator's order; the density
+ * quadrupole and hexadecapole are the leakage of the monopole through the window, the
+ * mixtures Q^dd_20 = Q_2 and Q^dd_40 = Q_4 of Sec. 4.3)
  *   Pt^(L)_X(k) = H_L[ sum_L' Q^X_LL'(r) xi^(L')_X(r) ](k),  xi^(L')_X = H^-1_L'[P^(L')_X],
  * of the tidal-alignment model (shapes e = -A T_ij, galaxies b_g delta; Eq.
  * power_for_validation scaled): P_dd^(0) = b^2 P, P_gd^(2) = -A b P / 6,
@@ -291,7 +328,7 @@ typedef struct {
 lpp_status lpp_surrogate_set_map(lpp_surrogate_t net, const lpp_surrogate_map* map);
 /* Training targets y (device FP32 [n][320]) from device params [n][6] and the native slots
  * that lpp_convolve_template returned for them at unit amplitude and no shot noise
- * (device FP64 [n][10][40]). */
+ * (device FP64 [n][LPP_N_MOMENTS][40]). */
 lpp_status lpp_surrogate_targets(lpp_surrogate_t net, const double* params, const double* native, int n, float* y,
                                  void* stream);
 /* Network inputs for device params [n][6] (FP64) -> device x [n][6] (FP32). */
@@ -336,23 +373,39 @@ lpp_status lpp_plan_kernel_stats(lpp_plan_t plan, int kind, double* ms, long lon
  * LPP_ERR_INVALID_ARG for a null plan or pointer. */
 lpp_status lpp_plan_launch_count(lpp_plan_t plan, long long* launches);
 
+/* Which forms of the fused assignment + x-FFT pass the last lpp_multipoles call ran (a
+ * check for tests and profiles; no counterpart in the paper).  stats[6], host output:
+ * [0] one-slot launches, [1] two-slot launches (two channel fields per CTA, FP32 interlaced
+ * 256^3 and 512^3 grids), [2] two-slot tiles accumulated in 32-bit fixed point, [3] two-slot
+ * tiles accumulated with float atomics, [4] one-slot channel tiles in fixed point, [5] one-slot
+ * channel tiles with float atomics (tiles that no particle reaches are not counted).
+ * Synchronises the plan's stream.  LPP_ERR_NOT_READY without a workspace. */
+lpp_status lpp_plan_path_stats(lpp_plan_t plan, long long* stats);
+
 /* Density monopole P_dd^(0) of a periodic catalogue without any device allocation.
  * The paper has no counterpart: this entry point exists for callers that cannot call
  * cudaMalloc (code running inside another framework's memory pool or under a fixed
- * per-process memory cap, plug-ins handed a stream but no allocator).  It runs the
- * same assignment, FFT and shell-sum kernels as the LPP_MOM_DD0 slot of
- * lpp_multipoles for a periodic box (I = (sum w)^2/V, shot noise sum w^2 / I always
- * subtracted), but keeps every intermediate in one fixed 40 MiB device array inside
- * the library, which each GPU that loads liblpp holds until the process exits.
- *  - Sizes: FP32 grids up to n = 128, FP64 grids up to n = 64; larger grids return
+ * per-process memory cap, plug-ins handed a stream but no allocator).  It computes the
+ * quantity of the LPP_MOM_DD0 slot of lpp_multipoles for a periodic box (I = (sum w)^2/V,
+ * shot noise sum w^2 / I always subtracted) by its own simpler path: an unsorted scatter
+ * with global atomics into one grid, a full 3D FFT and the partner-mode shell sums, not
+ * the fused sorted-tile kernels of lpp_multipoles.  Every intermediate lives in one fixed
+ * 40 MiB device array inside the library, which each GPU that loads liblpp holds until
+ * the process exits.
+ *  - Sizes: grids up to n = 128 in FP32 and in FP64; larger grids return
  *    LPP_ERR_WORKSPACE.  n_bins <= 256.
- *  - pos [3][count] and w [count] (or NULL) are device pointers of the given precision;
- *    p_out [n_bins] and n_modes_out [n_bins] (or NULL) are host memory.
+ *  - pos [3][count] and w [count] (or NULL: unit weights) are device pointers of the given
+ *    precision; p_out [n_bins] and n_modes_out [n_bins] (or NULL) are host memory.
+ *    count = 0 gives zeros.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *    and caches it; make that first call before any stream capture on the device.
+ *    and caches it for the lifetime of the process; after cudaDeviceReset on that device
+ *    the cached address is stale, so do not reset a device this entry point has used.
+ *  - Each call clears what it accumulates into, copies its results to the host and
+ *    synchronises `stream` before returning; it must not be called while `stream` (or the
+ *    legacy default stream it may be) is being captured into a CUDA graph.
  *  - All calls share the one array: calls that overlap on the GPU (other streams or
- *    other host threads) race and corrupt each other's results.  Each call clears what
- *    it accumulates into and synchronises `stream` before returning. */
+ *    other host threads) race and corrupt each other's results.  Host-side tables are
+ *    per thread. */
 lpp_status lpp_density_monopole_static(int n, double box, const double* origin, int scheme, int interlace,
                                        int compensate, int precision, const void* pos, const void* w,
                                        long long count, int n_bins, const double* k_edges, double* p_out,

@@ -44,9 +44,11 @@ K_MAX = 10.0
 Q_INV = 1.5
 Q_FWD = 0.5
 
-# output slots in the order of the estimator (dd0, cross2,4,6, plus0,2,4, minus4,6,8)
+# output slots in the order of the estimator (dd0, cross2,4,6, plus0,2,4, minus4,6,8, dd2,4);
+# the density quadrupole and hexadecapole of the model (no redshift-space distortions) are
+# pure window leakage of the monopole, the mixtures Q^dd_20 and Q^dd_40 (Sec. 4.3)
 SLOTS = [("dd", 0), ("cross", 2), ("cross", 4), ("cross", 6), ("plus", 0), ("plus", 2), ("plus", 4),
-         ("minus", 4), ("minus", 6), ("minus", 8)]
+         ("minus", 4), ("minus", 6), ("minus", 8), ("dd", 2), ("dd", 4)]
 M_OF = {"dd": 0, "cross": 2, "plus": 0, "minus": 4}
 
 
@@ -191,7 +193,7 @@ def bin_average(pk_grid, k_edges):
 
 
 def template(params, q_table, s, k_edges, shot_plus: float = 0.0, mixing=None):
-    """All ten window-convolved native multipoles of one parameter set, shell-averaged: (10, nb)."""
+    """All twelve window-convolved native multipoles of one parameter set, shell-averaged: (12, nb)."""
     k, r, delta = log_grid()
     pk = linear_pk(params)
     xi = {lp: hankel_inverse(pk, lp) for lp in (0, 2, 4)}

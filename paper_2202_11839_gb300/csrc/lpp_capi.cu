@@ -45,7 +45,8 @@ struct lpp_plan_s {
     std::vector<long long> n_modes;
     std::vector<double> k_mean;
     // channels
-    std::vector<Channel> channels;
+    std::vector<Channel> channels;   // tensor channels first, then the density multipole channels
+    int n_tensor_ch = 0;             // channels[0 .. n_tensor_ch) read the shape coefficients
     std::vector<CoeffGroup> groups;
     int n_coeff_rows = 2;
     bool need_d = false, need_g = false;
@@ -73,6 +74,7 @@ struct lpp_plan_s {
     size_t off_plive = 0;                // [3][n*n] bytes: x pencils reached per role
     size_t off_tranges = 0;              // per-tile range records of the two-slot fused passes
     size_t off_work = 0;                 // item counter of the dynamically scheduled fused passes
+    size_t off_pstat = 0;                // [4] tile counters of the fused passes (FusedArgs::pstat)
     int fty = 4, ftz = 4;
     int n_partner = 0;
     int out_rows = 0;
@@ -83,6 +85,7 @@ struct lpp_plan_s {
     std::string err;
     int n_sm = 152;
     long long n_launch = 0;   // kernels launched by the last estimate
+    long long n_fused[2] = {0, 0};   // fused assignment launches of the last estimate: one-slot, two-slot
 };
 
 // FP32 interlaced grids of 256^3 or 512^3: channel batches with an even slot count run the
@@ -146,7 +149,7 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
     if ((d.los_proj != LPP_LOS_LOCAL && d.los_proj != LPP_LOS_GLOBAL) ||
         (d.los_est != LPP_LOS_LOCAL && d.los_est != LPP_LOS_GLOBAL))
         return LPP_ERR_INVALID_ARG;
-    if ((d.moments & LPP_WANT_ALL) == 0) return LPP_ERR_INVALID_ARG;
+    if ((d.moments & (LPP_WANT_ALL | LPP_WANT_DENSITY)) == 0) return LPP_ERR_INVALID_ARG;
     if (d.max_shapes < 0 || d.max_density < 0 || d.max_randoms < 0) return LPP_ERR_INVALID_ARG;
     if (d.batch < 0 || d.batch > kMaxSlots) return LPP_ERR_INVALID_ARG;
     for (int i = 0; i < d.n_bins; ++i)
@@ -250,8 +253,26 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
     for (int i = 0; i < 3; ++i)
         if (m & (1u << minusSlot[i])) add_group(KIND_MINUS, 4 + 2 * i, 1, plan->kp.minus[i], 2 * i + 1, minusSlot[i]);
     plan->n_coeff_rows = row;
+    plan->n_tensor_ch = (int)plan->channels.size();
+    // density multipoles (Eqs. lpp_dens_app, delta_ell): by the addition theorem
+    // L_l(khat . xhat) = 4 pi / (2l+1) sum_n Y_ln(khat) Y_ln(xhat), 2l+1 real fields
+    // FT[w Y_ln(xhat)] of the density catalogue minus alpha times those of the randoms
+    for (int l = 2; l <= 4; l += 2) {
+        const int slot = l == 2 ? LPP_MOM_DD2 : LPP_MOM_DD4;
+        if (!(m & (1u << slot))) continue;
+        for (int nn = -l; nn <= l; ++nn) {
+            Channel c;
+            c.kind = KIND_DENS;
+            c.L = l;
+            c.n = nn;
+            c.part = PART_RE;
+            c.moment = slot;
+            c.coeff = -1;
+            plan->channels.push_back(c);
+        }
+    }
     plan->need_d = (m & ((1u << LPP_MOM_DD0) | (1u << LPP_MOM_CROSS2) | (1u << LPP_MOM_CROSS4) |
-                         (1u << LPP_MOM_CROSS6))) != 0;
+                         (1u << LPP_MOM_CROSS6) | LPP_WANT_DENSITY)) != 0;
     plan->need_g = (m & ((1u << LPP_MOM_PLUS0) | (1u << LPP_MOM_PLUS2) | (1u << LPP_MOM_PLUS4) |
                          (1u << LPP_MOM_MINUS4) | (1u << LPP_MOM_MINUS6) | (1u << LPP_MOM_MINUS8))) != 0;
     plan->n_partner = (plan->need_d ? 1 : 0) + (plan->need_g ? 2 : 0);
@@ -310,6 +331,7 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
     plan->off_plive = take((size_t)3 * n * n);
     plan->off_tranges = take(two_slot_grid(plan) ? tile_range_bytes(n, plan->fty, plan->ftz) : sizeof(int));
     plan->off_work = take(sizeof(int));
+    plan->off_pstat = take(4 * sizeof(int));
     plan->off_wout = take((size_t)kWindowChannels * 256 * 2 * sizeof(double));
     plan->off_wthr = take(257 * sizeof(int));
     plan->off_partner = take((size_t)std::max(1, plan->n_partner) * n3 * cs);
@@ -439,7 +461,7 @@ extern "C" lpp_status lpp_assign(lpp_plan_t plan, int role, const lpp_particles*
     int sk = role == LPP_SHAPES ? p->shape_kind : LPP_SHAPE_NONE;
     if (sk != LPP_SHAPE_NONE && sk != LPP_SHAPE_GAMMA12 && sk != LPP_SHAPE_TENSOR6)
         return fail(plan, LPP_ERR_INVALID_ARG, "bad shape kind");
-    if (role == LPP_SHAPES && plan->need_g + (plan->channels.empty() ? 0 : 1) > 0 && sk == LPP_SHAPE_NONE)
+    if (role == LPP_SHAPES && plan->need_g + (plan->n_tensor_ch > 0 ? 1 : 0) > 0 && sk == LPP_SHAPE_NONE)
         return fail(plan, LPP_ERR_INVALID_ARG, "the requested moments need shapes");
     if (sk != LPP_SHAPE_NONE && p->count > 0 && !p->shape) return fail(plan, LPP_ERR_INVALID_ARG, "null shapes");
     Catalogue c;
@@ -513,8 +535,10 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
     LPP_CUDA(cudaMemsetAsync(sums, 0, SUM_COUNT * sizeof(double), st));
     LPP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
     LPP_CUDA(cudaMemsetAsync(out, 0, (size_t)plan->out_rows * nb * 2 * sizeof(double), st));
+    LPP_CUDA(cudaMemsetAsync(plan->ws + plan->off_pstat, 0, 4 * sizeof(int), st));
     long long& nl = plan->n_launch;
     nl = 0;
+    plan->n_fused[0] = plan->n_fused[1] = 0;
 
     // 0. pencil sort of every catalogue (cell coordinates and weights in x-pencil key order)
     const long long caps[3] = {std::max<long long>(1, plan->d.max_shapes), std::max<long long>(1, plan->d.max_density),
@@ -724,6 +748,16 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
     fa.sums = sums;
     fa.pmask = pmask;
     fa.skip_empty = 1;
+    fa.pstat = (int*)(plan->ws + plan->off_pstat);
+    // harmonic weights of the density multipole channels: line of sight from the observer
+    // (or the global direction when the estimator uses one)
+    for (int a = 0; a < 3; ++a) {
+        fa.observer[a] = plan->d.observer[a];
+        fa.origin[a] = plan->d.origin[a];
+        fa.los_global[a] = plan->d.los_global[a];
+    }
+    fa.h = plan->box / n;
+    fa.ylm_global = plan->d.los_est == LPP_LOS_GLOBAL ? 1 : 0;
     const double xbytes = (double)n * n * plan->nky * sizeof(c2<T>);   // kept x pencils of one grid
     auto slot_bits = [&](const FusedSlot& f) {
         int bits = 0;
@@ -738,6 +772,7 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         if (tm) tm->begin(KK_ASSIGN, st);
         LPP_CUDA(launch_assign_xfft<T>(fa, st));
         nl += fa.n_slots > 0 ? 1 : 0;
+        if (fa.n_slots > 0) plan->n_fused[fa.dual ? 1 : 0] += 1;
         if (tm) {
             // kept x pencils are stored on the planes the slot's particles reach
             double wb = 0.0;
@@ -826,13 +861,19 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         if (tm) tm->end(KK_PARTNER, st, shell_modes * sizeof(c2<T>) * (pgrids + plan->n_partner));
     }
 
-    // 3. channel fields, a batch of grids at a time
+    // 3. channel fields, a batch of grids at a time: the tensor channels (coefficient rows of
+    // the shape catalogue), then the density multipole channels (harmonic weights of the density
+    // catalogue and the randoms); a batch never mixes the two
     const int per_grid = il ? 1 : 2;
     cb.partner_mode = 0;
+    const int n_tch = plan->n_tensor_ch;
+    std::vector<std::pair<int, int>> batches;
+    for (int c0 = 0; c0 < n_tch; c0 += plan->batch_ch) batches.push_back({c0, std::min(n_tch, c0 + plan->batch_ch)});
+    for (int c0 = n_tch; c0 < n_ch; c0 += plan->batch_ch) batches.push_back({c0, std::min(n_ch, c0 + plan->batch_ch)});
     // range records of the shape tiles, shared by every two-slot channel launch
     int* tranges = nullptr;
     bool any_dual = false;
-    for (int c0 = 0; c0 < n_ch; c0 += plan->batch_ch) any_dual |= (std::min(n_ch, c0 + plan->batch_ch) - c0) % 2 == 0;
+    for (const auto& bt : batches) any_dual |= bt.first < n_tch && (bt.second - bt.first) % 2 == 0;
     if (two_slot_grid(plan) && use_rows && any_dual) {
         tranges = (int*)(plan->ws + plan->off_tranges);
         FusedArgs<T> fr = fa;
@@ -848,8 +889,9 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         nl += 1;
         if (tm) tm->end(KK_OTHER, st, (double)tile_range_bytes(n, plan->fty, plan->ftz) * tile_frac(1 << LPP_SHAPES));
     }
-    for (int c0 = 0; c0 < n_ch; c0 += plan->batch_ch) {
-        const int c1 = std::min(n_ch, c0 + plan->batch_ch);
+    for (const auto& bt : batches) {
+        const int c0 = bt.first, c1 = bt.second;
+        const bool dens = c0 >= n_tch;
         const int nch = c1 - c0;
         const int ngr = (nch + per_grid - 1) / per_grid;
         fa.n_slots = 0;
@@ -859,12 +901,30 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         for (int gi = 0; gi < ngr; ++gi) {
             const int ca0 = c0 + gi * per_grid;
             FusedSlot fs{};
-            fs.n_src = 1;
-            fs.src[0] = FusedSrc{LPP_SHAPES, coeff + (long long)plan->channels[ca0].coeff * stride, 0};
-            fs.vals_b = (!il && ca0 + 1 < c1) ? coeff + (long long)plan->channels[ca0 + 1].coeff * stride : nullptr;
-            if (!plan->fp64) {
-                fs.amax_a = rmax + 2 * plan->channels[ca0].coeff;
-                fs.amax_b = fs.vals_b ? rmax + 2 * plan->channels[ca0 + 1].coeff : nullptr;
+            if (dens) {
+                fs.n_src = 1;
+                fs.src[0] = FusedSrc{dens_cat, nullptr, 0};
+                if (has_rand) fs.src[fs.n_src++] = FusedSrc{LPP_RANDOMS, nullptr, 1};
+                const Channel& ca = plan->channels[ca0];
+                fs.use_ylm = 1;
+                fs.yl_a = ca.L;
+                fs.yn_a = ca.n;
+                fs.ynorm_a = ylm_norm(ca.L, ca.n);
+                fs.yl_b = -1;
+                if (!il && ca0 + 1 < c1) {
+                    const Channel& cbb = plan->channels[ca0 + 1];
+                    fs.yl_b = cbb.L;
+                    fs.yn_b = cbb.n;
+                    fs.ynorm_b = ylm_norm(cbb.L, cbb.n);
+                }
+            } else {
+                fs.n_src = 1;
+                fs.src[0] = FusedSrc{LPP_SHAPES, coeff + (long long)plan->channels[ca0].coeff * stride, 0};
+                fs.vals_b = (!il && ca0 + 1 < c1) ? coeff + (long long)plan->channels[ca0 + 1].coeff * stride : nullptr;
+                if (!plan->fp64) {
+                    fs.amax_a = rmax + 2 * plan->channels[ca0].coeff;
+                    fs.amax_b = fs.vals_b ? rmax + 2 * plan->channels[ca0 + 1].coeff : nullptr;
+                }
             }
             fs.grid = gi;
             fa.slots[fa.n_slots++] = fs;
@@ -880,22 +940,23 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
             cc.part = ch.part;
             cc.out_row = c0 + ci;
             cc.ynorm = ylm_norm_scaled(ch.L, ch.n);
-            if (ch.kind == KIND_CROSS) cb.has_d = 1; else cb.has_g = 1;
+            if (ch.kind == KIND_CROSS || ch.kind == KIND_DENS) cb.has_d = 1; else cb.has_g = 1;
         }
-        fa.trows = use_rows ? trows : nullptr;
-        fa.trow_count = use_rows ? tcount : nullptr;
-        fa.dual = (tranges && fa.n_slots % 2 == 0) ? 1 : 0;
+        const int bits = dens ? slot_bits(fa.slots[0]) : 1 << LPP_SHAPES;
+        fa.trows = use_rows ? (dens ? trows + 256 : trows) : nullptr;
+        fa.trow_count = use_rows ? (dens ? tcount + 1 : tcount) : nullptr;
+        fa.dual = (!dens && tranges && fa.n_slots % 2 == 0) ? 1 : 0;
         fa.tranges = fa.dual ? tranges : nullptr;
-        { lpp_status s0 = assign_fused(sh.count); if (s0 != LPP_OK) return s0; }
+        { lpp_status s0 = assign_fused(dens ? de.count + (has_rand ? ra.count : 0) : sh.count); if (s0 != LPP_OK) return s0; }
         fa.dual = 0;
         fa.tranges = nullptr;
         FftGeom gc = geom;
         gc.pmask = pmask;
         gc.q_max = plan->thr[nb];
-        for (int i = 0; i < ngr; ++i) gc.gmask[i] = 1 << LPP_SHAPES;
-        gc.yread_frac = (float)plane_frac(1 << LPP_SHAPES);
+        for (int i = 0; i < ngr; ++i) gc.gmask[i] = bits;
+        gc.yread_frac = (float)plane_frac(bits);
         gc.plive = plive;
-        gc.ylive_frac = (float)pencil_frac(1 << LPP_SHAPES);
+        gc.ylive_frac = (float)pencil_frac(bits);
         LPP_CUDA(fft_yz<T>(grids, ngr, n, tw, gc, false, st, tm));
         if (tm) tm->begin(KK_COMBINE, st);
         LPP_CUDA(launch_combine<T>(cb, plan->n_sm, st));
@@ -955,6 +1016,7 @@ static lpp_status finish(lpp_plan_t plan, const double* h_out, const double* h_s
     for (int s = 0; s < LPP_N_MOMENTS; ++s) {
         double C = 1.0, I = i_auto, shot = 0.0;
         if (s == LPP_MOM_DD0) { I = i_dd; shot = shot_dd; }
+        else if (s == LPP_MOM_DD2 || s == LPP_MOM_DD4) { C = 4.0 * kPi; I = i_dd; }
         else if (s >= LPP_MOM_CROSS2 && s <= LPP_MOM_CROSS6) { C = norm_factor(2, 2 * s); I = i_cross; }
         else if (s >= LPP_MOM_PLUS0 && s <= LPP_MOM_PLUS4) {
             const int l = 2 * (s - LPP_MOM_PLUS0);
@@ -1183,6 +1245,18 @@ extern "C" lpp_status lpp_window_Q(lpp_plan_t plan, int n_s, const double* s_edg
     plan->err.clear();
     return plan->fp64 ? run_window<double>(plan, n_s, s_edges, q, s_mean, n_points, norm)
                       : run_window<float>(plan, n_s, s_edges, q, s_mean, n_points, norm);
+}
+
+extern "C" lpp_status lpp_plan_path_stats(lpp_plan_t plan, long long* stats) {
+    if (!plan || !stats) return LPP_ERR_INVALID_ARG;
+    if (!plan->ws) return fail(plan, LPP_ERR_NOT_READY, "workspace not set");
+    int dev[4] = {0, 0, 0, 0};
+    LPP_CUDA(cudaMemcpyAsync(dev, plan->ws + plan->off_pstat, sizeof(dev), cudaMemcpyDeviceToHost, plan->stream));
+    LPP_CUDA(cudaStreamSynchronize(plan->stream));
+    stats[0] = plan->n_fused[0];
+    stats[1] = plan->n_fused[1];
+    for (int i = 0; i < 4; ++i) stats[2 + i] = dev[i];
+    return LPP_OK;
 }
 
 extern "C" const char* lpp_status_string(lpp_status s) {

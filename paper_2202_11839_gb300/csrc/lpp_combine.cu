@@ -226,8 +226,10 @@ __global__ void __launch_bounds__(1024) k_combine(CombineArgs<T> a) {
                     if (a.has_d) field_at<T>(g0 + slot * a.grid_stride, 0, 0, c, Dm, Dp);
                 }
                 if (a.has_d) {
-                    a.pD[c.im] = Dm;
-                    a.pD[c.ip] = Dp;
+                    if (a.pD) {   // null: the caller wants only the shell sums
+                        a.pD[c.im] = Dm;
+                        a.pD[c.ip] = Dp;
+                    }
                     dd = Dm.x * Dm.x + Dm.y * Dm.y;
                     if (!c.self) dd += Dp.x * Dp.x + Dp.y * Dp.y;
                 }
@@ -291,7 +293,7 @@ __global__ void __launch_bounds__(1024) k_combine(CombineArgs<T> a) {
                             // partner: delta(-k) = conj D; gamma*(-k) = conj G1 - i conj G2;
                             // gamma(-k) = conj G1 + i conj G2
                             c2<T> Pm, Pp;
-                            if (ch.kind == KIND_CROSS) {
+                            if (ch.kind == KIND_CROSS || ch.kind == KIND_DENS) {
                                 Pm = cconj<T>(Dm);
                                 Pp = cconj<T>(Dp);
                             } else {

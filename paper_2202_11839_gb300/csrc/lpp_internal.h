@@ -108,7 +108,7 @@ __host__ __device__ inline double ylm_norm_scaled(int L, int n) {
 }
 
 // ------------------------------------------------------------------ channel tables
-enum Kind { KIND_CROSS = 0, KIND_PLUS = 1, KIND_MINUS = 2 };
+enum Kind { KIND_CROSS = 0, KIND_PLUS = 1, KIND_MINUS = 2, KIND_DENS = 3 };
 enum Part { PART_RE = 0, PART_IM = 1 };
 
 // One real k-space field of the estimate: the projection of the real or imaginary

@@ -213,6 +213,8 @@ struct FusedArgs {
     const c2<T>* tw;
     const double* sums;
     double observer[3], origin[3], h;   // for the harmonic weights
+    int ylm_global;                      // 1: harmonic weights of the fixed direction los_global
+    double los_global[3];
     const int* pmask;                    // [3][n] planes reached per role, or null (write every pencil)
     const int* trows;                    // z-tile rows to visit (persistent grid), or null (all tiles)
     const int* trow_count;
@@ -221,6 +223,9 @@ struct FusedArgs {
     const int* tranges;                  // two-slot launches: per-tile range records, or null
     int* work;                           // one-slot launches over trows: item counter, zeroed
                                          // before the launch (dynamic schedule), or null
+    int* pstat;                          // optional tile counters: [0] two-slot fixed-point tiles,
+                                         // [1] two-slot float tiles, [2] one-slot fixed-point
+                                         // tiles, [3] one-slot float tiles (FP32 channel slots)
 };
 
 void fused_geometry(int n, size_t elem_bytes, int* ty, int* tz, int* ipt, int* threads, size_t* smem);
@@ -269,7 +274,8 @@ struct CombineArgs {
     int n_ch;
     int per_grid;          // channels per batch grid: 1 (interlaced) or 2 (two packed fields)
     CombineChan ch[kMaxBatchCh];
-    // partner spectra (full n^3 arrays, valid on kept modes)
+    // partner spectra (full n^3 arrays, valid on kept modes); in partner mode a null pD
+    // skips storing D (only its shell sums are wanted)
     c2<T>* pD;
     c2<T>* pG1;
     c2<T>* pG2;

@@ -312,14 +312,14 @@ __global__ void k_decode(const double* __restrict__ theta, int m, const float* _
     }
 }
 
-// training targets: derived curves u of native template slots [n][10][40] (FP64, unit
+// training targets: derived curves u of native template slots [n][LPP_N_MOMENTS][40] (FP64, unit
 // amplitude, no shot noise), y = (u - baseline) / sd
 __global__ void k_targets(const double* __restrict__ theta, const double* __restrict__ native, int n,
                           float* __restrict__ y, MapArgs a) {
     constexpr int nb = kNout / 8;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * kNout; i += gridDim.x * blockDim.x) {
         const int r = i / kNout, j = i % kNout, c = j / nb, b = j % nb;
-        const double* o = native + (size_t)r * 10 * nb;
+        const double* o = native + (size_t)r * LPP_N_MOMENTS * nb;
         double u;
         if (c < 2) {
             u = a.N[c][0] * o[1 * nb + b] + a.N[c][1] * o[2 * nb + b] + a.N[c][2] * o[3 * nb + b];

@@ -3,9 +3,11 @@
 // Some callers cannot call cudaMalloc: code that runs inside another framework's
 // memory pool or under a hard per-process memory cap, plug-ins that are handed a
 // stream but no allocator, and paths that must not grow the device footprint after
-// start-up.  lpp_density_monopole_static serves them: it runs the same kernels as
-// the P_dd^(0) slot of lpp_multipoles (assignment, 3D FFT, shell sums) but keeps
-// every intermediate in one file-scope device array of fixed size, so the library
+// start-up.  lpp_density_monopole_static serves them.  It computes the same quantity as
+// the P_dd^(0) slot of lpp_multipoles for a periodic box, by its own simpler path: an
+// unsorted scatter of the particles into one grid with global atomics (k_assign), a full
+// 3D FFT (fft3d, x pass included) and the partner-mode shell sums of the combine kernel.
+// Every intermediate lives in one file-scope device array of fixed size, so the library
 // itself never allocates device memory on this path.
 #include <math.h>
 #include <string.h>
@@ -33,7 +35,7 @@ constexpr int kMaxBins = 256;
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t sums, err, out, thr, tw, iw, ph, grid, partner, total;
+    size_t sums, err, out, thr, tw, iw, ph, grid, total;
 };
 
 Layout layout(int n, int nb, size_t es) {
@@ -49,17 +51,16 @@ Layout layout(int n, int nb, size_t es) {
     l.iw = take(n * es);
     l.ph = take(n * cs);
     l.grid = take(n3 * cs);
-    l.partner = take(n3 * cs);
     l.total = off;
     return l;
 }
 
-// Host tables live in fixed-size static buffers (no allocation); a pageable copy
-// has consumed its source by the time cudaMemcpyAsync returns.
-int h_thr[kMaxBins + 1];
-long long h_nmodes[kMaxBins];
-double h_out[2 * kMaxBins * 2];
-double h_tab[3 * 2 * kMaxN];
+// Host tables live in fixed-size per-thread buffers (no allocation; host threads never
+// share them); a pageable copy has consumed its source by the time cudaMemcpyAsync returns.
+thread_local int h_thr[kMaxBins + 1];
+thread_local long long h_nmodes[kMaxBins];
+thread_local double h_out[2 * kMaxBins * 2];
+thread_local double h_tab[3 * 2 * kMaxN];
 
 template <typename T>
 lpp_status run_static(char* base, const Layout& lay, int n, double box, const double origin[3], int scheme,
@@ -157,7 +158,7 @@ lpp_status run_static(char* base, const Layout& lay, int n, double box, const do
     cb.grid_stride = (long long)n3;
     cb.n = n;
     cb.interlace = interlace;
-    cb.pD = reinterpret_cast<c2<T>*>(base + lay.partner);
+    cb.pD = nullptr;   // only the shell sums of D are wanted
     cb.partner_mode = 1;
     cb.has_d = 1;
     cb.has_g = 0;

@@ -7,8 +7,10 @@
 // expanded in a discrete Fourier series in ln x and each term is transformed with the Mellin
 // transform of j_l,  int_0^inf x^(s-1) j_l(x) dx = 2^(s-2) sqrt(pi) G((l+s)/2) / G((3+l-s)/2).
 // One CTA evaluates one parameter set: the BBKS model and its sigma_8 normalisation, three
-// inverse transforms (L' = 0, 2, 4), then for each of the ten output slots the mixture with
-// the window multipoles, one forward transform and the shell averages.  Everything is FP64.
+// inverse transforms (L' = 0, 2, 4), then for each of the twelve output slots (the
+// estimator's order, with the density quadrupole and hexadecapole last: their templates are
+// the leakage of the monopole through Q_2 and Q_4, Sec. 4.3) the mixture with the window
+// multipoles, one forward transform and the shell averages.  Everything is FP64.
 //
 // Grid (shared with the tests): 2048 log-spaced k in [1e-4, 10], zero padding to 4096,
 // k_0 r_0 = exp(-(N-1) Delta), biases 1.5 (inverse) and 0.5 (forward), the input tapered by
@@ -30,7 +32,7 @@ constexpr int kNfft = 4096;
 constexpr int kLogN = 12;
 constexpr double kKmin = 1e-4, kKmax = 10.0, kQinv = 1.5, kQfwd = 0.5, kTaper = 0.1;
 constexpr double kPi = 3.14159265358979323846;
-constexpr int kSlots = 10;
+constexpr int kSlots = LPP_N_MOMENTS;
 constexpr int kMaxTerms = 3;   // model multipoles L' feeding one output slot
 
 struct SlotDesc {
@@ -45,7 +47,7 @@ struct SlotDesc {
 struct TemplateArgs {
     const double* params;   // [n][6]: A, b_g, sigma8, tilt, Gamma, shot-noise scale
     int n_templates;
-    double* out;            // [n][10][nb]
+    double* out;            // [n][LPP_N_MOMENTS][nb]
     const double* kin;      // [2048] k_n
     const double* s8w;      // [2048] sigma_8 quadrature weight w_n k^3 W^2(8k) / (2 pi^2)
     const double* ain;      // [2048] k^3 taper k^-q_inv
@@ -356,8 +358,8 @@ extern "C" lpp_status lpp_template_create(const double* q, const double* s, int 
             qr[li * kNfft + m] = v;
         }
     // output slots: kind, L and the model multipoles feeding them
-    const int kinds[kSlots] = {0, 1, 1, 1, 2, 2, 2, 3, 3, 3};
-    const int Ls[kSlots] = {0, 2, 4, 6, 0, 2, 4, 4, 6, 8};
+    const int kinds[kSlots] = {0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 0, 0};
+    const int Ls[kSlots] = {0, 2, 4, 6, 0, 2, 4, 4, 6, 8, 2, 4};
     const int mX[4] = {0, 2, 0, 4};
     int rows = 0;
     for (int sl = 0; sl < kSlots; ++sl) {

@@ -578,6 +578,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int slot, int 
             fscale = 1073741824.f / bound;
             finv = bound / 1073741824.f;
         }
+        if (a.pstat && tid == 0) atomicAdd(a.pstat + (fixed ? 2 : 3), 1);
     }
     int r = 0;
     for (int t = tid; t < total; t += S::THREADS) {
@@ -595,14 +596,22 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int slot, int 
         bool two = vb_ptr != nullptr && r_src[r] == 0;
         T vb = two ? vb_ptr[j] : (T)0;
         if (sl.use_ylm) {
-            // line of sight of the particle from its cell coordinates
-            const T px = (T)a.origin[0] + ux * (T)a.h - (T)a.observer[0];
-            const T py = (T)a.origin[1] + uy * (T)a.h - (T)a.observer[1];
-            const T pz = (T)a.origin[2] + uz * (T)a.h - (T)a.observer[2];
+            // line of sight of the particle from its cell coordinates (or the fixed direction)
+            T px, py, pz;
+            if (a.ylm_global) {
+                px = (T)a.los_global[0];
+                py = (T)a.los_global[1];
+                pz = (T)a.los_global[2];
+            } else {
+                px = (T)a.origin[0] + ux * (T)a.h - (T)a.observer[0];
+                py = (T)a.origin[1] + uy * (T)a.h - (T)a.observer[1];
+                pz = (T)a.origin[2] + uz * (T)a.h - (T)a.observer[2];
+            }
             const T inv = (T)1 / sqrt(px * px + py * py + pz * pz);
             va *= (T)sl.ynorm_a * ylm_poly<T>(sl.yl_a, sl.yn_a, px * inv, py * inv, pz * inv);
             if (sl.yl_b >= 0) {
-                vb = base * (T)sl.ynorm_b * ylm_poly<T>(sl.yl_b, sl.yn_b, px * inv, py * inv, pz * inv);
+                const T sb = src.neg_alpha ? base * -alpha : base;
+                vb = sb * (T)sl.ynorm_b * ylm_poly<T>(sl.yl_b, sl.yn_b, px * inv, py * inv, pz * inv);
                 two = true;
             }
         }
@@ -786,6 +795,7 @@ __device__ __forceinline__ void fused_tile2(const FusedArgs<T>& a, int tile_y, i
             fixed = false;
         }
     }
+    if (a.pstat && tid == 0) atomicAdd(a.pstat + (fixed ? 0 : 1), 1);
     const int P = a.scheme;
     const PencilCat& cat = a.cat[s0.src[0].cat];
     const T* su = static_cast<const T*>(cat.su);

@@ -23,12 +23,16 @@ LPP_FP32, LPP_FP64 = 0, 1
 LPP_LOS_LOCAL, LPP_LOS_GLOBAL = 0, 1
 LPP_SHAPES, LPP_DENSITY, LPP_RANDOMS = 0, 1, 2
 LPP_SHAPE_NONE, LPP_SHAPE_GAMMA12, LPP_SHAPE_TENSOR6 = 0, 1, 2
-LPP_N_MOMENTS = 10
+LPP_N_MOMENTS = 12
 LPP_MOM_DD0, LPP_MOM_CROSS2, LPP_MOM_CROSS4, LPP_MOM_CROSS6, LPP_MOM_PLUS0, LPP_MOM_PLUS2, LPP_MOM_PLUS4, \
-    LPP_MOM_MINUS4, LPP_MOM_MINUS6, LPP_MOM_MINUS8 = range(LPP_N_MOMENTS)
-MOMENT_NAMES = ["dd0", "cross2", "cross4", "cross6", "plus0", "plus2", "plus4", "minus4", "minus6", "minus8"]
+    LPP_MOM_MINUS4, LPP_MOM_MINUS6, LPP_MOM_MINUS8, LPP_MOM_DD2, LPP_MOM_DD4 = range(LPP_N_MOMENTS)
+MOMENT_NAMES = ["dd0", "cross2", "cross4", "cross6", "plus0", "plus2", "plus4", "minus4", "minus6", "minus8",
+                "dd2", "dd4"]
 LPP_WANT_ALL = 0x3FF
-LPP_WANT_CROSS_B = 1 << 10
+LPP_WANT_DD2 = 1 << LPP_MOM_DD2
+LPP_WANT_DD4 = 1 << LPP_MOM_DD4
+LPP_WANT_DENSITY = LPP_WANT_DD2 | LPP_WANT_DD4
+LPP_WANT_CROSS_B = 1 << 16
 KERNEL_KINDS = ["assign", "fft", "combine", "coeffs", "partner", "other"]
 
 
@@ -109,6 +113,7 @@ EXPORTS = {
                                 C.POINTER(C.c_double)]),
     "lpp_plan_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "lpp_plan_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
+    "lpp_plan_path_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
     "lpp_plan_kernel_stats": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                                         C.POINTER(C.c_double)]),
     "lpp_density_monopole_static": (C.c_int, [C.c_int, C.c_double, C.POINTER(C.c_double), C.c_int, C.c_int, C.c_int,
@@ -240,6 +245,14 @@ class Plan:
         _check(self.lib, self.lib.lpp_plan_launch_count(self.h, C.byref(v)), self.h)
         return v.value
 
+    def path_stats(self) -> dict:
+        """Forms of the fused assignment pass the last estimate ran (lpp_plan_path_stats)."""
+        v = (C.c_longlong * 6)()
+        _check(self.lib, self.lib.lpp_plan_path_stats(self.h, v), self.h)
+        keys = ("one_slot_launches", "two_slot_launches", "two_slot_fixed_tiles", "two_slot_float_tiles",
+                "one_slot_fixed_tiles", "one_slot_float_tiles")
+        return dict(zip(keys, list(v)))
+
     def kernel_stats(self) -> dict:
         out = {}
         for k, name in enumerate(KERNEL_KINDS):
@@ -346,7 +359,7 @@ class Template:
                                                              C.c_void_p(self.stream.cuda_stream)))
 
     def __call__(self, params, out=None):
-        """params: torch float64 CUDA tensor [n, 6]; returns a [n, 10, nb] float64 CUDA tensor."""
+        """params: torch float64 CUDA tensor [n, 6]; returns a [n, 12, nb] float64 CUDA tensor."""
         import torch
         n = int(params.shape[0])
         if out is None:
@@ -357,7 +370,7 @@ class Template:
         return out
 
     def derived(self, params, ref=None, sigma=None, out=None):
-        """Native slots [n, 10, nb] (float64) and standardised derived curves [n, 8 * nb] (float32)."""
+        """Native slots [n, 12, nb] (float64) and standardised derived curves [n, 8 * nb] (float32)."""
         import torch
         n = int(params.shape[0])
         if out is None:
@@ -518,7 +531,7 @@ class Surrogate:
 
 
 def derive_eb(p: np.ndarray):
-    """Legendre multipoles (gE l=0,2; EE, BB l=0,2,4) from normalised native moments (10, nb) complex."""
+    """Legendre multipoles (gE l=0,2; EE, BB l=0,2,4) from normalised native moments (>= 10, nb) complex."""
     lib = load_library()
     nb = p.shape[1]
     pr = np.ascontiguousarray(np.stack([p.real, p.imag], axis=-1), dtype=np.float64)

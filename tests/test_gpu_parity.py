@@ -93,7 +93,7 @@ def test_host_inputs_match_device_inputs(L):
     b = U.run_gpu(cfg, cat, L.LPP_FP32, device_inputs=False)
     ref = U.run_oracle(cfg, cat)
     sc = U.scale(ref)
-    assert np.max(np.abs(a.p - b.p) / np.where(sc > 0, sc, 1)) < 1e-6
+    assert np.max(np.abs(a.p - b.p)[:len(O.MOMENTS)] / np.where(sc > 0, sc, 1)) < 1e-6
 
 
 def test_repeat_runs_agree(L):
@@ -104,7 +104,7 @@ def test_repeat_runs_agree(L):
     a = U.run_gpu(cfg, cat, L.LPP_FP32)
     b = U.run_gpu(cfg, cat, L.LPP_FP32)
     sc = U.scale(ref)
-    assert np.max(np.abs(a.p - b.p) / np.where(sc > 0, sc, 1)) < 1e-6
+    assert np.max(np.abs(a.p - b.p)[:len(O.MOMENTS)] / np.where(sc > 0, sc, 1)) < 1e-6
 
 
 def test_particle_outside_box_is_an_error(L):

@@ -1,8 +1,9 @@
 """Moment-slot sharding of one estimate (paper_2202_11839_gb300/shard.py): the partition
 covers every requested slot once and balances the ranks, and two gloo ranks that each hold
 an estimate of their own slots end up with the whole estimate.  Each rank's estimate comes
-from the FP64 oracle on a small catalogue (its rows outside the rank's slots must not
-leak into the result)."""
+from the FP64 oracle on a small catalogue, the ten tensor-estimator slots and the density
+quadrupole and hexadecapole (its rows outside the rank's slots must not leak into the
+result)."""
 import os
 import socket
 import sys
@@ -21,44 +22,54 @@ def _sh():
     return L, SH
 
 
-@pytest.mark.parametrize("extra", [0, 1 << 10])
-@pytest.mark.parametrize("moments", [0x3FF, 0x3FE, (1 << 5) | (1 << 9), 1 << 4])
-def test_partition_covers_each_slot_once_and_balances(moments, extra):
+@pytest.mark.parametrize("with_b", [False, True])
+@pytest.mark.parametrize("moments", [0x3FF, 0xFFF, 0x3FE, (1 << 5) | (1 << 9) | (1 << 11), 1 << 4])
+def test_partition_covers_each_slot_once_and_balances(moments, with_b):
     L, SH = _sh()
+    extra = L.LPP_WANT_CROSS_B if with_b else 0
     want = moments | extra
-    cross_b = bool(extra)
-    weight = {s: SH.slot_channels(s, cross_b) + 1 for s in range(10)}
+    ns = L.LPP_N_MOMENTS
+    weight = {s: SH.slot_channels(s, with_b) + 1 for s in range(ns)}
     for world in range(1, 13):
         masks = SH.partition(want, world)
         assert len(masks) == world
-        slots = [s for m in masks for s in range(10) if m & (1 << s)]
-        assert sorted(slots) == [s for s in range(10) if moments & (1 << s)]
+        slots = [s for m in masks for s in range(ns) if m & (1 << s)]
+        assert sorted(slots) == [s for s in range(ns) if moments & (1 << s)]
         for m in masks:
             assert (m & L.LPP_WANT_CROSS_B) == (extra if m else 0)
-        loads = [sum(weight[s] for s in range(10) if m & (1 << s)) for m in masks]
+        loads = [sum(weight[s] for s in range(ns) if m & (1 << s)) for m in masks]
         assert max(loads) - min(loads) <= max(weight[s] for s in slots)
 
 
 def test_slot_channels_match_the_plan_tables():
     L, SH = _sh()
-    # 133 channels for the ten slots without the B-mode cross parts, 160 with
+    # 133 channels for the ten slots without the B-mode cross parts, 160 with; 5 + 9 more for
+    # the density quadrupole and hexadecapole
     assert sum(SH.slot_channels(s, False) for s in range(10)) == 133
     assert sum(SH.slot_channels(s, True) for s in range(10)) == 160
+    assert SH.slot_channels(L.LPP_MOM_DD2, True) == 5 and SH.slot_channels(L.LPP_MOM_DD4, False) == 9
 
 
 def _oracle_estimate():
+    """Oracle estimate with twelve slots: the tensor-estimator slots and the density l = 2, 4."""
     sys.path.insert(0, ROOT)
+    from oracle import lpp_oracle as O
     from tests import parity_util as U
     cfg = dict(n=16, box=300.0, observer=(150.0, 150.0, -800.0), scheme=3, interlace=True,
                k_edges=U.default_edges(16, 300.0))
     cat = U.make_case("shard", 16, count=1200, seed=7, n_rand=2500)
-    return U.run_oracle(cfg, cat)
+    ref = U.run_oracle(cfg, cat)
+    dens = U.run_oracle_density(cfg, cat)
+    ref.p = np.concatenate([ref.p, dens.p[1:]])
+    ref.raw = np.concatenate([ref.raw, dens.raw[1:]])
+    assert ref.p.shape[0] == 12 and O.MOMENTS[0] == ("dd", 0)
+    return ref
 
 
 def test_single_process_gather_is_the_identity():
     L, SH = _sh()
     ref = _oracle_estimate()
-    out = SH.gather(ref, L.LPP_WANT_ALL)
+    out = SH.gather(ref, L.LPP_WANT_ALL | L.LPP_WANT_DENSITY)
     np.testing.assert_array_equal(out.p, ref.p)
     np.testing.assert_array_equal(out.raw, ref.raw)
     np.testing.assert_array_equal(out.n_modes, ref.n_modes)
@@ -84,13 +95,13 @@ def _rank(rank, world, port, moments, q):
         # gather must drop)
         mine = L.Estimate(ref.p.copy(), ref.raw.copy(), ref.k_mean, ref.n_modes, ref.norm_auto, ref.norm_cross,
                           ref.norm_dd, ref.shot_plus, ref.shot_dd, ref.alpha)
-        for s in range(10):
+        for s in range(12):
             if not mask & (1 << s):
                 mine.p[s] = 1e30 * (rank + 1)
                 mine.raw[s] = -1e30
     out = SH.gather(mine, mask, dist, "cpu")
     want = ref.p.copy()
-    for s in range(10):
+    for s in range(12):
         if not moments & (1 << s):
             want[s] = 0
     q.put((rank, mask, np.array_equal(out.p, want), np.array_equal(out.n_modes, ref.n_modes),
@@ -99,12 +110,12 @@ def _rank(rank, world, port, moments, q):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("moments", [0x3FF, (1 << 5) | (1 << 9)])
+@pytest.mark.parametrize("moments", [0xFFF, (1 << 5) | (1 << 9)])
 def test_two_gloo_ranks_gather_the_whole_estimate(moments):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    world = 2 if moments == 0x3FF else 3        # the second case leaves one rank without a slot
+    world = 2 if moments == 0xFFF else 3        # the second case leaves one rank without a slot
     procs = [ctx.Process(target=_rank, args=(r, world, port, moments, q)) for r in range(world)]
     for p in procs:
         p.start()
