@@ -250,7 +250,7 @@ __device__ __forceinline__ void last_stage_warp(const c2<T>* tile, int c, int l,
 // each pass.  load(e): point e of the input; store(k, value): output k (consecutive lanes
 // store consecutive k).  t1[(k0 - 1) 64 + m] = w^(m k0) and t2[(k1 - 1) 8 + n0] = w^(R1 n0 k1)
 // (forward twiddles; conjugated for INV).
-template <typename T, int LOGN, bool INV, int LD, class Load, class Store>
+template <typename T, int LOGN, bool INV, int LD, bool ZERO = false, class Load, class Store>
 __device__ __forceinline__ void fft_pencil_warp(c2<T>* tile, int c, int lane, const c2<T>* t1, const c2<T>* t2,
                                                 Load&& load, Store&& store) {
     constexpr int N = 1 << LOGN, R1 = N / 64, Q = 8 * R1, B = R1 / 4;
@@ -307,6 +307,15 @@ __device__ __forceinline__ void fft_pencil_warp(c2<T>* tile, int c, int lane, co
         const int q = lane + 32 * b;
 #pragma unroll
         for (int n0 = 0; n0 < 8; ++n0) v[b][n0] = col[(Q * n0 + ((q + 2 * n0) & (Q - 1))) * LD];
+    }
+    if constexpr (ZERO) {
+        // every row of the column was read exactly once by this pass: leave the column zeroed
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int q = lane + 32 * b;
+#pragma unroll
+            for (int n0 = 0; n0 < 8; ++n0) col[(Q * n0 + ((q + 2 * n0) & (Q - 1))) * LD] = mk<T>((T)0, (T)0);
+        }
     }
 #pragma unroll
     for (int b = 0; b < B; ++b) {

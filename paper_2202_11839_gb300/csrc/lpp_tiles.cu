@@ -23,6 +23,14 @@
 
 namespace lpp {
 
+// 16-byte global -> shared copy that does not hold registers while in flight (cp.async;
+// both addresses 16-byte aligned), and the wait for this thread's copies.
+__device__ __forceinline__ void copy16_async(void* smem_dst, const void* gmem_src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_pencil_count(const T* __restrict__ pos, long long count, int n, T ih,
                                                       T ox, T oy, T oz, int* __restrict__ key,
@@ -440,9 +448,10 @@ __device__ __forceinline__ void tile_setup(const FusedArgs<T>& a, const FusedSlo
 // out + (lz n + ly) n).  A fixed-point tile is converted back to floating point (value =
 // integer x unit) inside the first FFT stage.  t: the thread's index among the S::THREADS
 // that transform this tile; fixed is CTA-uniform.
-template <typename T, int LOGN>
+template <typename T, int LOGN, bool ZERO = false>
 __device__ __forceinline__ void x_transform(c2<T>* tile, int t, const c2<T>* tw, const c2<T>* twr, bool fixed,
                                             float unit, c2<T>* out, int nk_pos, int nk_neg) {
+    static_assert(!ZERO || FusedShape<T, LOGN>::WARP_FFT, "zeroing needs the warp-per-pencil transform");
     using S = FusedShape<T, LOGN>;
     constexpr int N = S::N, W = S::W, LD = S::LD, IPT = S::IPT, TY = S::TY, R0 = LeadRadix<LOGN>::R;
     if constexpr (S::WARP_FFT) {
@@ -456,7 +465,7 @@ __device__ __forceinline__ void x_transform(c2<T>* tile, int t, const c2<T>* tw,
         if constexpr (sizeof(T) == 4) {
             if (fixed) {
                 const int2* ti = reinterpret_cast<const int2*>(tile) + pc;
-                fft_pencil_warp<T, LOGN, false, LD>(tile, pc, lane, twr, twr + T1, [&](int e) {
+                fft_pencil_warp<T, LOGN, false, LD, ZERO>(tile, pc, lane, twr, twr + T1, [&](int e) {
                     const int2 q = ti[e * LD];
                     return mk<T>((T)((float)q.x * unit), (T)((float)q.y * unit));
                 }, store);
@@ -464,8 +473,8 @@ __device__ __forceinline__ void x_transform(c2<T>* tile, int t, const c2<T>* tw,
             }
         }
         const c2<T>* col = tile + pc;
-        fft_pencil_warp<T, LOGN, false, LD>(tile, pc, lane, twr, twr + T1, [&](int e) { return col[e * LD]; },
-                                            store);
+        fft_pencil_warp<T, LOGN, false, LD, ZERO>(tile, pc, lane, twr, twr + T1, [&](int e) { return col[e * LD]; },
+                                                  store);
     } else {
         const int c = t & (W - 1), u = t >> ilog2(W);
         bool converted = false;
@@ -615,14 +624,25 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int slot, int 
                 two = true;
             }
         }
-        if (fixed) {
+        if (a.interlace) {
+            // both sub-grids; odd lanes take the shifted one (the imaginary words) first, so that
+            // each atomic instruction spreads over the even and the odd banks
+            const int odd = tid & 1;
+            const T sh0 = odd ? (T)0.5 : (T)0, sh1 = odd ? (T)0 : (T)0.5;
+            if (fixed) {
+                va *= fscale;
+                scatter_one<T, true>(tilef, LD, N, P, ux, uy, uz, sh0, y0, z0, TY, TZ, va, (T)0, false, odd);
+                scatter_one<T, true>(tilef, LD, N, P, ux, uy, uz, sh1, y0, z0, TY, TZ, va, (T)0, false, 1 - odd);
+            } else {
+                scatter_one<T, false>(tilef, LD, N, P, ux, uy, uz, sh0, y0, z0, TY, TZ, va, (T)0, false, odd);
+                scatter_one<T, false>(tilef, LD, N, P, ux, uy, uz, sh1, y0, z0, TY, TZ, va, (T)0, false, 1 - odd);
+            }
+        } else if (fixed) {
             va *= fscale;
             vb *= fscale;
             scatter_one<T, true>(tilef, LD, N, P, ux, uy, uz, (T)0, y0, z0, TY, TZ, va, vb, two, 0);
-            if (a.interlace) scatter_one<T, true>(tilef, LD, N, P, ux, uy, uz, (T)0.5, y0, z0, TY, TZ, va, (T)0, false, 1);
         } else {
             scatter_one<T, false>(tilef, LD, N, P, ux, uy, uz, (T)0, y0, z0, TY, TZ, va, vb, two, 0);
-            if (a.interlace) scatter_one<T, false>(tilef, LD, N, P, ux, uy, uz, (T)0.5, y0, z0, TY, TZ, va, (T)0, false, 1);
         }
     }
     __syncthreads();
@@ -697,6 +717,7 @@ void fused_geometry(int n, size_t elem_bytes, int* ty, int* tz, int* ipt, int* t
     *threads = t1 / *ipt;
     const bool warp_out = n / 8 == 32 * *ipt && *threads == 32 * w;
     const bool warp_fft = warp_out && (n == 256 || n == 512);
+    // PencilWarpTw<LOGN>::SIZE: two-pass tables at n = 512, three-pass at n = 256
     const int twr = warp_fft ? (n / 64 - 1) * 64 + 56 : (warp_out ? 7 * (n / 8) : 0);
     *smem = (size_t)(n + n * (w + 1) + twr) * 2 * elem_bytes;
 }
@@ -732,8 +753,12 @@ __device__ __forceinline__ void load_twiddles(const FusedArgs<T>& a, c2<T>* tw, 
 // rows of the same catalogue) in one CTA of 2 x THREADS threads: one set-up, every particle
 // visit computes its stencils once for both tiles; the halves of the CTA transform and store
 // one tile each.  The tiles use fixed point only when both slots' units pass the guard.
+// With range records (rec) the tiles arrive zeroed: the kernel clears them once and every x
+// transform leaves its column zeroed; bnd[2 q], bnd[2 q + 1] are slot q's coefficient bounds
+// (max |c|, rms c), in shared memory.
 template <typename T, int LOGN>
-__device__ __forceinline__ void fused_tile2(const FusedArgs<T>& a, int tile_y, int tile_z, const int* rec) {
+__device__ __forceinline__ void fused_tile2(const FusedArgs<T>& a, int tile_y, int tile_z, const int* rec,
+                                            const float* bnd) {
     using S = FusedShape<T, LOGN>;
     constexpr int N = S::N, TY = S::TY, TZ = S::TZ, W = S::W, LD = S::LD;
     constexpr int NT = 2 * S::THREADS;
@@ -750,13 +775,11 @@ __device__ __forceinline__ void fused_tile2(const FusedArgs<T>& a, int tile_y, i
     const int y0 = tile_y * TY, z0 = tile_z * TZ;
     const FusedSlot& s0 = a.slots[2 * blockIdx.y];
     const FusedSlot& s1 = a.slots[2 * blockIdx.y + 1];
-    if (rec) {
-        tile_clear<T, LOGN, NT>(tile0, 2 * N * LD);
-    } else {
+    if (!rec) {
         tile_setup<T, LOGN, NT>(a, s0, y0, z0, tw, twr, tile0, 2 * N * LD, r_begin_s, r_pref_s, r_src_s,
                                 n_ranges_s, rcount, wmax_s);
+        __syncthreads();
     }
-    __syncthreads();
     const int* r_begin = rec ? rec + kRecBegin : r_begin_s;
     const int* r_pref = rec ? rec + kRecPref : r_pref_s;
     const int nr = rec ? rec[0] : n_ranges_s;
@@ -784,11 +807,9 @@ __device__ __forceinline__ void fused_tile2(const FusedArgs<T>& a, int tile_y, i
     bool fixed = sizeof(T) == 4;
     float fs[2] = {1.f, 1.f}, fi[2] = {1.f, 1.f};
     for (int q = 0; q < 2 && fixed; ++q) {
-        const FusedSlot& sq = q ? s1 : s0;
-        const float am = sq.amax_a[0], rms = sq.amax_a[1];
-        const float bound = (float)wmax * am;
+        const float bound = (float)wmax * bnd[2 * q];
         if (bound == 0.f) continue;
-        if (bound * (1.f / 1073741824.f) <= rms * (1.f / 65536.f)) {
+        if (bound * (1.f / 1073741824.f) <= bnd[2 * q + 1] * (1.f / 65536.f)) {
             fs[q] = 1073741824.f / bound;
             fi[q] = bound / 1073741824.f;
         } else {
@@ -804,6 +825,10 @@ __device__ __forceinline__ void fused_tile2(const FusedArgs<T>& a, int tile_y, i
     const long long cap = cat.cap;
     T* t0 = reinterpret_cast<T*>(tile0);
     T* t1 = reinterpret_cast<T*>(tile1);
+    // odd lanes scatter the shifted sub-grid (the imaginary words) first: every atomic
+    // instruction then spreads over the even and the odd banks
+    const int odd = tid & 1;
+    const T sh0 = odd ? (T)0.5 : (T)0, sh1 = odd ? (T)0 : (T)0.5;
     int r = 0;
     for (int t = tid; t < total; t += NT) {
         while (r + 1 < nr && r_pref[r + 1] <= t) ++r;
@@ -813,15 +838,21 @@ __device__ __forceinline__ void fused_tile2(const FusedArgs<T>& a, int tile_y, i
         if (fixed) {
             v0 *= fs[0];
             v1 *= fs[1];
-            scatter_two<T, true>(t0, t1, LD, N, P, ux, uy, uz, (T)0, y0, z0, TY, TZ, v0, v1, 0);
-            scatter_two<T, true>(t0, t1, LD, N, P, ux, uy, uz, (T)0.5, y0, z0, TY, TZ, v0, v1, 1);
+            scatter_two<T, true>(t0, t1, LD, N, P, ux, uy, uz, sh0, y0, z0, TY, TZ, v0, v1, odd);
+            scatter_two<T, true>(t0, t1, LD, N, P, ux, uy, uz, sh1, y0, z0, TY, TZ, v0, v1, 1 - odd);
         } else {
-            scatter_two<T, false>(t0, t1, LD, N, P, ux, uy, uz, (T)0, y0, z0, TY, TZ, v0, v1, 0);
-            scatter_two<T, false>(t0, t1, LD, N, P, ux, uy, uz, (T)0.5, y0, z0, TY, TZ, v0, v1, 1);
+            scatter_two<T, false>(t0, t1, LD, N, P, ux, uy, uz, sh0, y0, z0, TY, TZ, v0, v1, odd);
+            scatter_two<T, false>(t0, t1, LD, N, P, ux, uy, uz, sh1, y0, z0, TY, TZ, v0, v1, 1 - odd);
         }
     }
     __syncthreads();
     c2<T>* tile = half ? tile1 : tile0;
+    if constexpr (S::WARP_FFT) {
+        if (rec) {
+            x_transform<T, LOGN, true>(tile, th, tw, twr, fixed, fi[half], out, a.nk_pos, a.nk_neg);
+            return;
+        }
+    }
     x_transform<T, LOGN>(tile, th, tw, twr, fixed, fi[half], out, a.nk_pos, a.nk_neg);
 }
 
@@ -833,39 +864,38 @@ __global__ void __launch_bounds__(2 * FusedShape<T, LOGN>::THREADS, 1) k_assign_
     static_assert(S::MAXR <= kRecPref - kRecBegin && S::MAXR + 1 <= kRecSrc - kRecPref && S::MAXR <= kRec - kRecSrc,
                   "range record layout");
     constexpr int NTY = S::N / S::TY;
-    __shared__ int recs[2][kRec];
+    __shared__ __align__(16) int recs[2][kRec];
+    // the slots' coefficient bounds (max |c|, rms) for the fixed-point units, once per CTA
+    __shared__ float bnd[4];
     const int total = *a.trow_count * NTY;
     const int tid = threadIdx.x;
+    if (tid < 4) bnd[tid] = sizeof(T) == 4 ? a.slots[2 * blockIdx.y + (tid >> 1)].amax_a[tid & 1] : 0.f;
     if (a.tranges == nullptr) {
+        __syncthreads();
         for (int t = blockIdx.x; t < total; t += gridDim.x) {
-            fused_tile2<T, LOGN>(a, t % NTY, a.trows[t / NTY], nullptr);
+            fused_tile2<T, LOGN>(a, t % NTY, a.trows[t / NTY], nullptr, bnd);
             __syncthreads();
         }
         return;
     }
-    if (tid < 32 && (int)blockIdx.x < total) {
-#pragma unroll
-        for (int k = 0; k < kRec / 32; ++k) recs[0][tid + 32 * k] = a.tranges[(size_t)blockIdx.x * kRec + tid + 32 * k];
-    }
+    static_assert(kRec % 4 == 0 && kRec / 4 <= 32, "a record is copied by one warp in 16-byte pieces");
+    if (tid < kRec / 4 && (int)blockIdx.x < total) copy16_async(&recs[0][4 * tid], a.tranges + (size_t)blockIdx.x * kRec + 4 * tid);
+    cp_async_wait_all();
     {
         extern __shared__ __align__(16) unsigned char smem_raw[];
         c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
         load_twiddles<T, LOGN, 2 * S::THREADS>(a, tw, tw + S::N + 2 * S::N * S::LD);
+        // both tiles start zeroed; afterwards each x transform leaves its columns zeroed
+        tile_clear<T, LOGN, 2 * S::THREADS>(tw + S::N, 2 * S::N * S::LD);
     }
     __syncthreads();
     int buf = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int tn = t + gridDim.x;
-        int pre[kRec / 32];
-        if (tid < 32 && tn < total) {
-#pragma unroll
-            for (int k = 0; k < kRec / 32; ++k) pre[k] = a.tranges[(size_t)tn * kRec + tid + 32 * k];
-        }
-        fused_tile2<T, LOGN>(a, t % NTY, a.trows[t / NTY], recs[buf]);
-        if (tid < 32 && tn < total) {
-#pragma unroll
-            for (int k = 0; k < kRec / 32; ++k) recs[buf ^ 1][tid + 32 * k] = pre[k];
-        }
+        // the next tile's record streams into the other buffer while this tile is worked on
+        if (tid < kRec / 4 && tn < total) copy16_async(&recs[buf ^ 1][4 * tid], a.tranges + (size_t)tn * kRec + 4 * tid);
+        fused_tile2<T, LOGN>(a, t % NTY, a.trows[t / NTY], recs[buf], bnd);
+        cp_async_wait_all();
         __syncthreads();
         buf ^= 1;
     }
