@@ -42,6 +42,7 @@ struct lpp_plan_s {
     int nk_pos = 0, nk_neg = 0, nky = 0, nzi = 0;
     FftGeom geom;
     std::vector<int> thr;
+    std::vector<int4> items;        // work list of the combine (combine_items)
     std::vector<long long> n_modes;
     std::vector<double> k_mean;
     // channels
@@ -75,6 +76,7 @@ struct lpp_plan_s {
     size_t off_tranges = 0;              // per-tile range records of the two-slot fused passes
     size_t off_work = 0;                 // item counter of the dynamically scheduled fused passes
     size_t off_pstat = 0;                // [4] tile counters of the fused passes (FusedArgs::pstat)
+    size_t off_items = 0;                // the combine's work list
     int fty = 4, ftz = 4;
     int n_partner = 0;
     int out_rows = 0;
@@ -209,6 +211,7 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
         }
     plan->k_mean.assign(nb, 0.0);
     for (int b = 0; b < nb; ++b) plan->k_mean[b] = plan->n_modes[b] ? ksum[b] / plan->n_modes[b] : 0.0;
+    combine_items(n, plan->nk_pos, plan->nk_neg, plan->nky, plan->nzi, tmax, plan->items);
 
     // kernel polynomials and quadratures
     build_kernel_polys(plan->kp);
@@ -332,6 +335,7 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
     plan->off_tranges = take(two_slot_grid(plan) ? tile_range_bytes(n, plan->fty, plan->ftz) : sizeof(int));
     plan->off_work = take(sizeof(int));
     plan->off_pstat = take(4 * sizeof(int));
+    plan->off_items = take(std::max<size_t>(1, plan->items.size()) * sizeof(int4));
     plan->off_wout = take((size_t)kWindowChannels * 256 * 2 * sizeof(double));
     plan->off_wthr = take(257 * sizeof(int));
     plan->off_partner = take((size_t)std::max(1, plan->n_partner) * n3 * cs);
@@ -378,6 +382,7 @@ static lpp_status write_tables(lpp_plan_t plan) {
         return cudaMemcpyAsync(plan->ws + off, src, bytes, cudaMemcpyHostToDevice, plan->stream);
     };
     LPP_CUDA(put(plan->off_thr, plan->thr.data(), plan->thr.size() * sizeof(int)));
+    if (!plan->items.empty()) LPP_CUDA(put(plan->off_items, plan->items.data(), plan->items.size() * sizeof(int4)));
     // twiddles e^{-2 pi i j / n}
     std::vector<T> tw(2 * n), iw(n), ph(2 * n);
     for (int j = 0; j < n; ++j) {
@@ -723,6 +728,8 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
     cb.nky = plan->nky;
     cb.nzi = plan->nzi;
     cb.out = out;
+    cb.items = plan->items.empty() ? nullptr : (const int4*)(plan->ws + plan->off_items);
+    cb.n_items = (int)plan->items.size();
     const int n_ch = (int)plan->channels.size();
     cb.row_dd0 = n_ch;
     cb.row_plus0 = n_ch + 1;

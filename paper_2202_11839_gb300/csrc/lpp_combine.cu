@@ -119,8 +119,10 @@ __device__ __forceinline__ T ylm_channel(int L, int n, T x, T y, T z) {
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(1024) k_combine(CombineArgs<T> a) {
+// COMPACT: walk the work list (a.items, 256 threads, three CTAs per SM); otherwise one pass
+// per whole row (up to 1024 threads)
+template <typename T, bool COMPACT>
+__global__ void __launch_bounds__(COMPACT ? 256 : 1024, COMPACT ? 3 : 1) k_combine(CombineArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = a.n;
     const int nb = a.nb;
@@ -140,16 +142,6 @@ __global__ void __launch_bounds__(1024) k_combine(CombineArgs<T> a) {
     for (int i = tid; i <= nb; i += nthr) thr[i] = a.thr[i];
     __syncthreads();
 
-    const int P = nthr / 2;
-    const int fx = tid < P ? tid : -1 - (tid - P);
-    const bool xvalid = tid < P ? (fx <= a.nk_pos) : (-fx <= a.nk_neg);
-    const int x = fx >= 0 ? fx : n + fx;
-    const int xp = (n - x) & (n - 1);
-    const int fxp = freq_of<T>(xp, n);
-    const long long n2l = (long long)n * n;
-    const int rows = a.nzi * a.nky;
-
-    int nrow = 0;
     auto fold = [&]() {
         __syncthreads();
         for (int i = tid; i < E; i += nthr) {
@@ -161,18 +153,19 @@ __global__ void __launch_bounds__(1024) k_combine(CombineArgs<T> a) {
         }
         __syncthreads();
     };
-    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
-        const int zi = row / a.nky;
-        const int yj = row - zi * a.nky;
-        const int z = zi <= a.nk_pos ? zi : n / 2;
-        const int y = yj <= a.nk_pos ? yj : n - (a.nky - yj);
+    // The work of one mode pair (m, -m) with m = (fx, y, z) (grid indices y, z); xvalid: the
+    // lane has a mode; half: 0 for fx >= 0, 1 for fx < 0 (shell labels are monotone within a
+    // half, so (half, bin) keys the lane's segment in the warp-segmented sums).  Every lane of
+    // the warp calls it (the shell sums are warp-collective).
+    auto mode_work = [&](bool xvalid, int fx, int z, int y, int half) {
+        // shell label (contiguous along the warp) and whether this lane owns the pair
+        const int x = fx >= 0 ? fx : n + fx;
+        const int xp = (n - x) & (n - 1);
+        const int fxp = freq_of<T>(xp, n);
         const int zp = (n - z) & (n - 1);
         const int yp = (n - y) & (n - 1);
         const int fz = freq_of<T>(z, n), fy = freq_of<T>(y, n);
         const int fzp = freq_of<T>(zp, n), fyp = freq_of<T>(yp, n);
-        if (fy * fy + fz * fz >= thr[nb]) continue;   // no mode of this row lies in a shell (CTA-uniform)
-
-        // shell label (contiguous along the warp) and whether this lane owns the pair
         const int q2 = fx * fx + fy * fy + fz * fz;
         int bin = -1;
         if (xvalid && q2 > 0 && q2 >= thr[0] && q2 < thr[nb]) {
@@ -247,8 +240,9 @@ __global__ void __launch_bounds__(1024) k_combine(CombineArgs<T> a) {
                     }
                 }
             }
-            warp_bin_add<T>(dd, (T)0, bin, acc);
-            warp_bin_add<T>(gg, (T)0, bin, acc + 2 * nb);
+            const int key = bin >= 0 ? bin + half * 65536 : -1;
+            warp_bin_add<T>(dd, (T)0, bin, acc, key);
+            warp_bin_add<T>(gg, (T)0, bin, acc + 2 * nb, key);
         } else {
             c2<T> Dm = mk<T>(0, 0), Dp = Dm, G1m = Dm, G1p = Dm, G2m = Dm, G2p = Dm;
             if (own_pair) {
@@ -261,7 +255,7 @@ __global__ void __launch_bounds__(1024) k_combine(CombineArgs<T> a) {
             // a warp none of whose lanes owns a mode pair (rows near the last shell) has
             // nothing to add: it skips the channels (warp-uniform)
             const bool warp_live = __any_sync(0xffffffffu, own_pair);
-            const SegMask segm = seg_mask(bin);
+            const SegMask segm = seg_mask(bin >= 0 ? bin + half * 65536 : -1);
             const int n_slots = warp_live ? (a.n_ch + a.per_grid - 1) / a.per_grid : 0;
             // four slots at a time: their packed values at m and -m are loaded together
             for (int s0 = 0; s0 < n_slots; s0 += 4) {
@@ -319,11 +313,52 @@ __global__ void __launch_bounds__(1024) k_combine(CombineArgs<T> a) {
                 }
             }
         }
-        // fold the partials into the compensated accumulators every second row (a row pair
-        // adds at most 2 x 16 warp segments per shell to an FP32 partial)
-        if ((++nrow & 1) == 0) fold();
+    };
+
+    if constexpr (!COMPACT) {
+        // one pass per row (fz, fy) of the kept cube; lanes cover fx >= 0 (first half) and
+        // fx < 0 (second half)
+        const int P = nthr / 2;
+        const int fx = tid < P ? tid : -1 - (tid - P);
+        const bool xvalid = tid < P ? (fx <= a.nk_pos) : (-fx <= a.nk_neg);
+        const int rows = a.nzi * a.nky;
+        int nrow = 0;
+        for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+            const int zi = row / a.nky;
+            const int yj = row - zi * a.nky;
+            const int z = zi <= a.nk_pos ? zi : n / 2;
+            const int y = yj <= a.nk_pos ? yj : n - (a.nky - yj);
+            const int fz = freq_of<T>(z, n), fy = freq_of<T>(y, n);
+            if (fy * fy + fz * fz >= thr[nb]) continue;   // no mode of this row lies in a shell (CTA-uniform)
+            mode_work(xvalid, fx, z, y, tid < P ? 0 : 1);
+            // fold the partials into the compensated accumulators every second row (a row pair
+            // adds at most 2 x 16 warp segments per shell to an FP32 partial)
+            if ((++nrow & 1) == 0) fold();
+        }
+        if (nrow & 1) fold();
+    } else {
+        // the work list: each warp takes one item (32 consecutive modes of a row inside the
+        // last shell) per round; the partials are folded after every round
+        const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+        for (int base = blockIdx.x * nw; base < a.n_items; base += gridDim.x * nw) {
+            const int it = base + warp;
+            bool xvalid = false;
+            int fx = 0, z = 0, y = 0, half = 0;
+            if (it < a.n_items) {
+                const int4 item = a.items[it];
+                const int zi = item.x / a.nky;
+                const int yj = item.x - zi * a.nky;
+                z = zi <= a.nk_pos ? zi : n / 2;
+                y = yj <= a.nk_pos ? yj : n - (a.nky - yj);
+                const int t = item.y + lane;
+                xvalid = t <= item.z + item.w;
+                half = t > item.z ? 1 : 0;
+                fx = half ? -(t - item.z) : t;
+            }
+            mode_work(xvalid, fx, z, y, half);
+            fold();
+        }
     }
-    if (nrow & 1) fold();
     for (int i = tid; i < E; i += nthr) {
         const double v = Owned<T>::value(own + i, own + E + i);
         if (v != 0.0) {
@@ -337,18 +372,49 @@ __global__ void __launch_bounds__(1024) k_combine(CombineArgs<T> a) {
 
 template <typename T>
 cudaError_t launch_combine(const CombineArgs<T>& a, int n_sm, cudaStream_t st) {
-    const int P = ((a.nk_pos + 1) + 31) / 32 * 32;
-    const int threads = 2 * P;
     const int nacc = a.partner_mode ? 2 : a.n_ch;
     const int E = nacc * a.nb * 2;
     size_t smem = (size_t)E * sizeof(T) * (1 + Owned<T>::words) + (size_t)(a.n + (a.n & 1)) * sizeof(T) +
                   (size_t)a.n * sizeof(c2<T>) + (size_t)(a.nb + 1) * sizeof(int);
-    cudaFuncSetAttribute(k_combine<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (a.items != nullptr) {
+        // 8 warps per CTA, three CTAs per SM
+        cudaFuncSetAttribute(k_combine<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int threads = 256;
+        int blocks = n_sm * 3;
+        const int rounds = (a.n_items + 7) / 8;
+        if (blocks > rounds) blocks = rounds > 0 ? rounds : 1;
+        k_combine<T, true><<<blocks, threads, smem, st>>>(a);
+        return cudaGetLastError();
+    }
+    cudaFuncSetAttribute(k_combine<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int P = ((a.nk_pos + 1) + 31) / 32 * 32;
+    const int threads = 2 * P;
     const int rows = a.nzi * a.nky;
     int blocks = n_sm * (threads <= 256 ? 8 : (threads <= 512 ? 4 : 2));
     if (blocks > rows) blocks = rows;
-    k_combine<T><<<blocks, threads, smem, st>>>(a);
+    k_combine<T, false><<<blocks, threads, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+void combine_items(int n, int nk_pos, int nk_neg, int nky, int nzi, int q_max, std::vector<int4>& items) {
+    items.clear();
+    for (int zi = 0; zi < nzi; ++zi) {
+        const int z = zi <= nk_pos ? zi : n / 2;
+        const int fz = z < n / 2 ? z : z - n;
+        for (int yj = 0; yj < nky; ++yj) {
+            const int y = yj <= nk_pos ? yj : n - (nky - yj);
+            const int fy = y < n / 2 ? y : y - n;
+            const long long rem = (long long)q_max - (long long)fy * fy - (long long)fz * fz;
+            if (rem <= 0) continue;
+            // |fx| <= xr with fx^2 < rem
+            int xr = 0;
+            while ((long long)(xr + 1) * (xr + 1) < rem) ++xr;
+            const int xp = xr < nk_pos ? xr : nk_pos;
+            const int xn = xr < nk_neg ? xr : nk_neg;
+            const int m = xp + 1 + xn;
+            for (int t0 = 0; t0 < m; t0 += 32) items.push_back(make_int4(zi * nky + yj, t0, xp, xn));
+        }
+    }
 }
 
 template cudaError_t launch_combine<float>(const CombineArgs<float>&, int, cudaStream_t);

@@ -288,10 +288,18 @@ struct CombineArgs {
     int nb;
     int nk_pos, nk_neg, nky, nzi;
     double* out;           // [rows][nb][2]
+    // optional work list (combine_items): item = {row, first mode, x extent >= 0, x extent < 0}
+    // of the modes inside the last shell, 32 at a time; null: one CTA pass per whole row
+    const int4* items;
+    int n_items;
 };
 
 template <typename T>
 cudaError_t launch_combine(const CombineArgs<T>& a, int n_sm, cudaStream_t st);
+// The work list of the combine for a plan's kept cube: row r = zi * nky + yj (the combine's
+// row enumeration) holds the modes fx = 0 .. xp and -1 .. -xn with fx^2 + fy^2 + fz^2 < q_max;
+// they are split into items of 32 consecutive modes (fx = 0 .. xp first, then -1 .. -xn).
+void combine_items(int n, int nk_pos, int nk_neg, int nky, int nzi, int q_max, std::vector<int4>& items);
 
 // ------------------------------------------------------------------ window multipoles
 // pD[m] = Z[m] / W(m) over every mode of grid 0 (the window field alone in the real part)

@@ -29,28 +29,33 @@ template <> struct Owned<double> {
 template <typename T>
 __device__ __forceinline__ int freq_of(int i, int n) { return i < n / 2 ? i : i - n; }
 
-// segmented inclusive scan of (re, im) over lanes with equal, monotone shell labels;
-// the last lane of each run adds the run total to acc[bin][2].
+// segmented inclusive scan of (re, im) over lanes with equal segment keys, the keys monotone
+// along the warp (equal keys form one contiguous run); the last lane of each run adds the run
+// total to acc[bin][2].  key = bin when the shell labels themselves are monotone.
 template <typename T>
-__device__ __forceinline__ void warp_bin_add(T re, T im, int bin, T* acc) {
+__device__ __forceinline__ void warp_bin_add(T re, T im, int bin, T* acc, int key) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const int ob = __shfl_up_sync(full, bin, d);
+        const int ok = __shfl_up_sync(full, key, d);
         const T ore = __shfl_up_sync(full, re, d);
         const T oim = __shfl_up_sync(full, im, d);
-        if (lane >= d && ob == bin) {
+        if (lane >= d && ok == key) {
             re += ore;
             im += oim;
         }
     }
-    const int nb = __shfl_down_sync(full, bin, 1);
-    const bool last = (lane == 31) || (nb != bin);
+    const int nk = __shfl_down_sync(full, key, 1);
+    const bool last = (lane == 31) || (nk != key);
     if (last && bin >= 0) {
         atomicAdd(acc + 2 * bin, re);
         atomicAdd(acc + 2 * bin + 1, im);
     }
+}
+template <typename T>
+__device__ __forceinline__ void warp_bin_add(T re, T im, int bin, T* acc) {
+    warp_bin_add<T>(re, im, bin, acc, bin);
 }
 
 // The shell labels of a row are the same for every channel: the steps of the segmented scan
@@ -61,18 +66,19 @@ struct SegMask {
     bool last;      // the lane holds its segment's sum after the scan
 };
 
-__device__ __forceinline__ SegMask seg_mask(int bin) {
+// key: the lane's segment (equal keys contiguous along the warp), e.g. its shell label
+__device__ __forceinline__ SegMask seg_mask(int key) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     SegMask m;
     m.add = 0u;
 #pragma unroll
     for (int s = 0, d = 1; d < 32; d <<= 1, ++s) {
-        const int ob = __shfl_up_sync(full, bin, d);
-        if (lane >= d && ob == bin) m.add |= 1u << s;
+        const int ok = __shfl_up_sync(full, key, d);
+        if (lane >= d && ok == key) m.add |= 1u << s;
     }
-    const int nb = __shfl_down_sync(full, bin, 1);
-    m.last = (lane == 31) || (nb != bin);
+    const int nk = __shfl_down_sync(full, key, 1);
+    m.last = (lane == 31) || (nk != key);
     return m;
 }
 

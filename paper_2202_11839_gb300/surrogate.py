@@ -35,9 +35,9 @@ class TrainConfig:
     n_train: int = 20000
     n_test: int = 2000
     batch: int = 256
-    epochs: tuple = (150, 150, 150, 150)          # epochs per learning-rate phase
+    epochs: tuple = (450, 450, 450, 450)          # epochs per learning-rate phase
     lrs: tuple = (1e-3, 3e-4, 1e-4, 3e-5)
-    base_nodes: int = 5                           # Lobatto nodes per (tilt, Gamma) axis of the baseline
+    base_nodes: int = 8                           # Lobatto nodes per (tilt, Gamma) axis of the baseline
     seed: int = 0
 
 

@@ -210,8 +210,9 @@ def test_targets_decode_back_to_the_template():
 
 def test_emulator_accuracy_and_speed():
     """Train on 20k Latin-hypercube templates from the FFTLog path; evaluate on 2k held-out
-    parameter sets in units of the Gaussian error bar.  The trained network beats its
-    interpolated baseline by a wide margin and is much faster than the FFTLog path."""
+    parameter sets in units of the Gaussian error bar: every output within 1% of its error
+    bar (the emulator's accuracy target).  The trained network beats its interpolated
+    baseline by a wide margin and is much faster than the FFTLog path."""
     import torch
     from paper_2202_11839_gb300 import surrogate as SG
     tm = _template()
@@ -219,7 +220,7 @@ def test_emulator_accuracy_and_speed():
     em.train()
     rep = em.evaluate(2000, seed=77)
     print("emulator", rep)
-    assert rep.rms_sigma < 0.005 and rep.p99_sigma < 0.01 and rep.max_sigma < 0.2, rep
+    assert rep.max_sigma <= 0.01 and rep.p99_sigma < 0.002, rep
     assert rep.rms_sigma * 10 < rep.baseline_rms_sigma, rep
     # speed: one batch of 8192 parameter sets through each path
     net = em.inference_net(8192)
