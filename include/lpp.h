@@ -196,6 +196,25 @@ lpp_status lpp_multipoles(lpp_plan_t plan, lpp_result* result);
 lpp_status lpp_window_Q(lpp_plan_t plan, int n_s, const double* s_edges, double* q, double* s_mean,
                         long long* n_points, double* norm);
 
+/* Window multipoles by pair counting, the paper's own method for Q_l (Sec. 4.3; Eq. windowQ_ell
+ * with the endpoint line of sight d = xhat_r, W = alpha sum_r w_r delta_D(x - x_r)):
+ *   Q_l(b) = (2l+1) alpha^2 / (I V_b) sum_{r != r', |s_rr'| in b} w_r w_r' L_l(shat_rr' . xhat_r),
+ * s_rr' = x_r' - x_r (minimal image when box > 0, else none), V_b = 4 pi (e_{b+1}^3 - e_b^3) / 3,
+ * I = alpha sum_r nbar_r w_r^2 (the estimator's normalisation), xhat_r = unit(x_r - observer).
+ * A cross-check of lpp_window_Q (FFT correlations on a grid) for a subsample of the randoms: the
+ * cost grows as n^2 (every unordered pair once, FP64).  The shell of a pair is decided in FP64
+ * on e_b <= sqrt(dx^2 + dy^2 + dz^2) < e_{b+1} with correctly rounded operations.
+ * pos [3][n], w [n] (NULL: 1) and nbar [n] (NULL: 1) are FP64 device arrays; observer [3] and
+ * s_edges [n_s + 1] (increasing, >= 0) are host; q [5][n_s] (l = 0, 2, 4, 6, 8) is host output.
+ * workspace: a 256-byte aligned device buffer of lpp_window_Q_pairs_workspace_size() bytes,
+ * owned by the caller.  Runs on `stream` and synchronises it.  Errors: LPP_ERR_INVALID_ARG
+ * (bad sizes, pointers, alpha <= 0, box < 0, n_s outside 1..256), LPP_ERR_WORKSPACE (buffer too
+ * small), LPP_ERR_CUDA. */
+lpp_status lpp_window_Q_pairs_workspace_size(int n_s, size_t* bytes);
+lpp_status lpp_window_Q_pairs(const double* pos, const double* w, const double* nbar, long long n,
+                              const double* observer, double box, double alpha, int n_s, const double* s_edges,
+                              double* q, void* workspace, size_t bytes, void* stream);
+
 /* ------------------------------------------------------------------ batches of catalogues
  * Many catalogues (mocks) through a set of plans in one launch: the estimator of Secs.
  * 3.1.1-3.1.2 (each mock exactly as lpp_multipoles would compute it on its plan) over many
@@ -255,6 +274,12 @@ void lpp_template_destroy(lpp_template_t tmpl);
 lpp_status lpp_template_workspace_size(lpp_template_t tmpl, size_t* bytes);
 /* Device buffer (256-byte aligned, caller-owned); uploads the tables on `stream` and synchronises it. */
 lpp_status lpp_template_set_workspace(lpp_template_t tmpl, void* device_ptr, size_t bytes, void* stream);
+/* Spin-2 local primordial non-Gaussianity (Sec. 5): the shape response P -> [1 + 12 f_nl db_ia /
+ * M(k)] P with M(k) = (2/3) k^2 T(k) D (c/H0)^2 / omega_m, T the BBKS transfer function of the
+ * template's Gamma and D = 1; the cross spectra carry the factor once, the plus and minus spectra
+ * twice (each shape field responds), the density spectrum not.  f_nl = 0 (the default) is the
+ * Gaussian template.  LPP_ERR_INVALID_ARG for omega_m <= 0 or a NaN. */
+lpp_status lpp_template_set_png(lpp_template_t tmpl, double f_nl, double db_ia, double omega_m);
 /* params: device [n_templates][6]; out: device [n_templates][LPP_N_MOMENTS][n_bins].
  * Asynchronous on `stream`. */
 lpp_status lpp_convolve_template(lpp_template_t tmpl, const double* params, int n_templates, double* out,

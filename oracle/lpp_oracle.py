@@ -681,3 +681,41 @@ def window_pair_count(n: int, box: float, observer, rand_pos, rand_w, rand_nbar,
         out[li] = np.bincount(bp[ok], weights=val[ok], minlength=nbins)[:nbins]
     out = out * alpha * alpha / (np.maximum(npts, 1)[None, :] * h ** 3 * norm)
     return np.where(npts[None, :] > 0, out, 0.0)
+
+
+def window_pair_count_shells(rand_pos, rand_w, rand_nbar, alpha: float, observer, s_edges, box: float = 0.0,
+                             ells=(0, 2, 4, 6, 8)) -> np.ndarray:
+    """Window multipoles by pair counting (the paper's method for Q_l, Sec. 4.3, after
+    Eq. windowQ_ell with W = alpha sum_r w_r delta_D(x - x_r) and the endpoint line of sight):
+
+        Q_l(b) = (2l+1) alpha^2 / (I V_b) sum_{r != r', s_rr' in b} w_r w_r' L_l(shat_rr' . xhat_r),
+
+    s_rr' = x_r' - x_r (minimal image when box > 0), V_b = 4 pi (e_{b+1}^3 - e_b^3) / 3 the
+    volume of shell b = [e_b, e_{b+1}), I = alpha sum_r nbar w^2 (the estimator's normalisation)
+    and xhat_r the unit vector from the observer to x_r.  The direction average over the shell
+    (int dOmega / 4 pi at fixed |s|) is the pair sum divided by the shell volume.  Shell of a
+    pair: e_b <= sqrt(dx^2 + dy^2 + dz^2) < e_{b+1} in FP64, pairs at s = 0 excluded."""
+    from scipy.special import eval_legendre
+    rp = np.asarray(rand_pos, dtype=np.float64)
+    nr = rp.shape[1]
+    w = np.ones(nr) if rand_w is None else np.asarray(rand_w, dtype=np.float64)
+    nb_ = np.ones(nr) if rand_nbar is None else np.asarray(rand_nbar, dtype=np.float64)
+    norm = alpha * np.sum(nb_ * w * w)
+    edges = np.asarray(s_edges, dtype=np.float64)
+    nbins = len(edges) - 1
+    xh = line_of_sight(rp, observer)
+    out = np.zeros((len(ells), nbins))
+    for i in range(nr):
+        d = rp - rp[:, i:i + 1]                       # [3, r'] = x_r' - x_i
+        if box > 0:
+            d = d - box * np.round(d / box)
+        s = np.sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2])
+        b = np.searchsorted(edges, s, side="right") - 1
+        ok = (s > 0) & (b >= 0) & (b < nbins)
+        mu = (xh[i] @ d[:, ok]) / s[ok]
+        ww = w[i] * w[ok]
+        for li, ell in enumerate(ells):
+            out[li] += np.bincount(b[ok], weights=ww * eval_legendre(ell, mu), minlength=nbins)[:nbins]
+    vol = 4.0 * math.pi * (edges[1:] ** 3 - edges[:-1] ** 3) / 3.0
+    ell_fac = np.array([2 * ell + 1 for ell in ells], dtype=np.float64)[:, None]
+    return ell_fac * alpha * alpha * out / (norm * vol[None, :])

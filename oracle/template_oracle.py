@@ -160,6 +160,24 @@ def linear_pk(params):
     return pk
 
 
+C_OVER_H0 = 2997.92458   # Mpc/h: the speed of light over 100 km/s/Mpc
+
+
+def bbks_transfer(k, gamma):
+    """BBKS transfer function T(k / Gamma) (Bardeen et al. 1986), the shape's T in bbks_shape."""
+    q = k / gamma
+    return np.log(1.0 + 2.34 * q) / (2.34 * q) * (1.0 + 3.89 * q + (16.1 * q) ** 2 + (5.46 * q) ** 3
+                                                  + (6.71 * q) ** 4) ** -0.25
+
+
+def png_factor(k, gamma, f_nl, db_ia, omega_m):
+    """Response of a galaxy-shape field to spin-2 local primordial non-Gaussianity (Sec. 5):
+    P -> [1 + 12 f_NL delta b_IA / M(k)] P with M(k) = (2/3) k^2 T(k) D (c/H0)^2 / Omega_m, D = 1.
+    Reading: the factor multiplies each shape field, so P_gd carries it once and P_+- twice."""
+    mk = (2.0 / 3.0) * k * k * bbks_transfer(k, gamma) * C_OVER_H0 ** 2 / omega_m
+    return 1.0 + 12.0 * f_nl * db_ia / mk
+
+
 def model_multipoles(params):
     """Native multipoles P^(L')_X of the tidal-alignment model (Eq. power_for_validation with e = -A T,
     galaxies b_g delta): dd {0: b^2}, cross {2: -A b / 6}, plus {0: 2A^2/15, 2: -4A^2/21, 4: 2A^2/35},
@@ -192,20 +210,27 @@ def bin_average(pk_grid, k_edges):
     return out
 
 
-def template(params, q_table, s, k_edges, shot_plus: float = 0.0, mixing=None):
-    """All twelve window-convolved native multipoles of one parameter set, shell-averaged: (12, nb)."""
+def template(params, q_table, s, k_edges, shot_plus: float = 0.0, mixing=None, png=None):
+    """All twelve window-convolved native multipoles of one parameter set, shell-averaged: (12, nb).
+    png = (f_NL, delta b_IA, Omega_m): the shape spectra carry png_factor (cross once, plus and
+    minus twice; Sec. 5), the density spectrum not."""
     k, r, delta = log_grid()
     pk = linear_pk(params)
-    xi = {lp: hankel_inverse(pk, lp) for lp in (0, 2, 4)}
+    spec = {"dd": pk, "cross": pk, "plus": pk, "minus": pk}
+    if png is not None:
+        f = np.ones(N_FFT)
+        f[:N_IN] = png_factor(k[:N_IN], params[4], *png)
+        spec = {"dd": pk, "cross": pk * f, "plus": pk * f * f, "minus": pk * f * f}
     qr = q_on_r(np.asarray(q_table, dtype=np.float64), np.asarray(s, dtype=np.float64), r)
     model = model_multipoles(params)
+    xi = {(kind, lp): hankel_inverse(spec[kind], lp) for kind in model for lp in model[kind]}
     out = np.zeros((len(SLOTS), len(k_edges) - 1))
     for i, (kind, L) in enumerate(SLOTS):
         g = np.zeros(N_FFT)
         for lp, coef in model[kind].items():
             mix = mixing[(kind, L, lp)] if mixing else [float(c) for c in mixing_coefficients(kind, L, lp)]
             qx = sum(mix[j] * qr[j] for j in range(5))
-            g += coef * qx * xi[lp]
+            g += coef * qx * xi[(kind, lp)]
         pt = hankel_forward(g, L)
         if kind == "plus" and L == 0:
             pt = pt + params[5] * shot_plus

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblpp.so")
-SOURCES = ["lpp_capi.cu", "lpp_tables.cu", "lpp_assign.cu", "lpp_fft.cu", "lpp_combine.cu", "lpp_static.cu", "lpp_tiles.cu", "lpp_window.cu", "lpp_template.cu", "lpp_mlp.cu"]
+SOURCES = ["lpp_capi.cu", "lpp_tables.cu", "lpp_assign.cu", "lpp_fft.cu", "lpp_combine.cu", "lpp_static.cu", "lpp_tiles.cu", "lpp_window.cu", "lpp_template.cu", "lpp_mlp.cu", "lpp_pairs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

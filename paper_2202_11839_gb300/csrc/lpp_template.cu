@@ -70,7 +70,25 @@ struct TemplateArgs {
     const double* eb_ref;
     const double* eb_sigma;
     double N[2][3], M[3][3];
+    // spin-2 primordial non-Gaussianity (Sec. 5): 12 f_NL^(s=2) delta b_IA and (c / H0)^2 / Omega_m;
+    // png_amp = 0: Gaussian initial conditions
+    double png_amp, png_len2;
 };
+
+// BBKS transfer function T(q), q = k / Gamma (Bardeen, Bond, Kaiser & Szalay 1986)
+__device__ __forceinline__ double bbks_transfer(double k, double gam) {
+    const double q = k / gam;
+    return log(1.0 + 2.34 * q) / (2.34 * q) *
+           pow(1.0 + 3.89 * q + (16.1 * q) * (16.1 * q) + (5.46 * q) * (5.46 * q) * (5.46 * q) +
+                   (6.71 * q) * (6.71 * q) * (6.71 * q) * (6.71 * q),
+               -0.25);
+}
+
+// The shape response to spin-2 PNG: P -> [1 + 12 f_NL delta b_IA / M(k)] P for each shape field
+// (Sec. 5), M(k) = (2/3) k^2 T(k) D (c/H0)^2 / Omega_m with D = 1 (z = 0).
+__device__ __forceinline__ double png_factor(double k, double gam, double amp, double len2) {
+    return 1.0 + amp / ((2.0 / 3.0) * k * k * bbks_transfer(k, gam) * len2);
+}
 
 __device__ __forceinline__ double bbks_shape(double k, double gam, double tilt) {
     const double q = k / gam;
@@ -137,25 +155,49 @@ __global__ void __launch_bounds__(512, 1) k_template(TemplateArgs a) {
     for (int n = tid; n < kNin; n += nthr) av[n] *= norm * a.ain[n];
     __syncthreads();
 
-    // xi^(L') = H^-1_L'[P], L' = 0, 2, 4
-    for (int li = 0; li < 3; ++li) {
-        for (int m = tid; m < kNfft; m += nthr) wk[m] = make_double2(m < kNin ? av[m] : 0.0, 0.0);
+    // xi^(L') = H^-1_L'[P_X], one phase of at most three transforms: Gaussian: P at L' = 0, 2, 4
+    // for every slot; with PNG the shape spectra carry the response factor once (cross, phase 0
+    // with the density's P) or twice (plus and minus, phase 1)
+    const bool png = a.png_amp != 0.0;
+    for (int phase = 0; phase < (png ? 2 : 1); ++phase) {
+    int nrow = 3, rowL[3] = {0, 2, 4}, rowP[3] = {0, 0, 0};
+    if (png && phase == 0) { nrow = 2; rowL[1] = 2; rowP[1] = 1; }
+    if (png && phase == 1) { rowP[0] = rowP[1] = rowP[2] = 2; }
+    for (int r = 0; r < nrow; ++r) {
+        for (int m = tid; m < kNfft; m += nthr) {
+            double v = 0.0;
+            if (m < kNin) {
+                v = av[m];
+                if (rowP[r] > 0) {
+                    const double f = png_factor(a.kin[m], gam, a.png_amp, a.png_len2);
+                    v *= rowP[r] == 1 ? f : f * f;
+                }
+            }
+            wk[m] = make_double2(v, 0.0);
+        }
         __syncthreads();
-        log_fourier(wk, a.uinv + (size_t)li * kNfft, a.tw);
-        const double sgn = (li == 1) ? -1.0 : 1.0;   // i^L'
-        for (int m = tid; m < kNfft; m += nthr) xi[li * kNfft + m] = sgn * wk[m].x * a.rinv[m];
+        log_fourier(wk, a.uinv + (size_t)(rowL[r] / 2) * kNfft, a.tw);
+        const double sgn = (rowL[r] == 2) ? -1.0 : 1.0;   // i^L'
+        for (int m = tid; m < kNfft; m += nthr) xi[r * kNfft + m] = sgn * wk[m].x * a.rinv[m];
         __syncthreads();
     }
 
-    // each output slot: mixture with the window, forward transform, shell averages
+    // each output slot of this phase: mixture with the window, forward transform, shell averages
     for (int s = 0; s < kSlots; ++s) {
         const SlotDesc& sd = a.slots[s];
+        if (png && (sd.kind >= 2 ? 1 : 0) != phase) continue;
         double cf[kMaxTerms];
-        for (int j = 0; j < sd.n_terms; ++j) cf[j] = model_coef(sd.coef[j], A, b);
+        int row[kMaxTerms];
+        for (int j = 0; j < sd.n_terms; ++j) {
+            cf[j] = model_coef(sd.coef[j], A, b);
+            row[j] = 0;
+            for (int r = 0; r < nrow; ++r)
+                if (rowL[r] == sd.lp[j]) row[j] = r;
+        }
         for (int m = tid; m < kNfft; m += nthr) {
             double g = 0.0;
             for (int j = 0; j < sd.n_terms; ++j)
-                g += cf[j] * a.qx[(size_t)sd.qx[j] * kNfft + m] * xi[(sd.lp[j] / 2) * kNfft + m];
+                g += cf[j] * a.qx[(size_t)sd.qx[j] * kNfft + m] * xi[row[j] * kNfft + m];
             wk[m] = make_double2(g * a.rfwd[m], 0.0);
         }
         __syncthreads();
@@ -178,6 +220,7 @@ __global__ void __launch_bounds__(512, 1) k_template(TemplateArgs a) {
             if (lane == 0) a.out[((size_t)t * kSlots + s) * a.nb + bb] = den > 0.0 ? num / den + add : 0.0;
         }
         __syncthreads();
+    }
     }
     if (a.eb) {
         // Legendre multipoles of P_gE = Re P_gd and P_EE/BB = (P_+ +- P_-)/2 (Sec. 2.4, Eq. relation_pm_EB)
@@ -288,6 +331,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct lpp_template_s {
     int nb = 0;
     double shot_plus = 0.0;
+    double png_amp = 0.0, png_len2 = 0.0;   // 12 f_NL delta b_IA and (c/H0)^2 / Omega_m
     int qx_rows = 0;
     std::vector<double> kin, s8w, ain, rinv, rfwd, kfwd, qx, bin_w;
     std::vector<double2> uinv, ufwd, tw;
@@ -458,6 +502,14 @@ extern "C" lpp_status lpp_template_set_workspace(lpp_template_t t, void* dev, si
 static lpp_status convolve(lpp_template_t t, const double* params, int n_templates, double* out, float* eb,
                            const double* eb_ref, const double* eb_sigma, void* stream);
 
+extern "C" lpp_status lpp_template_set_png(lpp_template_t t, double f_nl, double db_ia, double omega_m) {
+    if (!t || !(omega_m > 0.0) || !(db_ia == db_ia) || !(f_nl == f_nl)) return LPP_ERR_INVALID_ARG;
+    const double c_over_h0 = 2997.92458;   // Mpc/h: c / (100 km/s/Mpc)
+    t->png_amp = 12.0 * f_nl * db_ia;
+    t->png_len2 = c_over_h0 * c_over_h0 / omega_m;
+    return LPP_OK;
+}
+
 extern "C" lpp_status lpp_convolve_template(lpp_template_t t, const double* params, int n_templates, double* out,
                                             void* stream) {
     return convolve(t, params, n_templates, out, nullptr, nullptr, nullptr, stream);
@@ -494,6 +546,8 @@ static lpp_status convolve(lpp_template_t t, const double* params, int n_templat
     a.bin_w = (const double*)(t->ws + t->o_bw);
     a.nb = t->nb;
     a.shot_plus = t->shot_plus;
+    a.png_amp = t->png_amp;
+    a.png_len2 = t->png_len2;
     for (int s = 0; s < kSlots; ++s) a.slots[s] = t->slots[s];
     a.eb = eb;
     a.eb_ref = eb_ref;

@@ -88,6 +88,7 @@ EXPORTS = {
     "lpp_template_create": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double),
                                       C.c_int, C.c_double, C.POINTER(C.c_void_p)]),
     "lpp_template_destroy": (None, [C.c_void_p]),
+    "lpp_template_set_png": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double]),
     "lpp_template_workspace_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "lpp_template_set_workspace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "lpp_convolve_template": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
@@ -120,6 +121,10 @@ EXPORTS = {
                                               C.c_int, C.c_void_p, C.c_void_p, C.c_longlong, C.c_int,
                                               C.POINTER(C.c_double), C.POINTER(C.c_double),
                                               C.POINTER(C.c_longlong), C.c_void_p]),
+    "lpp_window_Q_pairs_workspace_size": (C.c_int, [C.c_int, C.POINTER(C.c_size_t)]),
+    "lpp_window_Q_pairs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.POINTER(C.c_double),
+                                     C.c_double, C.c_double, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                     C.c_void_p, C.c_size_t, C.c_void_p]),
     "lpp_status_string": (C.c_char_p, [C.c_int]),
     "lpp_plan_last_error": (C.c_char_p, [C.c_void_p]),
 }
@@ -358,6 +363,10 @@ class Template:
         _check(self.lib, self.lib.lpp_template_set_workspace(h, C.c_void_p(addr + off), C.c_size_t(sz.value),
                                                              C.c_void_p(self.stream.cuda_stream)))
 
+    def set_png(self, f_nl: float, db_ia: float = 0.17, omega_m: float = 0.3):
+        """Spin-2 PNG response of the shape spectra (lpp_template_set_png); f_nl = 0: Gaussian."""
+        _check(self.lib, self.lib.lpp_template_set_png(self.h, float(f_nl), float(db_ia), float(omega_m)))
+
     def __call__(self, params, out=None):
         """params: torch float64 CUDA tensor [n, 6]; returns a [n, 12, nb] float64 CUDA tensor."""
         import torch
@@ -528,6 +537,30 @@ class Surrogate:
             self.close()
         except Exception:
             pass
+
+
+def window_q_pairs(pos, w, nbar, observer, s_edges, alpha: float = 1.0, box: float = 0.0, stream=None):
+    """Window multipoles Q_l(s), l = 0..8 even, by pair counting (lpp_window_Q_pairs): pos, w,
+    nbar are FP64 CUDA tensors ([3, n], [n] or None, [n] or None).  Returns q [5, n_s]."""
+    import torch
+    lib = load_library()
+    e = np.ascontiguousarray(s_edges, dtype=np.float64)
+    ns = len(e) - 1
+    sz = C.c_size_t()
+    _check(lib, lib.lpp_window_Q_pairs_workspace_size(ns, C.byref(sz)))
+    ws = torch.empty(sz.value + 256, dtype=torch.uint8, device=pos.device)
+    addr = ws.data_ptr() + (-ws.data_ptr()) % 256
+    for a in (pos, w, nbar):
+        if a is not None and (a.dtype != torch.float64 or not a.is_contiguous() or not a.is_cuda):
+            raise ValueError("pair-count inputs must be contiguous FP64 CUDA tensors")
+    obs = (C.c_double * 3)(*observer)
+    q = np.zeros((5, ns))
+    st = stream if stream is not None else torch.cuda.current_stream(pos.device)
+    dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    _check(lib, lib.lpp_window_Q_pairs(_ptr(pos), _ptr(w), _ptr(nbar), int(pos.shape[1]), obs, float(box),
+                                       float(alpha), ns, dp(e), dp(q), C.c_void_p(addr), C.c_size_t(sz.value),
+                                       C.c_void_p(st.cuda_stream)))
+    return q
 
 
 def derive_eb(p: np.ndarray):

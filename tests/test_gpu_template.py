@@ -52,3 +52,32 @@ def test_template_empty_batch_and_bad_args():
     assert lib.lpp_convolve_template(tm.h, None, 0, None, None) == L.LPP_OK
     assert lib.lpp_convolve_template(tm.h, None, 3, None, None) == L.LPP_ERR_INVALID_ARG
     tm.close()
+
+
+def test_template_png_parity_fp64():
+    """Spin-2 PNG templates (lpp_template_set_png, Sec. 5) against the oracle at 1e-10 per shell."""
+    import torch
+    from paper_2202_11839_gb300 import lpp as L
+    L.load_library()
+    q, s = _window_table()
+    edges = np.linspace(0.0, 0.2, 41)
+    rng = np.random.default_rng(9)
+    lo = np.array([0.0, 1.0, 0.6, -0.2, 0.1, 0.5])
+    hi = np.array([3.0, 3.0, 1.0, 0.2, 0.3, 2.0])
+    params = lo + (hi - lo) * rng.random((4, 6))
+    tm = L.Template(q, s, edges, shot_plus=1234.5)
+    mix = T.mixing_table()
+    for png in ((-180.0, 0.17, 0.3), (40.0, 0.3, 0.25)):
+        tm.set_png(*png)
+        out = tm(torch.from_numpy(params).cuda()).cpu().numpy()
+        for i in range(params.shape[0]):
+            ref = T.template(params[i], q, s, edges, shot_plus=1234.5, mixing=mix, png=png)
+            for j, (kind, Lm) in enumerate(T.SLOTS):
+                scale = np.abs(ref[j]) + 1e-3 * np.abs(ref[FAMILY_SCALE[kind]]).max()
+                err = (np.abs(out[i, j] - ref[j]) / scale).max()
+                assert err < 1e-10, (png, i, kind, Lm, err)
+    tm.set_png(0.0)
+    out0 = tm(torch.from_numpy(params).cuda()).cpu().numpy()
+    ref0 = T.template(params[0], q, s, edges, shot_plus=1234.5, mixing=mix)
+    np.testing.assert_allclose(out0[0], ref0, rtol=1e-9, atol=1e-12 * np.abs(ref0).max())
+    tm.close()

@@ -167,3 +167,36 @@ def test_linear_pk_sigma8_normalisation(params):
     tail = quad(f, math.log(T.K_MAX), math.log(1e3), epsabs=0.0, epsrel=1e-10, limit=4000)[0] + \
         quad(f, math.log(1e-9), math.log(T.K_MIN), epsabs=0.0, epsrel=1e-10)[0]
     assert tail < 1e-5 * s8 * s8
+
+
+def test_png_response_on_the_right_families():
+    """Spin-2 PNG (Sec. 5) through a broad unit window (the identity, as in
+    test_round_trip_and_unit_window): the density slots keep the Gaussian model, the cross
+    slot follows the model times the response factor once and the plus / minus slots times
+    it twice; the factor is 1 + 12 f_NL db_IA / M with M -> (2/3) k^2 (c/H0)^2 / Omega_m at
+    small k (T -> 1), c / H0 = 299792.458 km/s over 100 km/s/Mpc.  f_NL = -20 (about the CMB
+    bound): a much larger |f_NL| makes the squared factor grow as k^-4 at the lowest k, and that
+    power leaks through any window of finite width, so the unit-window identity no longer holds."""
+    params = (1.2, 1.7, 0.8, 0.05, 0.21, 1.0)
+    png = (-20.0, 0.17, 0.3)
+    s = np.geomspace(0.01, 9000.0, 400)
+    qt = np.zeros((5, s.size))
+    qt[0] = np.exp(-(s / 3000.0) ** 2)
+    edges = np.linspace(0.03, 0.2, 10)
+    tmpl = T.template(params, qt, s, edges, png=png)
+    k, r, delta = T.log_grid()
+    pk = T.linear_pk(params)
+    f = np.ones(T.N_FFT)
+    f[:T.N_IN] = T.png_factor(k[:T.N_IN], params[4], *png)
+    model = T.model_multipoles(params)
+    power = {"dd": 0, "cross": 1, "plus": 2, "minus": 2}
+    for i, (kind, L) in enumerate(T.SLOTS):
+        want = T.bin_average(model[kind].get(L, 0.0) * pk * f ** power[kind], edges)
+        scale = np.abs(T.bin_average(model[kind][min(model[kind])] * pk * f ** power[kind], edges))
+        assert np.max(np.abs(tmpl[i] - want) / scale) < 3e-3, (kind, L)
+    # the small-k limit of M, and f_NL = 0 is the Gaussian template
+    kk = 1e-6
+    m_small = 12.0 * 0.17 * (-180.0) / (T.png_factor(kk, 0.21, -180.0, 0.17, 0.3) - 1.0)
+    assert m_small / kk ** 2 == pytest.approx((2.0 / 3.0) * (299792.458 / 100.0) ** 2 / 0.3, rel=1e-4)
+    np.testing.assert_array_equal(T.template(params, qt, s, edges, png=(0.0, 0.17, 0.3)),
+                                  T.template(params, qt, s, edges))
