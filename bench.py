@@ -345,7 +345,8 @@ def batch_leg(args, dev, steps: int):
            "galaxies": {"min": int(min(counts)), "max": int(max(counts)), "total": int(sum(counts))},
            "ms_per_batch": ms / steps, "steps": steps, "graph": True,
            "plans": {f"{n}^3": {"slots": slots[n], "grids_per_pass": tuning[n].batch,
-                                "autotune_ms": {str(k): round(v, 2) for k, v in tuning[n].ms.items()}}
+                                "fused_slots": tuning[n].fused_slots,
+                                "autotune_ms (grids/fused_slots)": {str(k): round(v, 2) for k, v in tuning[n].ms.items()}}
                      for n in grids},
            "error_vs_fp64": errs, "mock_generation_s": gen_s}
     run.close()

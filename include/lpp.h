@@ -106,6 +106,10 @@ typedef struct {
     long long max_randoms;
     int host_inputs;         /* 1: reserve staging so lpp_assign accepts host catalogues       */
     int batch;               /* complex grids per field pass; 0 = library default             */
+    int fused_slots;         /* channel fields per CTA of the fused assignment + x-FFT pass:
+                                0 = library choice (two for FP32 interlaced 256^3 and 512^3 grids
+                                when a batch holds an even number), 1 = always one (a tuning knob;
+                                results agree within the FP32 tolerance)                          */
 } lpp_plan_desc;
 
 typedef struct {

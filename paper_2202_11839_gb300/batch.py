@@ -10,8 +10,10 @@ tensors) are drawn on the host for a few base seeds; each mock then draws its ow
 count, Poisson sample, positions within cells and shape noise from its own seed on the
 device (torch's counter-based generator), so 64 mocks are ready in seconds.
 
-The grids per pass of each plan (its `batch`) are chosen by `autotune`: every candidate is
-timed on a sample mock with the library's own kernel timers.
+The grids per pass of each plan (its `batch`) and the fused pass's channel fields per CTA
+(`fused_slots`) are chosen by `autotune`: every combination is timed on a sample mock with the
+library's own kernel timers.  (The fused kernel's tile shape, 4 x 4 pencils, is fixed at
+compile time.)
 """
 from __future__ import annotations
 
@@ -100,43 +102,47 @@ def k_edges(n: int):
     return K_EDGES[n] if n in K_EDGES else S.linear_edges(0.0, 0.8 * math.pi * n / BOX, 20)
 
 
-def plan_for(n: int, max_shapes: int, batch: int, precision=L.LPP_FP32, device=None, stream=None) -> L.Plan:
+def plan_for(n: int, max_shapes: int, batch: int, precision=L.LPP_FP32, device=None, stream=None,
+             fused_slots: int = 0) -> L.Plan:
     return L.Plan(n, BOX, k_edges(n), observer=OBSERVER, scheme=L.LPP_TSC,
                   interlace=True, precision=precision, max_shapes=max_shapes, batch=batch, device=device,
-                  stream=stream)
+                  stream=stream, fused_slots=fused_slots)
 
 
 @dataclass
 class Tuning:
     n: int
     batch: int
-    ms: dict = field(default_factory=dict)      # candidate -> ms per estimate
+    fused_slots: int = 0
+    ms: dict = field(default_factory=dict)      # "grids/slots" -> ms per estimate
 
 
-def autotune(mock: Mock, candidates=(4, 8, 16), repeats: int = 2) -> Tuning:
-    """Grids per pass for plans of the mock's grid size: the candidate with the shortest
-    estimate, timed by the library's kernel timers on the sample mock."""
+def autotune(mock: Mock, candidates=(4, 6, 8, 16), slot_modes=(0, 1), repeats: int = 2) -> Tuning:
+    """Plan shape for the mock's grid size: grids per pass x the fused pass's channel fields per
+    CTA (library choice, or always one), the combination with the shortest estimate, timed by
+    the library's own kernel timers on the sample mock."""
     import torch
     res = Tuning(mock.n, candidates[0])
     best = None
     for c in candidates:
-        try:
-            plan = plan_for(mock.n, mock.count, c, device=mock.pos.device)
-        except (L.LppError, torch.OutOfMemoryError):
-            continue
-        plan.assign(L.LPP_SHAPES, mock.pos, None, None, mock.shape, L.LPP_SHAPE_TENSOR6)
-        plan.multipoles()
-        plan.set_timing(True)
-        ms = []
-        for _ in range(repeats):
+        for fs in slot_modes:
+            try:
+                plan = plan_for(mock.n, mock.count, c, device=mock.pos.device, fused_slots=fs)
+            except (L.LppError, torch.OutOfMemoryError):
+                continue
+            plan.assign(L.LPP_SHAPES, mock.pos, None, None, mock.shape, L.LPP_SHAPE_TENSOR6)
             plan.multipoles()
-            ms.append(sum(v["ms"] for v in plan.kernel_stats().values()))
-        plan.set_timing(False)
-        res.ms[c] = min(ms)
-        if best is None or res.ms[c] < best:
-            best, res.batch = res.ms[c], c
-        del plan
-        torch.cuda.empty_cache()
+            plan.set_timing(True)
+            ms = []
+            for _ in range(repeats):
+                plan.multipoles()
+                ms.append(sum(v["ms"] for v in plan.kernel_stats().values()))
+            plan.set_timing(False)
+            res.ms[f"{c}/{fs}"] = min(ms)
+            if best is None or min(ms) < best:
+                best, res.batch, res.fused_slots = min(ms), c, fs
+            del plan
+            torch.cuda.empty_cache()
     return res
 
 
@@ -157,7 +163,9 @@ class BatchRun:
             slot_index[n] = []
             for _ in range(k):
                 slot_index[n].append(len(self.plans))
-                self.plans.append(plan_for(n, cap, tuning[n].batch if n in tuning else 8, device=ms[0].pos.device))
+                t = tuning.get(n)
+                self.plans.append(plan_for(n, cap, t.batch if t else 8, device=ms[0].pos.device,
+                                           fused_slots=t.fused_slots if t else 0))
         seen = {n: 0 for n in by_grid}
         # mocks of a grid size go round-robin over its slots
         for m in mocks:

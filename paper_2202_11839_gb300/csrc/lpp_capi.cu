@@ -93,7 +93,8 @@ struct lpp_plan_s {
 // FP32 interlaced grids of 256^3 or 512^3: channel batches with an even slot count run the
 // two-slot fused kernel (with per-tile range records)
 static bool two_slot_grid(lpp_plan_t p) {
-    return !p->fp64 && p->d.interlace && (p->d.n == 256 || p->d.n == 512) && p->d.n / p->ftz <= 256;
+    return !p->fp64 && p->d.interlace && (p->d.n == 256 || p->d.n == 512) && p->d.n / p->ftz <= 256 &&
+           p->d.fused_slots != 1;
 }
 
 static lpp_status fail(lpp_plan_t p, lpp_status s, const std::string& msg) {
@@ -154,6 +155,7 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
     if ((d.moments & (LPP_WANT_ALL | LPP_WANT_DENSITY)) == 0) return LPP_ERR_INVALID_ARG;
     if (d.max_shapes < 0 || d.max_density < 0 || d.max_randoms < 0) return LPP_ERR_INVALID_ARG;
     if (d.batch < 0 || d.batch > kMaxSlots) return LPP_ERR_INVALID_ARG;
+    if (d.fused_slots < 0 || d.fused_slots > 2) return LPP_ERR_INVALID_ARG;
     for (int i = 0; i < d.n_bins; ++i)
         if (!(d.k_edges[i] < d.k_edges[i + 1])) return LPP_ERR_INVALID_ARG;
     const double pn = sqrt(d.pole[0] * d.pole[0] + d.pole[1] * d.pole[1] + d.pole[2] * d.pole[2]);

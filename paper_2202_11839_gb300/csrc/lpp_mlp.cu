@@ -297,18 +297,36 @@ __device__ double baseline(const MapArgs& a, const double* t, int j) {
     return u;
 }
 
-// network outputs y [m][320] -> standardised curves (pre_c (baseline + sd y) + theta_5 s - ref) / sigma
-__global__ void k_decode(const double* __restrict__ theta, int m, const float* __restrict__ y, float* __restrict__ out,
-                         MapArgs a) {
+// network outputs y [m][320] -> standardised curves (pre_c (baseline + sd y) + theta_5 s - ref) / sigma.
+// One CTA of kNout threads per parameter row at a time: the row's Lagrange weights
+// l_a(x_p) l_b(x_q) are formed once in shared memory, then thread j sums its baseline output
+// (the same terms in the same order as baseline()).
+__global__ void __launch_bounds__(kNout) k_decode(const double* __restrict__ theta, int m, const float* __restrict__ y,
+                                                  float* __restrict__ out, MapArgs a) {
     constexpr int nb = kNout / 8;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m * kNout; i += gridDim.x * blockDim.x) {
-        const int r = i / kNout, j = i % kNout;
+    __shared__ double la[kMaxNodes], lb[kMaxNodes], wab[kMaxNodes * kMaxNodes];
+    const int j = threadIdx.x;
+    const int nn = a.base ? a.nodes * a.nodes : 0;
+    for (int r = blockIdx.x; r < m; r += gridDim.x) {
         const double* t = theta + (size_t)r * kNin;
+        if (a.base) {
+            if (j < 2) {
+                const int c = a.base_in[j];
+                lobatto_basis(t[c] * a.dscale[c] + a.dshift[c], a.nodes, j == 0 ? la : lb);
+            }
+            __syncthreads();
+            for (int q = j; q < nn; q += blockDim.x) wab[q] = la[q / a.nodes] * lb[q % a.nodes];
+            __syncthreads();
+        }
+        double u = a.mu[j];
+        for (int q = 0; q < nn; ++q) u += wab[q] * a.base[(size_t)q * kNout + j];
+        const size_t i = (size_t)r * kNout + j;
         const double amp = t[2] * t[2] * ((j / nb) < 2 ? t[0] * t[1] : t[0] * t[0]);
-        double v = amp * (baseline(a, t, j) + a.sd[j] * (double)y[i]) + t[5] * a.shot[j];
+        double v = amp * (u + a.sd[j] * (double)y[i]) + t[5] * a.shot[j];
         if (a.ref) v -= a.ref[j];
         if (a.sigma) v /= a.sigma[j];
         out[i] = (float)v;
+        __syncthreads();   // la, lb, wab are rewritten for the next row
     }
 }
 
@@ -570,7 +588,12 @@ extern "C" lpp_status lpp_surrogate_predict(lpp_surrogate_t s, const double* the
         k_encode<<<(m * kNin + 255) / 256, 256, 0, st>>>(th, m, x, s->map);
         float* y = out + (size_t)r0 * kNout;
         if (forward(s, x, nullptr, m, false, y, st) != cudaSuccess) return LPP_ERR_CUDA;
-        k_decode<<<(m * kNout + 255) / 256, 256, 0, st>>>(th, m, y, y, s->map);
+        {
+            int dev = 0, sms = 152;
+            if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const int blocks = m < sms * 6 ? (m > 0 ? m : 1) : sms * 6;
+            k_decode<<<blocks, kNout, 0, st>>>(th, m, y, y, s->map);
+        }
     }
     return cudaGetLastError() == cudaSuccess ? LPP_OK : LPP_ERR_CUDA;
 }

@@ -50,7 +50,7 @@ class PlanDesc(C.Structure):
         ("moments", C.c_uint), ("n_bins", C.c_int), ("k_edges", C.POINTER(C.c_double)),
         ("norm_override", C.c_double), ("subtract_shot", C.c_int), ("max_shapes", C.c_longlong),
         ("max_density", C.c_longlong), ("max_randoms", C.c_longlong), ("host_inputs", C.c_int),
-        ("batch", C.c_int),
+        ("batch", C.c_int), ("fused_slots", C.c_int),
     ]
 
 
@@ -194,7 +194,8 @@ class Plan:
                  precision: int = LPP_FP32, los_proj: int = LPP_LOS_LOCAL, los_est: int = LPP_LOS_LOCAL,
                  los_global=(0.0, 0.0, 1.0), moments: int = LPP_WANT_ALL, norm_override: float = 0.0,
                  subtract_shot: bool = True, max_shapes: int = 0, max_density: int = 0, max_randoms: int = 0,
-                 host_inputs: bool = False, batch: int = 0, stream=None, workspace=None, device=None):
+                 host_inputs: bool = False, batch: int = 0, fused_slots: int = 0, stream=None, workspace=None,
+                 device=None):
         import torch
         self.lib = load_library()
         self.torch = torch
@@ -213,7 +214,7 @@ class Plan:
         d.k_edges = self.edges.ctypes.data_as(C.POINTER(C.c_double))
         d.norm_override, d.subtract_shot = norm_override, int(subtract_shot)
         d.max_shapes, d.max_density, d.max_randoms = max_shapes, max_density, max_randoms
-        d.host_inputs, d.batch = int(host_inputs), batch
+        d.host_inputs, d.batch, d.fused_slots = int(host_inputs), batch, fused_slots
         self.desc = d
         self.precision = precision
         self.dtype = np.float64 if precision == LPP_FP64 else np.float32

@@ -83,7 +83,7 @@ def run_gpu(cfg: dict, cat: dict, precision: int, device_inputs: bool = True):
                   norm_override=cfg.get("norm_override", 0.0), subtract_shot=cfg.get("subtract_shot", True),
                   max_shapes=cat["pos"].shape[1], max_density=cat["dpos"].shape[1] if "dpos" in cat else 0,
                   max_randoms=cat["rpos"].shape[1] if "rpos" in cat else 0, host_inputs=not device_inputs,
-                  batch=cfg.get("batch", 0))
+                  batch=cfg.get("batch", 0), fused_slots=cfg.get("fused_slots", 0))
 
     def conv(a):
         if a is None:

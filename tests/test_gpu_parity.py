@@ -222,3 +222,21 @@ def test_periodic_fp64_workload_full_size(L):
     ref = U.run_oracle(cfg, cat)
     gpu = U.run_gpu(cfg, cat, L.LPP_FP64)
     U.assert_parity(gpu, ref, TOL64, wl.name)
+
+
+def test_one_slot_fused_pass_matches_two_slot(L):
+    """fused_slots = 1 (the autotuner's alternative) against the library's two-slot choice at
+    256^3, TSC + interlacing, FP32: the same estimate within the FP32 tolerance, and the path
+    counters show which form ran."""
+    n, box = 256, 1000.0
+    cat = U.make_case("slots256", n, count=60_000, seed=23, box=box, dtype=np.float32, yslab=(0.2, 0.6),
+                      zslab=(0.35, 0.7), n_rand=100_000)
+    cfg = _cfg(n, box, scheme=3, interlace=True, frac=0.5, nb=12, cross_b=True)
+    two = U.run_gpu(cfg, cat, L.LPP_FP32)
+    one = U.run_gpu(dict(cfg, fused_slots=1), cat, L.LPP_FP32)
+    assert two.extra["path"]["two_slot_launches"] > 0
+    assert one.extra["path"]["two_slot_launches"] == 0
+    pp = np.abs(two.raw[O.M_INDEX[("plus", 0)]].real) / two.norm_auto
+    pd = np.abs(two.raw[O.M_INDEX[("dd", 0)]].real) / two.norm_dd
+    sc = np.abs(two.p) + np.sqrt(pp * pd)[None, :]
+    assert (np.abs(one.p - two.p) / np.where(sc > 0, sc, 1.0)).max() < TOL32
