@@ -508,13 +508,17 @@ def run_lpp(args):
     cpu = None
     if world == 1 and not args.no_cpu:
         cpu = cpu_baseline_leg(wl)
+    # measured DRAM bytes per launch of the dominant kernel kind (profiles/traffic.json), for the
+    # default full-size configuration only (the figures were taken for it)
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
+    default_cfg = (args.n == 512 and args.data == 1_500_000 and args.randoms == 15_000_000 and args.batch == 0
+                   and args.moment_mask < 0)
+    if default_cfg and os.path.exists(prof):
         with open(prof) as f:
             tr = json.load(f)
-        if tr.get("kernel") == dom and tr.get("workload") == wl.name:
-            traffic = tr.get("bytes_per_launch")
+        if tr.get("workload") == wl.name:
+            traffic = tr.get("kernels", {}).get(dom, {}).get("bytes_per_launch")
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
