@@ -195,9 +195,9 @@ class OracleTimer:
         from oracle import lpp_oracle as O
         t0 = time.perf_counter()
         if self.pool is None:
-            _oracle_slot_task((self.cfg, self.cat, tuple(O.MOMENTS)))
+            _oracle_slot_task((self.cfg, self.cat, tuple(O.DEFAULT_MOMENTS)))
         else:
-            self.pool.map(_oracle_slot_task, [(self.cfg, self.cat, (mom,)) for mom in O.MOMENTS], chunksize=1)
+            self.pool.map(_oracle_slot_task, [(self.cfg, self.cat, (mom,)) for mom in O.DEFAULT_MOMENTS], chunksize=1)
         wall = time.perf_counter() - t0
         wl = self.wl
         desc = (f"one complete oracle estimate (ten slots, cross E+B, TSC+interlacing) on a {self.ns}^3 grid over "

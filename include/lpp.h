@@ -8,7 +8,7 @@
  *
  *   cross  P^(L)_gd, L = 2,4,6   Sec. 3.1.2, Eqs. lpp_estimator_cross_Xiij, def_of_Xiij
  *   plus   P^(l)_+,  l = 0,2,4   Eq. lpp_estimator_auto_+ (Appendix B)
- *   minus  P^(L)_-,  L = 4,6,8   Eqs. lpp_estimator_auto_-, def_of_Xiijkl (Appendix B)
+ *   minus  P^(L)_-,  L = 4..12   Eqs. lpp_estimator_auto_-, def_of_Xiijkl (Appendix B)
  *   density   P^(l)_dd, l = 0,2,4 Sec. 3.1.1, Eqs. lpp_dens_app, delta_ell
  *
  * The shear of each galaxy is gamma = e_ij(x) s_ij (Eq. gamma_def), with
@@ -61,14 +61,16 @@ enum { LPP_SHAPE_NONE = 0, LPP_SHAPE_GAMMA12 = 1, LPP_SHAPE_TENSOR6 = 2 };
 
 /* Moment slots of every output array, in this order.  Slots 10 and 11 are the density
  * quadrupole and hexadecapole P^(2,4)_dd of Eq. lpp_dens_app (Yamamoto form: each
- * catalogue's delta^(l) with its own endpoint lines of sight, Eq. delta_ell). */
-#define LPP_N_MOMENTS 12
+ * catalogue's delta^(l) with its own endpoint lines of sight, Eq. delta_ell).  Slots 12 and 13
+ * are the minus moments L = 10, 12. */
+#define LPP_N_MOMENTS 14
 enum {
     LPP_MOM_DD0 = 0,
     LPP_MOM_CROSS2 = 1, LPP_MOM_CROSS4 = 2, LPP_MOM_CROSS6 = 3,
     LPP_MOM_PLUS0 = 4, LPP_MOM_PLUS2 = 5, LPP_MOM_PLUS4 = 6,
     LPP_MOM_MINUS4 = 7, LPP_MOM_MINUS6 = 8, LPP_MOM_MINUS8 = 9,
-    LPP_MOM_DD2 = 10, LPP_MOM_DD4 = 11
+    LPP_MOM_DD2 = 10, LPP_MOM_DD4 = 11,
+    LPP_MOM_MINUS10 = 12, LPP_MOM_MINUS12 = 13
 };
 /* bitmask of requested moments: bit i enables slot i.  LPP_WANT_ALL is the ten slots of
  * the density monopole and the tensor estimators; LPP_WANT_DENSITY adds the density
@@ -79,6 +81,9 @@ enum {
 #define LPP_WANT_DD2 (1u << LPP_MOM_DD2)
 #define LPP_WANT_DD4 (1u << LPP_MOM_DD4)
 #define LPP_WANT_DENSITY (LPP_WANT_DD2 | LPP_WANT_DD4)
+/* the minus moments beyond L = 8 (Eq. lpp_estimator_auto_- with L = 10, 12; 2 (2L+1) fields each),
+ * for the completeness of the minus-spectrum expansion (Sec. 2.4) and its systematics tests */
+#define LPP_WANT_MINUS_HIGH ((1u << LPP_MOM_MINUS10) | (1u << LPP_MOM_MINUS12))
 #define LPP_WANT_CROSS_B (1u << 16)
 
 typedef struct lpp_plan_s* lpp_plan_t;

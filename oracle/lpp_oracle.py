@@ -12,7 +12,7 @@ It follows the paper's own Cartesian form of the estimators:
       Xi^(L)_ij(k) = FT[ gamma 2 e*_ij(x) Lm2_L(k.x) / (1-(k.x)^2) ]
 * plus (Eq. lpp_estimator_auto_+)
       P^(l)_+(k) = (2l+1) < gamma^(l)(k) gamma*(-k) >_shell,  gamma^(l) = FT[gamma L_l(k.x)]
-* minus (Eq. lpp_estimator_auto_-, Eq. def_of_Xiijkl)
+* minus (Eq. lpp_estimator_auto_-, Eq. def_of_Xiijkl), L = 4, 6, ..., 12
       P^(L)_-(k) = (2L+1)(L-4)!/(L+4)! < Xi^(L)_ijkl(k) k_i k_j k_k k_l gamma(-k) >_shell
       Xi^(L)_ijkl = FT[ gamma 4 e*_ij e*_kl Lm4_L(k.x) / (1-(k.x)^2)^2 ]
 
@@ -46,9 +46,13 @@ import numpy as np
 from numpy.polynomial import legendre as npleg
 from numpy.polynomial import polynomial as nppoly
 
-# moment slots (fixed order, shared with the public header's documented layout)
+# moments this oracle evaluates, in a fixed order: the density monopole, the ten of the paper's
+# headline set (cross L <= 6, plus l <= 4, minus L <= 8), then the minus moments L = 10, 12 that
+# continue the expansion of P_-(k, mu) in Lm4_L (Sec. 2.4); a Plan evaluates DEFAULT_MOMENTS
+# unless told otherwise
 MOMENTS = [("dd", 0), ("cross", 2), ("cross", 4), ("cross", 6), ("plus", 0), ("plus", 2),
-           ("plus", 4), ("minus", 4), ("minus", 6), ("minus", 8)]
+           ("plus", 4), ("minus", 4), ("minus", 6), ("minus", 8), ("minus", 10), ("minus", 12)]
+DEFAULT_MOMENTS = MOMENTS[:10]
 M_INDEX = {m: i for i, m in enumerate(MOMENTS)}
 
 
@@ -345,7 +349,7 @@ class Plan:
     los_proj_global: bool = False   # True: project shapes with the global n (case (c))
     los_est_global: bool = False    # True: estimator uses the global n (cases (b), (c))
     los_global: tuple = (0.0, 0.0, 1.0)
-    moments: tuple = tuple(MOMENTS)
+    moments: tuple = tuple(DEFAULT_MOMENTS)
     cross_b: bool = False
     k_edges: np.ndarray = field(default_factory=lambda: np.zeros(0))
     norm_override: float = 0.0

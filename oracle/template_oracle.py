@@ -44,11 +44,13 @@ K_MAX = 10.0
 Q_INV = 1.5
 Q_FWD = 0.5
 
-# output slots in the order of the estimator (dd0, cross2,4,6, plus0,2,4, minus4,6,8, dd2,4);
-# the density quadrupole and hexadecapole of the model (no redshift-space distortions) are
-# pure window leakage of the monopole, the mixtures Q^dd_20 and Q^dd_40 (Sec. 4.3)
+# output slots in the order of the estimator (dd0, cross2,4,6, plus0,2,4, minus4,6,8, dd2,4,
+# minus10,12); the density quadrupole and hexadecapole of the model (no redshift-space
+# distortions) are pure window leakage of the monopole, the mixtures Q^dd_20 and Q^dd_40
+# (Sec. 4.3), and so are the minus moments L = 10, 12 of the minus hexadecapole (Q^-_L4 with
+# the window multipoles l'' = 6, 8 for L = 10 and l'' = 8 for L = 12)
 SLOTS = [("dd", 0), ("cross", 2), ("cross", 4), ("cross", 6), ("plus", 0), ("plus", 2), ("plus", 4),
-         ("minus", 4), ("minus", 6), ("minus", 8), ("dd", 2), ("dd", 4)]
+         ("minus", 4), ("minus", 6), ("minus", 8), ("dd", 2), ("dd", 4), ("minus", 10), ("minus", 12)]
 M_OF = {"dd": 0, "cross": 2, "plus": 0, "minus": 4}
 
 
@@ -211,7 +213,7 @@ def bin_average(pk_grid, k_edges):
 
 
 def template(params, q_table, s, k_edges, shot_plus: float = 0.0, mixing=None, png=None):
-    """All twelve window-convolved native multipoles of one parameter set, shell-averaged: (12, nb).
+    """All fourteen window-convolved native multipoles of one parameter set, shell-averaged: (14, nb).
     png = (f_NL, delta b_IA, Omega_m): the shape spectra carry png_factor (cross once, plus and
     minus twice; Sec. 5), the density spectrum not."""
     k, r, delta = log_grid()

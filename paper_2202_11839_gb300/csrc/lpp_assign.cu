@@ -40,7 +40,8 @@ __device__ __forceinline__ void sky_frame(const T xh[3], const double pole[3], T
 // (x, y, z, 0) and the table transposed to [S][NHP] (NHP = 2L + 1 rounded up to a multiple
 // of 4), so that a quadrature point reads its direction and its 2L + 1 table entries in
 // 16-byte words; every thread of a block reads the same entries at the same time
-// (broadcast).  The blocks of L = 2, 4, 6, 8 follow one another, then the polynomials.
+// (broadcast).  The blocks of L = 2, 4, ..., 12 follow one another, then the polynomials; a
+// degree that no group of the plan uses has S = 0 and takes no space.
 __host__ __device__ constexpr int quad_nhp(int q) { return (2 * (2 * (q + 1)) + 1 + 3) & ~3; }
 
 template <typename T>
@@ -62,13 +63,14 @@ __device__ __forceinline__ void project_group(const CoeffArgs<T>& a, const Coeff
     const T* tab = dirs + 4 * S;
     int op = 0;
 #pragma unroll
-    for (int qq = 0; qq < 4; ++qq) op += quad_block_words(a, qq);
+    for (int qq = 0; qq < kQuadDegrees; ++qq) op += quad_block_words(a, qq);
     const T* poly = sm + op + g.poly;
-    // the kernel polynomial in registers, zero-padded to 8 coefficients (the leading zeros
-    // leave Horner's scheme exact)
-    T pc[8];
+    // the kernel polynomial in registers, zero-padded to NPC coefficients (the leading zeros
+    // leave Horner's scheme exact); the minus kernel of L = 12 has degree 8
+    constexpr int NPC = L > 10 ? 9 : 8;
+    T pc[NPC];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) pc[k] = k < g.npoly ? poly[k] : (T)0;
+    for (int k = 0; k < NPC; ++k) pc[k] = k < g.npoly ? poly[k] : (T)0;
     T accr[NH], acci[NH];
 #pragma unroll
     for (int n = 0; n < NH; ++n) { accr[n] = (T)0; acci[n] = (T)0; }
@@ -99,7 +101,7 @@ __device__ __forceinline__ void project_group(const CoeffArgs<T>& a, const Coeff
         const T mu = kx * xh[0] + ky * xh[1] + kz * xh[2];
         T pm = (T)0;
 #pragma unroll
-        for (int k = 7; k >= 0; --k) pm = pm * mu + pc[k];
+        for (int k = NPC - 1; k >= 0; --k) pm = pm * mu + pc[k];
         T kre, kim;
         if (g.kind == KIND_PLUS) {
             kre = gre * pm;
@@ -168,22 +170,24 @@ __device__ __forceinline__ void block_add(double v, double* dst) {
     }
 }
 
-// Shared-memory words for the quadrature directions and tables (L = 2, 4, 6, 8, laid out as
-// in project_group) and the polynomials.
+// Shared-memory words for the quadrature directions and tables (L = 2, 4, ..., 12, laid out
+// as in project_group) and the polynomials.
 template <typename T>
 __host__ __device__ inline int coeff_smem_words(const CoeffArgs<T>& a) {
     int w = a.n_polys;
-    for (int q = 0; q < 4; ++q) w += quad_block_words(a, q);
+    for (int q = 0; q < kQuadDegrees; ++q) w += quad_block_words(a, q);
     return w;
 }
 
-template <typename T>
+// HIGH: the plan has groups of degree 10 or 12 (the minus moments beyond L = 8), a separate
+// instantiation so that their register arrays leave the usual one unchanged
+template <typename T, bool HIGH>
 __global__ void __launch_bounds__(256) k_coeffs(CoeffArgs<T> a) {
     extern __shared__ __align__(16) unsigned char coeff_smem[];
     T* sm = reinterpret_cast<T*>(coeff_smem);
     {
         int o = 0;
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < kQuadDegrees; ++q) {
             const int S = a.quad_S[q], nh = 2 * (2 * (q + 1)) + 1, nhp = quad_nhp(q);
             // directions [S][3] -> [S][4]; table [nh][S] -> [S][nhp] (zero padding)
             for (int i = threadIdx.x; i < 4 * S; i += blockDim.x)
@@ -253,6 +257,9 @@ __global__ void __launch_bounds__(256) k_coeffs(CoeffArgs<T> a) {
                 else project_group<T, 6, false>(a, g, i, w, g1, g2, ete, epe, xe, sm);
             } else if (g.L == 8) {
                 project_group<T, 8, true>(a, g, i, w, g1, g2, ete, epe, xe, sm);
+            } else if constexpr (HIGH) {
+                if (g.L == 10) project_group<T, 10, true>(a, g, i, w, g1, g2, ete, epe, xe, sm);
+                else if (g.L == 12) project_group<T, 12, true>(a, g, i, w, g1, g2, ete, epe, xe, sm);
             }
         }
     }
@@ -267,8 +274,15 @@ cudaError_t launch_coeffs(const CoeffArgs<T>& a, cudaStream_t st) {
     if (blocks > 152 * 16) blocks = 152 * 16;
     const size_t smem = (size_t)coeff_smem_words(a) * sizeof(T);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
-    cudaFuncSetAttribute(k_coeffs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_coeffs<T><<<(int)blocks, 256, smem, st>>>(a);
+    bool high = false;
+    for (int g = 0; g < a.n_groups; ++g) high = high || a.groups[g].L > 8;
+    if (high) {
+        cudaFuncSetAttribute(k_coeffs<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_coeffs<T, true><<<(int)blocks, 256, smem, st>>>(a);
+    } else {
+        cudaFuncSetAttribute(k_coeffs<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_coeffs<T, false><<<(int)blocks, 256, smem, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

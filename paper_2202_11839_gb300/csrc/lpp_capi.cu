@@ -55,14 +55,14 @@ struct lpp_plan_s {
     int batch_ch = 8;
     // host tables
     std::vector<double> polys;
-    Quadrature quad[4];
+    Quadrature quad[kQuadDegrees];
     KernelPolys kp;
     // workspace
     char* ws = nullptr;
     size_t ws_bytes = 0;
     size_t ws_need = 0;
     size_t off_sums = 0, off_err = 0, off_out = 0, off_thr = 0, off_tw = 0, off_iw = 0, off_ph = 0;
-    size_t off_quad_dirs[4] = {0}, off_quad_tab[4] = {0}, off_polys = 0, off_coeff = 0;
+    size_t off_quad_dirs[kQuadDegrees] = {0}, off_quad_tab[kQuadDegrees] = {0}, off_polys = 0, off_coeff = 0;
     size_t off_partner = 0, off_grids = 0, off_stage[3] = {0, 0, 0};
     // pencil-sorted catalogues: key, cell coordinates, weights, key offsets; shapes permutation
     size_t off_key[3] = {0, 0, 0}, off_su[3] = {0, 0, 0}, off_sw[3] = {0, 0, 0}, off_koff[3] = {0, 0, 0};
@@ -218,7 +218,7 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
 
     // kernel polynomials and quadratures
     build_kernel_polys(plan->kp);
-    for (int qi = 0; qi < 4; ++qi) build_quadrature(2 * (qi + 1), plan->quad[qi]);
+    for (int qi = 0; qi < kQuadDegrees; ++qi) build_quadrature(2 * (qi + 1), plan->quad[qi]);
 
     // channel groups: (kind, L) -> 2L+1 coefficient rows per projected part
     const unsigned m = d.moments;
@@ -255,8 +255,8 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
         if (m & (1u << crossSlot[i])) add_group(KIND_CROSS, 2 * (i + 1), cross_b ? 1 : 0, plan->kp.cross[i], 2 * i + 1, crossSlot[i]);
     if (m & (1u << LPP_MOM_PLUS2)) add_group(KIND_PLUS, 2, 1, plan->kp.plus[1], 3, LPP_MOM_PLUS2);
     if (m & (1u << LPP_MOM_PLUS4)) add_group(KIND_PLUS, 4, 1, plan->kp.plus[2], 5, LPP_MOM_PLUS4);
-    const int minusSlot[3] = {LPP_MOM_MINUS4, LPP_MOM_MINUS6, LPP_MOM_MINUS8};
-    for (int i = 0; i < 3; ++i)
+    const int minusSlot[5] = {LPP_MOM_MINUS4, LPP_MOM_MINUS6, LPP_MOM_MINUS8, LPP_MOM_MINUS10, LPP_MOM_MINUS12};
+    for (int i = 0; i < 5; ++i)
         if (m & (1u << minusSlot[i])) add_group(KIND_MINUS, 4 + 2 * i, 1, plan->kp.minus[i], 2 * i + 1, minusSlot[i]);
     plan->n_coeff_rows = row;
     plan->n_tensor_ch = (int)plan->channels.size();
@@ -280,7 +280,8 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
     plan->need_d = (m & ((1u << LPP_MOM_DD0) | (1u << LPP_MOM_CROSS2) | (1u << LPP_MOM_CROSS4) |
                          (1u << LPP_MOM_CROSS6) | LPP_WANT_DENSITY)) != 0;
     plan->need_g = (m & ((1u << LPP_MOM_PLUS0) | (1u << LPP_MOM_PLUS2) | (1u << LPP_MOM_PLUS4) |
-                         (1u << LPP_MOM_MINUS4) | (1u << LPP_MOM_MINUS6) | (1u << LPP_MOM_MINUS8))) != 0;
+                         (1u << LPP_MOM_MINUS4) | (1u << LPP_MOM_MINUS6) | (1u << LPP_MOM_MINUS8) |
+                         LPP_WANT_MINUS_HIGH)) != 0;
     plan->n_partner = (plan->need_d ? 1 : 0) + (plan->need_g ? 2 : 0);
     plan->out_rows = (int)plan->channels.size() + 2;
 
@@ -307,7 +308,7 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
     plan->off_tw = take(n * cs);
     plan->off_iw = take(n * es);
     plan->off_ph = take(n * cs);
-    for (int qi = 0; qi < 4; ++qi) {
+    for (int qi = 0; qi < kQuadDegrees; ++qi) {
         plan->off_quad_dirs[qi] = take(plan->quad[qi].dirs.size() * es);
         plan->off_quad_tab[qi] = take(plan->quad[qi].table.size() * es);
     }
@@ -402,14 +403,14 @@ static lpp_status write_tables(lpp_plan_t plan) {
     }
     // host copies stay alive until the stream has consumed them (synchronised below)
     std::vector<std::vector<T>> keep;
-    keep.reserve(16);
+    keep.reserve(32);
     keep.push_back(tw);
     keep.push_back(iw);
     keep.push_back(ph);
     LPP_CUDA(put(plan->off_tw, keep[0].data(), keep[0].size() * sizeof(T)));
     LPP_CUDA(put(plan->off_iw, keep[1].data(), keep[1].size() * sizeof(T)));
     LPP_CUDA(put(plan->off_ph, keep[2].data(), keep[2].size() * sizeof(T)));
-    for (int qi = 0; qi < 4; ++qi) {
+    for (int qi = 0; qi < kQuadDegrees; ++qi) {
         keep.emplace_back(plan->quad[qi].dirs.begin(), plan->quad[qi].dirs.end());
         LPP_CUDA(put(plan->off_quad_dirs[qi], keep.back().data(), keep.back().size() * sizeof(T)));
         keep.emplace_back(plan->quad[qi].table.begin(), plan->quad[qi].table.end());
@@ -664,10 +665,12 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
     ca.stride = stride;
     ca.n_groups = (int)plan->groups.size();
     for (int g = 0; g < ca.n_groups; ++g) ca.groups[g] = plan->groups[g];
-    for (int qi = 0; qi < 4; ++qi) {
+    for (int qi = 0; qi < kQuadDegrees; ++qi) {
+        bool used = false;
+        for (const CoeffGroup& g : plan->groups) used = used || g.quad == qi;
         ca.quad_dirs[qi] = (const T*)(plan->ws + plan->off_quad_dirs[qi]);
         ca.quad_tab[qi] = (const T*)(plan->ws + plan->off_quad_tab[qi]);
-        ca.quad_S[qi] = plan->quad[qi].S;
+        ca.quad_S[qi] = used ? plan->quad[qi].S : 0;
     }
     ca.polys = (const T*)(plan->ws + plan->off_polys);
     ca.n_polys = (int)plan->polys.size();
@@ -1046,7 +1049,10 @@ static lpp_status finish(lpp_plan_t plan, const double* h_out, const double* h_s
             const int l = 2 * (s - LPP_MOM_PLUS0);
             C = 2.0 * l + 1.0;
             if (l == 0) shot = shot_plus;
-        } else { C = norm_factor(4, 4 + 2 * (s - LPP_MOM_MINUS4)); }
+        } else {
+            const int Lm = s == LPP_MOM_MINUS10 ? 10 : s == LPP_MOM_MINUS12 ? 12 : 4 + 2 * (s - LPP_MOM_MINUS4);
+            C = norm_factor(4, Lm);
+        }
         const bool on = (want & (1u << s)) != 0;
         for (int b = 0; b < nb; ++b) {
             const size_t k = ((size_t)s * nb + b) * 2;

@@ -28,7 +28,7 @@ template <typename T> __host__ __device__ __forceinline__ c2<T> cscale(c2<T> a, 
 // multiply by -i
 template <typename T> __host__ __device__ __forceinline__ c2<T> cmul_mi(c2<T> a) { return mk<T>(a.y, -a.x); }
 
-// ------------------------------------------------- real spherical harmonics, degree <= 8
+// ------------------------------------------------ real spherical harmonics, degree <= 12
 // Real orthonormal harmonics on the unit sphere:
 //   Y_{L,0}  = N_L0 Q_L^0(z)
 //   Y_{L,+m} = sqrt(2) N_Lm Q_L^m(z) Re[(x + i y)^m]
@@ -135,7 +135,7 @@ struct KernelPolys {
     // cross: Lm2_L / (1 - mu^2);  minus: Lm4_L / (1 - mu^2)^2;  plus: L_l
     double cross[4][8];   // L = 2,4,6 (index L/2 - 1); up to mu^6
     double plus[3][8];    // l = 0,2,4 (index l/2)
-    double minus[3][8];   // L = 4,6,8 (index L/2 - 2)
+    double minus[5][9];   // L = 4,6,8,10,12 (index L/2 - 2); up to mu^8
 };
 
 void build_quadrature(int L, Quadrature& q);

@@ -83,6 +83,7 @@ cudaError_t fft_yz(c2<T>* data, int n_grids, int n, const c2<T>* tw, const FftGe
 
 // ---------------------------------------------------------- per-particle weights
 constexpr int kMaxGroups = 16;
+constexpr int kQuadDegrees = 6;    // harmonic projection quadratures for L = 2, 4, ..., 12
 constexpr int kMaxSlots = 8;       // complex grids per batch (FftGeom::gmask has as many)
 constexpr int kMaxBatchCh = 16;    // real fields per batch
 
@@ -113,9 +114,9 @@ struct CoeffArgs {
     long long stride;
     int n_groups;
     CoeffGroup groups[kMaxGroups];
-    const T* quad_dirs[4];   // per L = 2,4,6,8: [S][3]
-    const T* quad_tab[4];    // per L: [2L+1][S]
-    int quad_S[4];
+    const T* quad_dirs[kQuadDegrees];   // per L = 2,4,...,12: [S][3]
+    const T* quad_tab[kQuadDegrees];    // per L: [2L+1][S]
+    int quad_S[kQuadDegrees];           // 0 for a degree no group of the plan uses
     const T* polys;          // concatenated mu-polynomial coefficients
     int n_polys;
     double* sums;            // FP64 reductions (see SumSlot)

@@ -37,7 +37,8 @@ static int derive(double* c, int deg, int m) {
 
 void build_kernel_polys(KernelPolys& kp) {
     for (int i = 0; i < 4; ++i) for (int j = 0; j < 8; ++j) kp.cross[i][j] = 0.0;
-    for (int i = 0; i < 3; ++i) for (int j = 0; j < 8; ++j) { kp.plus[i][j] = 0.0; kp.minus[i][j] = 0.0; }
+    for (int i = 0; i < 3; ++i) for (int j = 0; j < 8; ++j) kp.plus[i][j] = 0.0;
+    for (int i = 0; i < 5; ++i) for (int j = 0; j < 9; ++j) kp.minus[i][j] = 0.0;
     double c[16];
     // Lm_L(mu)/(1-mu^2)^(m/2) = (-1)^m d^m L_L / dmu^m (m even: sign +1)
     for (int L = 2; L <= 6; L += 2) {
@@ -51,7 +52,7 @@ void build_kernel_polys(KernelPolys& kp) {
         legendre_poly(l, c);
         for (int i = 0; i <= l; ++i) kp.plus[l / 2][i] = c[i];
     }
-    for (int L = 4; L <= 8; L += 2) {
+    for (int L = 4; L <= 12; L += 2) {
         for (int i = 0; i < 16; ++i) c[i] = 0.0;
         legendre_poly(L, c);
         const int d = derive(c, L, 4);

@@ -7,9 +7,10 @@
 // expanded in a discrete Fourier series in ln x and each term is transformed with the Mellin
 // transform of j_l,  int_0^inf x^(s-1) j_l(x) dx = 2^(s-2) sqrt(pi) G((l+s)/2) / G((3+l-s)/2).
 // One CTA evaluates one parameter set: the BBKS model and its sigma_8 normalisation, three
-// inverse transforms (L' = 0, 2, 4), then for each of the twelve output slots (the
-// estimator's order, with the density quadrupole and hexadecapole last: their templates are
-// the leakage of the monopole through Q_2 and Q_4, Sec. 4.3) the mixture with the window
+// inverse transforms (L' = 0, 2, 4), then for each of the fourteen output slots (the
+// estimator's order: the density quadrupole and hexadecapole, whose templates are the
+// leakage of the monopole through Q_2 and Q_4, Sec. 4.3, then the minus moments L = 10, 12,
+// which the model leaves zero and only the window fills) the mixture with the window
 // multipoles, one forward transform and the shell averages.  Everything is FP64.
 //
 // Grid (shared with the tests): 2048 log-spaced k in [1e-4, 10], zero padding to 4096,
@@ -33,6 +34,7 @@ constexpr int kLogN = 12;
 constexpr double kKmin = 1e-4, kKmax = 10.0, kQinv = 1.5, kQfwd = 0.5, kTaper = 0.1;
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kSlots = LPP_N_MOMENTS;
+constexpr int kNfwd = 7;      // forward transforms of order l = 0, 2, ..., 12 (the output slots' L)
 constexpr int kMaxTerms = 3;   // model multipoles L' feeding one output slot
 
 struct SlotDesc {
@@ -53,7 +55,7 @@ struct TemplateArgs {
     const double* ain;      // [2048] k^3 taper k^-q_inv
     const double2* uinv;    // [3][4096] inverse kernels (1/N folded in)
     const double* rinv;     // [4096] r^-q_inv / (2 pi^2)
-    const double2* ufwd;    // [5][4096] forward kernels (1/N folded in)
+    const double2* ufwd;    // [7][4096] forward kernels of l = 0, 2, ..., 12 (1/N folded in)
     const double* rfwd;     // [4096] r^(3 - q_fwd)
     const double* kfwd;     // [2048] 4 pi k^-q_fwd
     const double* qx;       // [rows][4096] mixed window Q^X_LL'(r_m)
@@ -381,8 +383,8 @@ extern "C" lpp_status lpp_template_create(const double* q, const double* s, int 
     }
     t->uinv.resize(3 * kNfft);
     for (int li = 0; li < 3; ++li) fftlog_kernel(2 * li, kQinv, delta, kr0, &t->uinv[li * kNfft]);
-    t->ufwd.resize(5 * kNfft);
-    for (int li = 0; li < 5; ++li) fftlog_kernel(2 * li, kQfwd, delta, kr0, &t->ufwd[li * kNfft]);
+    t->ufwd.resize(kNfwd * kNfft);
+    for (int li = 0; li < kNfwd; ++li) fftlog_kernel(2 * li, kQfwd, delta, kr0, &t->ufwd[li * kNfft]);
     t->tw.resize(kNfft);
     for (int j = 0; j < kNfft; ++j) t->tw[j] = make_double2(cos(2.0 * kPi * j / kNfft), -sin(2.0 * kPi * j / kNfft));
     // window multipoles on the r grid: linear in s, held below s_0, zero beyond the last s
@@ -402,8 +404,8 @@ extern "C" lpp_status lpp_template_create(const double* q, const double* s, int 
             qr[li * kNfft + m] = v;
         }
     // output slots: kind, L and the model multipoles feeding them
-    const int kinds[kSlots] = {0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 0, 0};
-    const int Ls[kSlots] = {0, 2, 4, 6, 0, 2, 4, 4, 6, 8, 2, 4};
+    const int kinds[kSlots] = {0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 0, 0, 3, 3};
+    const int Ls[kSlots] = {0, 2, 4, 6, 0, 2, 4, 4, 6, 8, 2, 4, 10, 12};
     const int mX[4] = {0, 2, 0, 4};
     int rows = 0;
     for (int sl = 0; sl < kSlots; ++sl) {
@@ -449,7 +451,7 @@ extern "C" lpp_status lpp_template_create(const double* q, const double* s, int 
     t->o_ain = take(kNin * 8);
     t->o_uinv = take(3 * kNfft * 16);
     t->o_rinv = take(kNfft * 8);
-    t->o_ufwd = take(5 * kNfft * 16);
+    t->o_ufwd = take(kNfwd * kNfft * 16);
     t->o_rfwd = take(kNfft * 8);
     t->o_kfwd = take(kNin * 8);
     t->o_qx = take((size_t)rows * kNfft * 8);
@@ -485,7 +487,7 @@ extern "C" lpp_status lpp_template_set_workspace(lpp_template_t t, void* dev, si
     if (e == cudaSuccess) e = put(t->o_ain, t->ain.data(), kNin * 8);
     if (e == cudaSuccess) e = put(t->o_uinv, t->uinv.data(), 3 * kNfft * 16);
     if (e == cudaSuccess) e = put(t->o_rinv, t->rinv.data(), kNfft * 8);
-    if (e == cudaSuccess) e = put(t->o_ufwd, t->ufwd.data(), 5 * kNfft * 16);
+    if (e == cudaSuccess) e = put(t->o_ufwd, t->ufwd.data(), kNfwd * kNfft * 16);
     if (e == cudaSuccess) e = put(t->o_rfwd, t->rfwd.data(), kNfft * 8);
     if (e == cudaSuccess) e = put(t->o_kfwd, t->kfwd.data(), kNin * 8);
     if (e == cudaSuccess) e = put(t->o_qx, t->qx.data(), t->qx.size() * 8);

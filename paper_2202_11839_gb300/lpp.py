@@ -23,15 +23,17 @@ LPP_FP32, LPP_FP64 = 0, 1
 LPP_LOS_LOCAL, LPP_LOS_GLOBAL = 0, 1
 LPP_SHAPES, LPP_DENSITY, LPP_RANDOMS = 0, 1, 2
 LPP_SHAPE_NONE, LPP_SHAPE_GAMMA12, LPP_SHAPE_TENSOR6 = 0, 1, 2
-LPP_N_MOMENTS = 12
+LPP_N_MOMENTS = 14
 LPP_MOM_DD0, LPP_MOM_CROSS2, LPP_MOM_CROSS4, LPP_MOM_CROSS6, LPP_MOM_PLUS0, LPP_MOM_PLUS2, LPP_MOM_PLUS4, \
-    LPP_MOM_MINUS4, LPP_MOM_MINUS6, LPP_MOM_MINUS8, LPP_MOM_DD2, LPP_MOM_DD4 = range(LPP_N_MOMENTS)
+    LPP_MOM_MINUS4, LPP_MOM_MINUS6, LPP_MOM_MINUS8, LPP_MOM_DD2, LPP_MOM_DD4, LPP_MOM_MINUS10, \
+    LPP_MOM_MINUS12 = range(LPP_N_MOMENTS)
 MOMENT_NAMES = ["dd0", "cross2", "cross4", "cross6", "plus0", "plus2", "plus4", "minus4", "minus6", "minus8",
-                "dd2", "dd4"]
+                "dd2", "dd4", "minus10", "minus12"]
 LPP_WANT_ALL = 0x3FF
 LPP_WANT_DD2 = 1 << LPP_MOM_DD2
 LPP_WANT_DD4 = 1 << LPP_MOM_DD4
 LPP_WANT_DENSITY = LPP_WANT_DD2 | LPP_WANT_DD4
+LPP_WANT_MINUS_HIGH = (1 << LPP_MOM_MINUS10) | (1 << LPP_MOM_MINUS12)
 LPP_WANT_CROSS_B = 1 << 16
 KERNEL_KINDS = ["assign", "fft", "combine", "coeffs", "partner", "other"]
 

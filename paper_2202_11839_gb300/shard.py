@@ -6,7 +6,7 @@ harmonic channels).  So a rank builds its plan with a subset of the slots (the p
 `moments` mask), recomputes the partner fields it needs locally (three grids, cheaper than
 sending them), and computes only its slots' channels.  Each normalised row is then complete
 on the rank that owns it (its shot noise is subtracted there once), and an all-reduce (sum)
-of the (2, 12, n_bins, 2) FP64 array of normalised and raw rows, each row non-zero on
+of the (2, LPP_N_MOMENTS, n_bins, 2) FP64 array of normalised and raw rows, each row non-zero on
 exactly one rank, gives every rank the whole estimate; the shell counts, mean |k|,
 normalisations and shot noises, the same on every rank that computed them, travel in a
 second, max all-reduce of 2 n_bins + 6 numbers.
@@ -24,7 +24,7 @@ from . import lpp as L
 # dd0 and plus0 come from the partner fields alone; the density multipoles have one part)
 _SLOT_L = {L.LPP_MOM_CROSS2: 2, L.LPP_MOM_CROSS4: 4, L.LPP_MOM_CROSS6: 6, L.LPP_MOM_PLUS2: 2,
            L.LPP_MOM_PLUS4: 4, L.LPP_MOM_MINUS4: 4, L.LPP_MOM_MINUS6: 6, L.LPP_MOM_MINUS8: 8,
-           L.LPP_MOM_DD2: 2, L.LPP_MOM_DD4: 4}
+           L.LPP_MOM_DD2: 2, L.LPP_MOM_DD4: 4, L.LPP_MOM_MINUS10: 10, L.LPP_MOM_MINUS12: 12}
 _CROSS = (L.LPP_MOM_CROSS2, L.LPP_MOM_CROSS4, L.LPP_MOM_CROSS6)
 _ONE_PART = (L.LPP_MOM_DD2, L.LPP_MOM_DD4)
 

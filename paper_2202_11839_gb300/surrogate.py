@@ -115,7 +115,7 @@ class Emulator:
         self.net = None
 
     def _derived64(self, params: np.ndarray):
-        """Native slots [12, nb] of one parameter set from the template kernel (FP64) and its
+        """Native slots [LPP_N_MOMENTS, nb] of one parameter set from the template kernel (FP64) and its
         derived curves [8, nb] in FP64 (lpp_derive_eb)."""
         torch = self.torch
         native = self.t(torch.from_numpy(np.ascontiguousarray(params, dtype=np.float64)).to(self.device))

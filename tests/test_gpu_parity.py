@@ -52,6 +52,10 @@ CASES64 = {
     # confined in y and z: empty tiles and unreached pencils inside the reached planes
     "yz_box_tsc_il_randoms_n32": (_cfg(32, 300.0, scheme=3, interlace=True, frac=0.6),
                                   dict(count=1500, n_rand=4000, yslab=(0.55, 0.8), zslab=(0.2, 0.4))),
+    # every tensor moment, the minus moments L = 10, 12 included (0x3000: slots 12 and 13)
+    "minus_high_tsc_il_randoms_density": (_cfg(16, 300.0, scheme=3, interlace=True, gpu_moments=0x33FF,
+                                               oracle_moments=tuple(O.MOMENTS)),
+                                          dict(count=1200, n_rand=3000, separate_density=True)),
 }
 
 
@@ -74,6 +78,10 @@ CASES32 = {
                            dict(count=6000, n_rand=12000, yslab=(0.1, 0.35), zslab=(0.6, 0.75))),
     "zslab_randoms_n64": (_cfg(64, 800.0, scheme=3, interlace=True, frac=0.5), dict(count=6000, n_rand=12000,
                                                                                    zslab=(0.55, 0.7))),
+    # the minus moments L = 10, 12 alone beside the two monopoles (slots 0, 4, 12, 13)
+    "minus_high_only_n32": (_cfg(32, 500.0, scheme=3, interlace=True, gpu_moments=0x3011,
+                                 oracle_moments=(("dd", 0), ("plus", 0), ("minus", 10), ("minus", 12))),
+                            dict(count=6000)),
 }
 
 
@@ -93,7 +101,7 @@ def test_host_inputs_match_device_inputs(L):
     b = U.run_gpu(cfg, cat, L.LPP_FP32, device_inputs=False)
     ref = U.run_oracle(cfg, cat)
     sc = U.scale(ref)
-    assert np.max(np.abs(a.p - b.p)[:len(O.MOMENTS)] / np.where(sc > 0, sc, 1)) < 1e-6
+    assert np.max(np.abs(U.oracle_rows(a.p) - U.oracle_rows(b.p)) / np.where(sc > 0, sc, 1)) < 1e-6
 
 
 def test_repeat_runs_agree(L):
@@ -104,7 +112,7 @@ def test_repeat_runs_agree(L):
     a = U.run_gpu(cfg, cat, L.LPP_FP32)
     b = U.run_gpu(cfg, cat, L.LPP_FP32)
     sc = U.scale(ref)
-    assert np.max(np.abs(a.p - b.p)[:len(O.MOMENTS)] / np.where(sc > 0, sc, 1)) < 1e-6
+    assert np.max(np.abs(U.oracle_rows(a.p) - U.oracle_rows(b.p)) / np.where(sc > 0, sc, 1)) < 1e-6
 
 
 def test_particle_outside_box_is_an_error(L):
@@ -208,7 +216,7 @@ def test_fp32_interlaced_256_matches_fp64(L, cross_b):
     sc = np.abs(g64.p) + np.sqrt(pp * pd)[None, :]
     err = np.abs(g32.p - g64.p) / np.where(sc > 0, sc, 1.0)
     np.testing.assert_array_equal(g32.n_modes, g64.n_modes)
-    assert err.max() < TOL32, {O.MOMENTS[i]: float(e) for i, e in enumerate(err.max(axis=1))}
+    assert err.max() < TOL32, {L.MOMENT_NAMES[i]: float(e) for i, e in enumerate(err.max(axis=1))}
 
 
 @pytest.mark.slow

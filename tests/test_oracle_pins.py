@@ -23,7 +23,7 @@ def _poly(c, x):
 
 
 # ----------------------------------------------------------------- Legendre pins
-@pytest.mark.parametrize("m,L", [(2, 2), (2, 4), (2, 6), (4, 4), (4, 6), (4, 8), (0, 2), (0, 4)])
+@pytest.mark.parametrize("m,L", [(2, 2), (2, 4), (2, 6), (4, 4), (4, 6), (4, 8), (4, 10), (4, 12), (0, 2), (0, 4)])
 def test_reduced_assoc_legendre_matches_scipy(m, L):
     """(1-mu^2)^(m/2) * reduced poly == scipy lpmv (Condon-Shortley phase included; Eq. def_of_asso)."""
     mu = np.linspace(-0.97, 0.97, 41)
@@ -34,7 +34,7 @@ def test_reduced_assoc_legendre_matches_scipy(m, L):
 @pytest.mark.parametrize("m", [2, 4])
 def test_assoc_legendre_orthogonality(m):
     """int dmu/2 Lm_L Lm_L' = (L+m)!/((2L+1)(L-m)!) delta_LL' (Eq. ortho_asso_legendre)."""
-    Ls = [L for L in range(m, 11, 2)]
+    Ls = [L for L in range(m, 15, 2)]
     for L in Ls:
         for Lp in Ls:
             a = (1 - GL_X ** 2) ** (m // 2) * _poly(O.reduced_assoc_legendre(m, L), GL_X)
@@ -65,6 +65,8 @@ def test_tidal_model_normalisation_coefficients():
     assert minus(4) == pytest.approx(1 / 420, abs=1e-15)
     assert minus(6) == pytest.approx(0.0, abs=1e-13)
     assert minus(8) == pytest.approx(0.0, abs=1e-12)
+    assert minus(10) == pytest.approx(0.0, abs=1e-12)
+    assert minus(12) == pytest.approx(0.0, abs=1e-12)
 
 
 def test_exact_legendre_fractions_match_float():
@@ -149,7 +151,7 @@ def _on_node_catalogue(n, box, count, seed):
 
 
 @pytest.mark.parametrize("kind,L", [("cross", 2), ("cross", 4), ("cross", 6), ("plus", 2), ("plus", 4),
-                                    ("minus", 4), ("minus", 6), ("minus", 8)])
+                                    ("minus", 4), ("minus", 6), ("minus", 8), ("minus", 10), ("minus", 12)])
 def test_cartesian_expansion_equals_direct_sum_on_nodes(kind, L):
     """Particles on grid nodes, CIC, no deconvolution/interlacing: the gridded Cartesian
     expansion equals the direct per-mode sum sum_g w K_X(k; x_g) e^{-ik.x_g} to rounding."""
@@ -228,7 +230,7 @@ def _grid_catalogues(n, box, dk):
 def test_gpp_identity_per_mode():
     """With x := n everywhere the LPP machinery equals the per-mode GPP estimator
     C <gamma(k) e^{-2i phi_k} Lm2_L(mu_k) delta*(k)> (Eq. gpp_estimator_cross), and likewise
-    (2l+1)<gamma(k) L_l(mu) gamma*(k)> and C<gamma(k) e^{-4i phi} Lm4_L gamma(-k)>."""
+    (2l+1)<gamma(k) L_l(mu) gamma*(k)> and C<gamma(k) e^{-4i phi} Lm4_L gamma(-k)> (minus L up to 12)."""
     n, box = 12, 300.0
     rng = np.random.default_rng(7)
     pos = rng.uniform(0, box, (3, 200))
@@ -239,7 +241,7 @@ def test_gpp_identity_per_mode():
     edges = np.linspace(0, np.pi * n / box, 6)
     plan = O.Plan(n=n, box=box, observer=(0, 0, -1e4), scheme=2, compensate=False,
                   los_proj_global=True, los_est_global=True, los_global=tuple(nvec), cross_b=True,
-                  k_edges=edges, norm_override=1.0, subtract_shot=False)
+                  k_edges=edges, norm_override=1.0, subtract_shot=False, moments=tuple(O.MOMENTS))
     res = O.multipoles(plan, pos, shapes_s6=s6, dens_pos=pos, dens_w=dens_w)
     mg = O.ModeGrid(n, box)
     st = O.assignment_stencil(pos, n, box, (0, 0, 0), 2, 0.0)
@@ -262,7 +264,7 @@ def test_gpp_identity_per_mode():
         v = G * lpmv(0, l, mu) * np.conj(G)
         want = (2 * l + 1) * O._shell_sum(v, b, nb) / nm
         np.testing.assert_allclose(res.p[O.M_INDEX[("plus", l)]], want, rtol=1e-9, atol=1e-9 * np.abs(want).max())
-    for L in (4, 6, 8):
+    for L in (4, 6, 8, 10, 12):
         v = G * np.exp(-4j * phi) * lpmv(4, L, mu) * np.conj(Gc)
         want = O.norm_factor(4, L) * O._shell_sum(v, b, nb) / nm
         np.testing.assert_allclose(res.p[O.M_INDEX[("minus", L)]], want, rtol=1e-9, atol=1e-9 * np.abs(want).max())
@@ -280,7 +282,7 @@ def test_fixed_amplitude_tidal_field_closed_form():
     edges = np.linspace(0, np.pi * n / box, 7)
     plan = O.Plan(n=n, box=box, observer=(0, 0, -1e5), scheme=2, compensate=False,
                   los_proj_global=True, los_est_global=True, los_global=tuple(nvec), cross_b=True,
-                  k_edges=edges, norm_override=1.0, subtract_shot=False)
+                  k_edges=edges, norm_override=1.0, subtract_shot=False, moments=tuple(O.MOMENTS))
     res = O.multipoles(plan, pos, shapes_s6=tij, dens_pos=pos, dens_w=delta)
     mg = O.ModeGrid(n, box)
     D = np.fft.fftn(delta.reshape(n, n, n))
@@ -297,7 +299,7 @@ def test_fixed_amplitude_tidal_field_closed_form():
     for l in (0, 2, 4):
         want = (2 * l + 1) * shell(0.25 * (1 - mu ** 2) ** 2 * lpmv(0, l, mu) * p2)
         np.testing.assert_allclose(res.p[O.M_INDEX[("plus", l)]].real, want, rtol=1e-9, atol=1e-9 * p2.max())
-    for L in (4, 6, 8):
+    for L in (4, 6, 8, 10, 12):
         want = O.norm_factor(4, L) * shell(0.25 * (1 - mu ** 2) ** 2 * lpmv(4, L, mu) * p2)
         got = res.p[O.M_INDEX[("minus", L)]]
         np.testing.assert_allclose(got.real, want, rtol=1e-9, atol=1e-9 * p2.max())

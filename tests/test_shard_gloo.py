@@ -23,7 +23,8 @@ def _sh():
 
 
 @pytest.mark.parametrize("with_b", [False, True])
-@pytest.mark.parametrize("moments", [0x3FF, 0xFFF, 0x3FE, (1 << 5) | (1 << 9) | (1 << 11), 1 << 4])
+@pytest.mark.parametrize("moments", [0x3FF, 0xFFF, 0x3FFF, 0x3FE, (1 << 5) | (1 << 9) | (1 << 11), 1 << 4,
+                                     (1 << 12) | (1 << 13)])
 def test_partition_covers_each_slot_once_and_balances(moments, with_b):
     L, SH = _sh()
     extra = L.LPP_WANT_CROSS_B if with_b else 0
@@ -48,28 +49,33 @@ def test_slot_channels_match_the_plan_tables():
     assert sum(SH.slot_channels(s, False) for s in range(10)) == 133
     assert sum(SH.slot_channels(s, True) for s in range(10)) == 160
     assert SH.slot_channels(L.LPP_MOM_DD2, True) == 5 and SH.slot_channels(L.LPP_MOM_DD4, False) == 9
+    # and 2 x 21 + 2 x 25 for the minus moments L = 10, 12
+    assert SH.slot_channels(L.LPP_MOM_MINUS10, False) == 42 and SH.slot_channels(L.LPP_MOM_MINUS12, True) == 50
 
 
 def _oracle_estimate():
-    """Oracle estimate with twelve slots: the tensor-estimator slots and the density l = 2, 4."""
+    """Oracle estimate in the library's fourteen slots: the tensor-estimator slots, the density
+    l = 2, 4 and the minus moments L = 10, 12."""
     sys.path.insert(0, ROOT)
     from oracle import lpp_oracle as O
     from tests import parity_util as U
     cfg = dict(n=16, box=300.0, observer=(150.0, 150.0, -800.0), scheme=3, interlace=True,
-               k_edges=U.default_edges(16, 300.0))
+               k_edges=U.default_edges(16, 300.0), oracle_moments=tuple(O.MOMENTS))
     cat = U.make_case("shard", 16, count=1200, seed=7, n_rand=2500)
     ref = U.run_oracle(cfg, cat)
     dens = U.run_oracle_density(cfg, cat)
-    ref.p = np.concatenate([ref.p, dens.p[1:]])
-    ref.raw = np.concatenate([ref.raw, dens.raw[1:]])
-    assert ref.p.shape[0] == 12 and O.MOMENTS[0] == ("dd", 0)
+    # the library's slot order: the oracle's ten default moments, the density l = 2, 4, then
+    # the minus moments L = 10, 12
+    ref.p = np.concatenate([ref.p[:10], dens.p[1:], ref.p[10:12]])
+    ref.raw = np.concatenate([ref.raw[:10], dens.raw[1:], ref.raw[10:12]])
+    assert ref.p.shape[0] == 14 and O.MOMENTS[0] == ("dd", 0) and O.MOMENTS[10] == ("minus", 10)
     return ref
 
 
 def test_single_process_gather_is_the_identity():
     L, SH = _sh()
     ref = _oracle_estimate()
-    out = SH.gather(ref, L.LPP_WANT_ALL | L.LPP_WANT_DENSITY)
+    out = SH.gather(ref, L.LPP_WANT_ALL | L.LPP_WANT_DENSITY | L.LPP_WANT_MINUS_HIGH)
     np.testing.assert_array_equal(out.p, ref.p)
     np.testing.assert_array_equal(out.raw, ref.raw)
     np.testing.assert_array_equal(out.n_modes, ref.n_modes)
@@ -95,13 +101,13 @@ def _rank(rank, world, port, moments, q):
         # gather must drop)
         mine = L.Estimate(ref.p.copy(), ref.raw.copy(), ref.k_mean, ref.n_modes, ref.norm_auto, ref.norm_cross,
                           ref.norm_dd, ref.shot_plus, ref.shot_dd, ref.alpha)
-        for s in range(12):
+        for s in range(L.LPP_N_MOMENTS):
             if not mask & (1 << s):
                 mine.p[s] = 1e30 * (rank + 1)
                 mine.raw[s] = -1e30
     out = SH.gather(mine, mask, dist, "cpu")
     want = ref.p.copy()
-    for s in range(12):
+    for s in range(L.LPP_N_MOMENTS):
         if not moments & (1 << s):
             want[s] = 0
     q.put((rank, mask, np.array_equal(out.p, want), np.array_equal(out.n_modes, ref.n_modes),
@@ -110,12 +116,12 @@ def _rank(rank, world, port, moments, q):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("moments", [0xFFF, (1 << 5) | (1 << 9)])
+@pytest.mark.parametrize("moments", [0x3FFF, (1 << 5) | (1 << 9)])
 def test_two_gloo_ranks_gather_the_whole_estimate(moments):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    world = 2 if moments == 0xFFF else 3        # the second case leaves one rank without a slot
+    world = 2 if moments == 0x3FFF else 3       # the second case leaves one rank without a slot
     procs = [ctx.Process(target=_rank, args=(r, world, port, moments, q)) for r in range(world)]
     for p in procs:
         p.start()

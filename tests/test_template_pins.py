@@ -58,6 +58,19 @@ def test_fftlog_gaussian_pair(ell):
     assert np.max(np.abs(xi[sel] - want[sel])) < 1e-7 * scale
 
 
+@pytest.mark.parametrize("ell", [2, 8, 10, 12])
+def test_fftlog_forward_gaussian_pair(ell):
+    """The forward transform of the output slots' orders, up to the minus moments L = 10, 12:
+    4 pi (-i)^l int r^(l+2) e^{-b r^2} j_l(kr) dr = 4 pi (-i)^l sqrt(pi) k^l e^{-k^2/4b} / (2^(l+2) b^(l+3/2))."""
+    k, r, delta = T.log_grid()
+    for b in (0.01, 0.001):
+        pk = T.hankel_forward(r ** ell * np.exp(-b * r * r), ell)
+        want = 4.0 * math.pi * ((-1j) ** ell).real * math.sqrt(math.pi) * k ** ell * np.exp(-k * k / (4 * b)) / (
+            2 ** (ell + 2) * b ** (ell + 1.5))
+        sel = (k > 1e-3) & (k < 3.0)
+        assert np.max(np.abs(pk[sel] - want[sel])) < 1e-10 * np.abs(want[sel]).max()
+
+
 def test_fftlog_matches_direct_quadrature():
     """H^-1_l of the (tapered) BBKS spectrum against adaptive quadrature of the same integrand."""
     from scipy.interpolate import interp1d
