@@ -289,6 +289,12 @@ lpp_status lpp_template_set_workspace(lpp_template_t tmpl, void* device_ptr, siz
  * twice (each shape field responds), the density spectrum not.  f_nl = 0 (the default) is the
  * Gaussian template.  LPP_ERR_INVALID_ARG for omega_m <= 0 or a NaN. */
 lpp_status lpp_template_set_png(lpp_template_t tmpl, double f_nl, double db_ia, double omega_m);
+/* The output slots to compute (bit i: slot i, as in lpp_plan_desc.moments; default all
+ * LPP_N_MOMENTS): the others are written as zeros and cost nothing.  lpp_convolve_template_eb
+ * needs the nine slots its derived curves read (mask 0x3FE: cross, plus and minus up to L = 8)
+ * and returns LPP_ERR_INVALID_ARG without them.  LPP_ERR_INVALID_ARG for bits at or above
+ * LPP_N_MOMENTS.  Host-only. */
+lpp_status lpp_template_set_slots(lpp_template_t tmpl, unsigned mask);
 /* params: device [n_templates][6]; out: device [n_templates][LPP_N_MOMENTS][n_bins].
  * Asynchronous on `stream`. */
 lpp_status lpp_convolve_template(lpp_template_t tmpl, const double* params, int n_templates, double* out,

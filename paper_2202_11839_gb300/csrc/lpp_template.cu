@@ -34,6 +34,8 @@ constexpr int kLogN = 12;
 constexpr double kKmin = 1e-4, kKmax = 10.0, kQinv = 1.5, kQfwd = 0.5, kTaper = 0.1;
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kSlots = LPP_N_MOMENTS;
+// the slots the derived curves read: cross L = 2, 4, 6, plus l = 0, 2, 4, minus L = 4, 6, 8
+constexpr unsigned kEbSlots = 0x3FEu;
 constexpr int kNfwd = 7;      // forward transforms of order l = 0, 2, ..., 12 (the output slots' L)
 constexpr int kMaxTerms = 3;   // model multipoles L' feeding one output slot
 
@@ -75,6 +77,7 @@ struct TemplateArgs {
     // spin-2 primordial non-Gaussianity (Sec. 5): 12 f_NL^(s=2) delta b_IA and (c / H0)^2 / Omega_m;
     // png_amp = 0: Gaussian initial conditions
     double png_amp, png_len2;
+    unsigned slot_mask;     // output slots to compute; the others are written as zeros
 };
 
 // BBKS transfer function T(q), q = k / Gamma (Bardeen, Bond, Kaiser & Szalay 1986)
@@ -188,6 +191,10 @@ __global__ void __launch_bounds__(512, 1) k_template(TemplateArgs a) {
     for (int s = 0; s < kSlots; ++s) {
         const SlotDesc& sd = a.slots[s];
         if (png && (sd.kind >= 2 ? 1 : 0) != phase) continue;
+        if (!((a.slot_mask >> s) & 1u)) {
+            for (int bb = tid; bb < a.nb; bb += nthr) a.out[((size_t)t * kSlots + s) * a.nb + bb] = 0.0;
+            continue;
+        }
         double cf[kMaxTerms];
         int row[kMaxTerms];
         for (int j = 0; j < sd.n_terms; ++j) {
@@ -334,6 +341,7 @@ struct lpp_template_s {
     int nb = 0;
     double shot_plus = 0.0;
     double png_amp = 0.0, png_len2 = 0.0;   // 12 f_NL delta b_IA and (c/H0)^2 / Omega_m
+    unsigned slot_mask = (1u << kSlots) - 1u;
     int qx_rows = 0;
     std::vector<double> kin, s8w, ain, rinv, rfwd, kfwd, qx, bin_w;
     std::vector<double2> uinv, ufwd, tw;
@@ -512,6 +520,12 @@ extern "C" lpp_status lpp_template_set_png(lpp_template_t t, double f_nl, double
     return LPP_OK;
 }
 
+extern "C" lpp_status lpp_template_set_slots(lpp_template_t t, unsigned mask) {
+    if (!t || (mask >> kSlots) != 0u) return LPP_ERR_INVALID_ARG;
+    t->slot_mask = mask;
+    return LPP_OK;
+}
+
 extern "C" lpp_status lpp_convolve_template(lpp_template_t t, const double* params, int n_templates, double* out,
                                             void* stream) {
     return convolve(t, params, n_templates, out, nullptr, nullptr, nullptr, stream);
@@ -520,6 +534,7 @@ extern "C" lpp_status lpp_convolve_template(lpp_template_t t, const double* para
 extern "C" lpp_status lpp_convolve_template_eb(lpp_template_t t, const double* params, int n_templates, double* out,
                                                float* eb, const double* eb_ref, const double* eb_sigma, void* stream) {
     if (n_templates > 0 && !eb) return LPP_ERR_INVALID_ARG;
+    if (t && (t->slot_mask & kEbSlots) != kEbSlots) return LPP_ERR_INVALID_ARG;
     return convolve(t, params, n_templates, out, eb, eb_ref, eb_sigma, stream);
 }
 
@@ -550,6 +565,7 @@ static lpp_status convolve(lpp_template_t t, const double* params, int n_templat
     a.shot_plus = t->shot_plus;
     a.png_amp = t->png_amp;
     a.png_len2 = t->png_len2;
+    a.slot_mask = t->slot_mask;
     for (int s = 0; s < kSlots; ++s) a.slots[s] = t->slots[s];
     a.eb = eb;
     a.eb_ref = eb_ref;

@@ -34,6 +34,7 @@ LPP_WANT_DD2 = 1 << LPP_MOM_DD2
 LPP_WANT_DD4 = 1 << LPP_MOM_DD4
 LPP_WANT_DENSITY = LPP_WANT_DD2 | LPP_WANT_DD4
 LPP_WANT_MINUS_HIGH = (1 << LPP_MOM_MINUS10) | (1 << LPP_MOM_MINUS12)
+TEMPLATE_EB_SLOTS = 0x3FE   # the template slots the derived E/B curves read
 LPP_WANT_CROSS_B = 1 << 16
 KERNEL_KINDS = ["assign", "fft", "combine", "coeffs", "partner", "other"]
 
@@ -91,6 +92,7 @@ EXPORTS = {
                                       C.c_int, C.c_double, C.POINTER(C.c_void_p)]),
     "lpp_template_destroy": (None, [C.c_void_p]),
     "lpp_template_set_png": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double]),
+    "lpp_template_set_slots": (C.c_int, [C.c_void_p, C.c_uint]),
     "lpp_template_workspace_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "lpp_template_set_workspace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "lpp_convolve_template": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
@@ -370,8 +372,12 @@ class Template:
         """Spin-2 PNG response of the shape spectra (lpp_template_set_png); f_nl = 0: Gaussian."""
         _check(self.lib, self.lib.lpp_template_set_png(self.h, float(f_nl), float(db_ia), float(omega_m)))
 
+    def set_slots(self, mask: int):
+        """Output slots to compute (lpp_template_set_slots); the others come back as zeros."""
+        _check(self.lib, self.lib.lpp_template_set_slots(self.h, int(mask)))
+
     def __call__(self, params, out=None):
-        """params: torch float64 CUDA tensor [n, 6]; returns a [n, 12, nb] float64 CUDA tensor."""
+        """params: torch float64 CUDA tensor [n, 6]; returns a [n, LPP_N_MOMENTS, nb] float64 CUDA tensor."""
         import torch
         n = int(params.shape[0])
         if out is None:
@@ -382,7 +388,8 @@ class Template:
         return out
 
     def derived(self, params, ref=None, sigma=None, out=None):
-        """Native slots [n, 12, nb] (float64) and standardised derived curves [n, 8 * nb] (float32)."""
+        """Native slots [n, LPP_N_MOMENTS, nb] (float64) and standardised derived curves [n, 8 * nb]
+        (float32); the template's slot mask must hold TEMPLATE_EB_SLOTS."""
         import torch
         n = int(params.shape[0])
         if out is None:

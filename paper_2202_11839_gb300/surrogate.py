@@ -66,13 +66,16 @@ def unit_amplitude(params: np.ndarray) -> np.ndarray:
 
 
 class Emulator:
-    """Surrogate of one window (q table) and binning; see the module docstring."""
+    """Surrogate of one window (q table) and binning; see the module docstring.  The emulator
+    sets the template's slot mask to TEMPLATE_EB_SLOTS (the slots its curves read)."""
 
     def __init__(self, template: L.Template, volume: float, noise_g: float, cfg: TrainConfig | None = None,
                  device=None):
         import torch
         self.torch = torch
         self.t = template
+        # the curves read the cross, plus and minus slots up to L = 8: the template computes those alone
+        template.set_slots(L.TEMPLATE_EB_SLOTS)
         self.cfg = cfg or TrainConfig()
         if template.nb * 8 != 320:
             raise ValueError("the surrogate emulates 8 curves x 40 shells")

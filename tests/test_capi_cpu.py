@@ -120,6 +120,12 @@ def test_template_tables_build_on_host():
     assert lib.lpp_template_workspace_size(h, C.byref(sz)) == L.LPP_OK
     assert sz.value > 16 * 4096 * 8
     assert lib.lpp_convolve_template(h, None, 1, None, None) == L.LPP_ERR_INVALID_ARG
+    # slot masks: bits beyond the last slot are refused; the derived curves need slots 1..9
+    assert lib.lpp_template_set_slots(h, C.c_uint(1 << L.LPP_N_MOMENTS)) == L.LPP_ERR_INVALID_ARG
+    assert lib.lpp_template_set_slots(h, C.c_uint(L.TEMPLATE_EB_SLOTS & ~(1 << L.LPP_MOM_MINUS8))) == L.LPP_OK
+    one = C.c_void_p(8)   # never dereferenced: the mask check comes first
+    assert lib.lpp_convolve_template_eb(h, one, 1, one, one, None, None, None) == L.LPP_ERR_INVALID_ARG
+    assert lib.lpp_template_set_slots(h, C.c_uint(L.TEMPLATE_EB_SLOTS)) == L.LPP_OK
     lib.lpp_template_destroy(h)
     bad = s[::-1].copy()
     assert lib.lpp_template_create(dp(q), dp(bad), s.size, dp(e), 10, 0.0, C.byref(h)) == L.LPP_ERR_INVALID_ARG

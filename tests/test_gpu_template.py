@@ -42,6 +42,39 @@ def test_template_parity_fp64():
     tm.close()
 
 
+def test_template_slot_mask():
+    """lpp_template_set_slots: the masked-in slots are the full computation's, bit for bit, and
+    the others zero; the derived curves come out the same from the nine slots they read."""
+    import torch
+    from paper_2202_11839_gb300 import lpp as L
+    L.load_library()
+    q, s = _window_table()
+    edges = np.linspace(0.0, 0.2, 41)
+    params = torch.from_numpy(np.array([[1.3, 1.8, 0.82, 0.05, 0.2, 1.0], [0.4, 2.5, 0.7, -0.1, 0.15, 0.6]])).cuda()
+    tm = L.Template(q, s, edges, shot_plus=50.0)
+
+    def run(fn):
+        res = fn(params)
+        torch.cuda.synchronize()
+        return tuple(x.cpu().numpy() for x in res) if isinstance(res, tuple) else res.cpu().numpy()
+    derived = lambda p: tm.derived(p, ref=None, sigma=None)
+    full, eb_full = run(derived)
+    tm.set_slots(L.TEMPLATE_EB_SLOTS)
+    part, eb_part = run(derived)
+    for j in range(L.LPP_N_MOMENTS):
+        if (L.TEMPLATE_EB_SLOTS >> j) & 1:
+            np.testing.assert_array_equal(part[:, j], full[:, j])
+        else:
+            assert np.all(part[:, j] == 0.0) and np.any(full[:, j] != 0.0), j
+    np.testing.assert_array_equal(eb_part, eb_full)
+    tm.set_slots((1 << L.LPP_MOM_MINUS12) | 1)
+    only = run(tm)
+    np.testing.assert_array_equal(only[:, L.LPP_MOM_MINUS12], full[:, L.LPP_MOM_MINUS12])
+    np.testing.assert_array_equal(only[:, 0], full[:, 0])
+    assert np.all(only[:, 1:L.LPP_MOM_MINUS12] == 0.0)
+    tm.close()
+
+
 def test_template_empty_batch_and_bad_args():
     import ctypes as C
     from paper_2202_11839_gb300 import lpp as L
