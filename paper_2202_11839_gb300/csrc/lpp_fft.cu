@@ -68,8 +68,8 @@ __global__ void __launch_bounds__(PassShape<LOGN>::THREADS, sizeof(T) == 4 ? (LO
         }
         cs = 1;
     }
-    for (int i = tid; i < N; i += S::THREADS) tw[i] = twg[i];
     if constexpr (MODE == 0) {
+        for (int i = tid; i < N; i += S::THREADS) tw[i] = twg[i];
 #pragma unroll
         for (int k = 0; k < S::PER; ++k) {
             const int idx = tid + k * S::THREADS;
@@ -123,6 +123,9 @@ __global__ void __launch_bounds__(PassShape<LOGN>::THREADS, sizeof(T) == 4 ? (LO
                 live |= (hit ? 1u : 0u) << b;
             }
         }
+        // the twiddles are first read after the first stage's barrier: loaded here, after the
+        // plane test (a CTA of an unreached plane loads nothing) and beside the operand loads
+        for (int i = tid; i < N; i += S::THREADS) tw[i] = twg[i];
         fft_columns_io<T, LOGN, INV, S::IPT, LD>(
             tile, c, u, tw,
             [&](int b, int e) { return ((live >> b) & 1u) ? gp[(size_t)e * ES] : mk<T>((T)0, (T)0); },

@@ -194,6 +194,16 @@ __device__ __forceinline__ void stencil1(T u, int n, int P, int cells[3], T w[3]
     for (int k = 0; k < 3; ++k) cells[k] &= (n - 1);   // periodic wrap (n is a power of two)
 }
 
+// Fixed-point tiles: the units below keep every contribution within |x| <= 2^21 (a cell's
+// window bound is taken as at least kMinWindow particles), where adding 1.5 x 2^23 in FP32
+// leaves round-to-nearest-even(x) in the low mantissa bits.  fixed_round(a, b) is that
+// integer for the exact product a b: one FFMA and one integer subtraction, against the
+// quarter-rate conversion instruction.
+constexpr int kMinWindow = 512;
+__device__ __forceinline__ int fixed_round(float a, float b) {
+    return __float_as_int(fmaf(a, b, 12582912.0f)) - 0x4B400000;
+}
+
 // Scatter one particle's weights (stencil at offset `shift` cells) into the tile part `im`.
 // The loops run to the fixed bound 3 with a guard on P so the stencil stays in registers.
 template <typename T, bool FIXED>
@@ -222,8 +232,8 @@ __device__ __forceinline__ void scatter_one(T* tilef, int ld, int n, int P, T ux
                 if constexpr (FIXED) {
                     // va, vb arrive pre-scaled to the tile's fixed-point unit
                     int* ti = reinterpret_cast<int*>(tilef);
-                    atomicAdd(ti + idx + im, __float2int_rn((float)(va * ww)));
-                    if (two_fields) atomicAdd(ti + idx + 1, __float2int_rn((float)(vb * ww)));
+                    atomicAdd(ti + idx + im, fixed_round((float)va, (float)ww));
+                    if (two_fields) atomicAdd(ti + idx + 1, fixed_round((float)vb, (float)ww));
                 } else {
                     atomicAdd(tilef + idx + im, va * ww);
                     if (two_fields) atomicAdd(tilef + idx + 1, vb * ww);
@@ -259,8 +269,8 @@ __device__ __forceinline__ void scatter_two(T* t0, T* t1, int ld, int n, int P, 
                 const int idx = 2 * (cx[kx] * ld + line) + im;
                 const T ww = wyz * wx[kx];
                 if constexpr (FIXED) {
-                    atomicAdd(reinterpret_cast<int*>(t0) + idx, __float2int_rn((float)(v0 * ww)));
-                    atomicAdd(reinterpret_cast<int*>(t1) + idx, __float2int_rn((float)(v1 * ww)));
+                    atomicAdd(reinterpret_cast<int*>(t0) + idx, fixed_round((float)v0, (float)ww));
+                    atomicAdd(reinterpret_cast<int*>(t1) + idx, fixed_round((float)v1, (float)ww));
                 } else {
                     atomicAdd(t0 + idx, v0 * ww);
                     atomicAdd(t1 + idx, v1 * ww);
@@ -573,8 +583,9 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int slot, int 
     const T* vb_ptr = (!a.interlace && sl.vals_b) ? static_cast<const T*>(sl.vals_b) : nullptr;
     // fixed-point accumulation (FP32 channel slots): a cell sums at most wmax contributions
     // (particles of its 4 x 4 key-row window) of magnitude <= amax (the TSC/CIC weights are
-    // <= 1), so 2^30 / (wmax amax) units keep every cell and its rounding (<= wmax units, two
-    // sub-grid stencils) inside int32.  The tile takes it only
+    // <= 1), so 2^30 / (max(wmax, kMinWindow) amax) units keep every cell and its rounding
+    // (<= wmax units, two sub-grid stencils) inside int32 and every contribution within
+    // 2^21 units (fixed_round).  The tile takes it only
     // when that unit is at most 2^-16 of the rows' rms value, so that rounding each
     // contribution to the unit costs no more than the FP32 sums it replaces; otherwise float
     // atomics.
@@ -586,7 +597,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int slot, int 
             am = fmaxf(am, sl.amax_b[0]);
             rms = fminf(rms, sl.amax_b[1]);
         }
-        const float bound = (float)wmax * am;
+        const float bound = (float)max(wmax, kMinWindow) * am;
         if (bound == 0.f) {
             fixed = true;                        // every value is zero
         } else if (bound * (1.f / 1073741824.f) <= rms * (1.f / 65536.f)) {
@@ -599,12 +610,14 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int slot, int 
         // weight slots: a cell sums at most wmax_q contributions of source q, each at most
         // max |w_q| (times alpha for the randoms); the guard compares the unit with the smallest
         // nonzero contribution scale, so one heavy weight cannot make the unit coarse for the rest
-        float bound = 0.f, small = 3.0e38f;
+        float bound = 0.f, small = 3.0e38f, big = 0.f;
         for (int q = 0; q < sl.n_src && q < 2; ++q) {
             const float sc = sl.src[q].neg_alpha ? fabsf((float)alpha) : 1.f;
             bound += (float)(q == 0 ? wmax : wmax1) * __uint_as_float(sl.wb[q][0]) * sc;
             small = fminf(small, __uint_as_float(sl.wb[q][1]) * sc);
+            big = fmaxf(big, __uint_as_float(sl.wb[q][0]) * sc);
         }
+        bound = fmaxf(bound, (float)kMinWindow * big);   // every contribution within 2^21 units
         if (bound == 0.f) {
             fixed = true;
         } else if (bound * (1.f / 1073741824.f) <= small * (1.f / 65536.f)) {
@@ -832,7 +845,7 @@ __device__ __forceinline__ void fused_tile2(const FusedArgs<T>& a, int tile_y, i
     bool fixed = sizeof(T) == 4;
     float fs[2] = {1.f, 1.f}, fi[2] = {1.f, 1.f};
     for (int q = 0; q < 2 && fixed; ++q) {
-        const float bound = (float)wmax * bnd[2 * q];
+        const float bound = (float)max(wmax, kMinWindow) * bnd[2 * q];
         if (bound == 0.f) continue;
         if (bound * (1.f / 1073741824.f) <= bnd[2 * q + 1] * (1.f / 65536.f)) {
             fs[q] = 1073741824.f / bound;
