@@ -8,6 +8,7 @@
 
 #include "lpp_internal.h"
 #include "lpp_kernels.h"
+#include <nvtx3/nvToolsExt.h>
 
 using namespace lpp;
 
@@ -97,6 +98,19 @@ static bool two_slot_grid(lpp_plan_t p) {
     return !p->fp64 && p->d.interlace && (p->d.n == 256 || p->d.n == 512) && p->d.n / p->ftz <= 256 &&
            p->d.fused_slots != 1;
 }
+
+// Named host ranges around the steps of an estimate (NVTX): a timeline profiler shows each step
+// beside the kernels it enqueues; without a tool attached a range costs a few nanoseconds.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    void next(const char* name) {   // end this range and open the next step's
+        nvtxRangePop();
+        nvtxRangePushA(name);
+    }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 static lpp_status fail(lpp_plan_t p, lpp_status s, const std::string& msg) {
     if (p) p->err = msg;
@@ -550,7 +564,9 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
     nl = 0;
     plan->n_fused[0] = plan->n_fused[1] = 0;
 
+    NvtxRange r_est("lpp estimate");
     // 0. pencil sort of every catalogue (cell coordinates and weights in x-pencil key order)
+    NvtxRange r_step("lpp 0 sort and reach masks");
     const long long caps[3] = {std::max<long long>(1, plan->d.max_shapes), std::max<long long>(1, plan->d.max_density),
                                std::max<long long>(1, plan->d.max_randoms)};
     int* perm = (int*)(plan->ws + plan->off_perm);
@@ -645,6 +661,7 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         return (double)c / n;
     };
 
+    r_step.next("lpp 1 harmonic weights");
     // 1. sky frames, shears and harmonic weights of the shape catalogue (in sorted order)
     CoeffArgs<T> ca;
     memset(&ca, 0, sizeof(ca));
@@ -800,6 +817,7 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
     double shell_modes = 0.0;
     for (int b = 0; b < nb; ++b) shell_modes += (double)plan->n_modes[b];
 
+    r_step.next("lpp 2 partner fields");
     // 2. partner fields: G1, G2 (shapes) and D = density - alpha randoms
     const int il = plan->d.interlace;
     const int dens_cat = plan->cat[LPP_DENSITY].set ? LPP_DENSITY : LPP_SHAPES;
@@ -888,6 +906,7 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         if (tm) tm->end(KK_PARTNER, st, shell_modes * sizeof(c2<T>) * (pgrids + plan->n_partner));
     }
 
+    r_step.next("lpp 3 channel batches");
     // 3. channel fields, a batch of grids at a time: the tensor channels (coefficient rows of
     // the shape catalogue), then the density multipole channels (harmonic weights of the density
     // catalogue and the randoms); a batch never mixes the two
@@ -991,6 +1010,7 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         if (tm) tm->end(KK_COMBINE, st, shell_modes * sizeof(c2<T>) * (ngr + (cb.has_d ? 1 : 0) + (cb.has_g ? 2 : 0)));
     }
 
+    r_step.next("lpp 4 results");
     // 4. results to the host
     LPP_CUDA(cudaMemcpyAsync(host_out, out, (size_t)plan->out_rows * nb * 2 * sizeof(double), cudaMemcpyDeviceToHost,
                              st));
@@ -1103,6 +1123,7 @@ extern "C" lpp_status lpp_multipoles(lpp_plan_t plan, lpp_result* res) {
 template <typename T>
 static lpp_status run_window(lpp_plan_t plan, int nb, const double* s_edges, double* q, double* s_mean,
                              long long* n_points, double* norm_out) {
+    NvtxRange r_win("lpp window multipoles");
     const int n = plan->n;
     const size_t n3 = (size_t)n * n * n;
     const double h = plan->box / n;
@@ -1338,6 +1359,7 @@ static lpp_status batch_fail(lpp_batch_t b, lpp_status s, const std::string& m) 
 
 // All mocks, each on its plan's batch stream (mocks of one plan in order, plans concurrently).
 static lpp_status batch_enqueue(lpp_batch_t b, cudaStream_t root) {
+    NvtxRange r_batch("lpp batch");
     LPP_BCUDA(cudaEventRecord(b->start, root));
     for (size_t p = 0; p < b->plans.size(); ++p) LPP_BCUDA(cudaStreamWaitEvent(b->streams[p], b->start, 0));
     b->n_launch = 0;

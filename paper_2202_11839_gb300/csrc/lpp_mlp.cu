@@ -11,6 +11,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <utility>
 #include <vector>
 
 #include "lpp_internal.h"
@@ -458,6 +459,82 @@ extern "C" lpp_status lpp_surrogate_set_workspace(lpp_surrogate_t s, void* dev, 
     AdamArgs a = adam_args(s);
     k_refresh<<<dim3(64, kLayers), 256, 0, st>>>(a);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return LPP_ERR_CUDA;
+    return LPP_OK;
+}
+
+// Training state (checkpoint): a 16-byte header (magic, version, Adam step), then per layer
+// the FP32 master W (rows padded to kInPad, the device layout), its Adam moments m and v, the
+// bias and its m and v.  The BF16 copies are derived and rebuilt on load.
+constexpr unsigned kStateMagic = 0x5350504Cu;   // "LPPS"
+constexpr unsigned kStateVersion = 1u;
+
+static size_t state_bytes() {
+    size_t b = 16;
+    for (int l = 0; l < kLayers; ++l) b += (size_t)3 * ((size_t)kOut[l] * kInPad[l] + kOut[l]) * 4;
+    return b;
+}
+
+extern "C" lpp_status lpp_surrogate_state_size(lpp_surrogate_t s, size_t* bytes) {
+    if (!s || !bytes) return LPP_ERR_INVALID_ARG;
+    *bytes = state_bytes();
+    return LPP_OK;
+}
+
+// The state's device arrays in file order: {offset, bytes} per layer.
+static void state_parts(lpp_surrogate_t s, std::vector<std::pair<size_t, size_t>>& parts) {
+    parts.clear();
+    for (int l = 0; l < kLayers; ++l) {
+        const size_t nw = (size_t)kOut[l] * kInPad[l] * 4, nb = (size_t)kOut[l] * 4;
+        parts.push_back({s->w[l], nw});
+        parts.push_back({s->mw[l], nw});
+        parts.push_back({s->vw[l], nw});
+        parts.push_back({s->b[l], nb});
+        parts.push_back({s->mb[l], nb});
+        parts.push_back({s->vb[l], nb});
+    }
+}
+
+extern "C" lpp_status lpp_surrogate_save_state(lpp_surrogate_t s, void* host, size_t bytes, void* stream) {
+    if (!s || !s->ws || !host || bytes < state_bytes()) return LPP_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char* p = (unsigned char*)host;
+    const unsigned hdr[2] = {kStateMagic, kStateVersion};
+    memcpy(p, hdr, 8);
+    const long long step = s->step;
+    memcpy(p + 8, &step, 8);
+    size_t o = 16;
+    std::vector<std::pair<size_t, size_t>> parts;
+    state_parts(s, parts);
+    for (const auto& q : parts) {
+        if (cudaMemcpyAsync(p + o, s->ws + q.first, q.second, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return LPP_ERR_CUDA;
+        o += q.second;
+    }
+    return cudaStreamSynchronize(st) == cudaSuccess ? LPP_OK : LPP_ERR_CUDA;
+}
+
+extern "C" lpp_status lpp_surrogate_load_state(lpp_surrogate_t s, const void* host, size_t bytes, void* stream) {
+    if (!s || !s->ws || !host || bytes < state_bytes()) return LPP_ERR_INVALID_ARG;
+    const unsigned char* p = (const unsigned char*)host;
+    unsigned hdr[2];
+    memcpy(hdr, p, 8);
+    if (hdr[0] != kStateMagic || hdr[1] != kStateVersion) return LPP_ERR_INVALID_ARG;
+    long long step = 0;
+    memcpy(&step, p + 8, 8);
+    if (step < 0) return LPP_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t o = 16;
+    std::vector<std::pair<size_t, size_t>> parts;
+    state_parts(s, parts);
+    for (const auto& q : parts) {
+        if (cudaMemcpyAsync(s->ws + q.first, p + o, q.second, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return LPP_ERR_CUDA;
+        o += q.second;
+    }
+    AdamArgs a = adam_args(s);
+    k_refresh<<<dim3(64, kLayers), 256, 0, st>>>(a);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return LPP_ERR_CUDA;
+    s->step = step;
     return LPP_OK;
 }
 

@@ -103,6 +103,9 @@ EXPORTS = {
     "lpp_surrogate_workspace_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "lpp_surrogate_set_workspace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_float), C.c_void_p]),
     "lpp_surrogate_get_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_void_p]),
+    "lpp_surrogate_state_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "lpp_surrogate_save_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "lpp_surrogate_load_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "lpp_surrogate_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_float,
                                       C.c_void_p, C.c_void_p]),
     "lpp_surrogate_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_float),
@@ -466,6 +469,21 @@ class Surrogate:
         _check(self.lib, self.lib.lpp_surrogate_get_params(self.h, out.ctypes.data_as(C.POINTER(C.c_float)),
                                                            C.c_void_p(self.stream.cuda_stream)))
         return out
+
+    def save_state(self) -> np.ndarray:
+        """The training state (lpp_surrogate_save_state) as a uint8 array."""
+        sz = C.c_size_t()
+        _check(self.lib, self.lib.lpp_surrogate_state_size(self.h, C.byref(sz)))
+        buf = np.zeros(sz.value, dtype=np.uint8)
+        _check(self.lib, self.lib.lpp_surrogate_save_state(self.h, C.c_void_p(buf.ctypes.data), C.c_size_t(sz.value),
+                                                           C.c_void_p(self.stream.cuda_stream)))
+        return buf
+
+    def load_state(self, state):
+        """Restore a state from save_state (lpp_surrogate_load_state)."""
+        buf = np.ascontiguousarray(state, dtype=np.uint8)
+        _check(self.lib, self.lib.lpp_surrogate_load_state(self.h, C.c_void_p(buf.ctypes.data), C.c_size_t(buf.size),
+                                                           C.c_void_p(self.stream.cuda_stream)))
 
     def train(self, x, y, schedule, lr: float, losses=None):
         """x, y: float32 CUDA tensors; schedule: int32 CUDA tensor [n_steps * batch]."""

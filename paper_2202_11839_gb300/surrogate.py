@@ -17,6 +17,7 @@ seeded) and moves arrays.
 """
 from __future__ import annotations
 
+import json
 import math
 from dataclasses import dataclass, field
 
@@ -142,7 +143,17 @@ class Emulator:
         native = self.t(torch.from_numpy(unit_amplitude(theta)).to(self.device))
         return th, self.net.targets(th, native)
 
-    def train(self):
+    def _fingerprint(self) -> str:
+        c = self.cfg
+        return json.dumps([c.n_train, c.batch, list(c.epochs), list(c.lrs), c.base_nodes, c.seed])
+
+    def train(self, checkpoint: str | None = None, resume: str | None = None, phases: int | None = None):
+        """Train on cfg.n_train Latin-hypercube templates, one Adam schedule per learning-rate
+        phase.  checkpoint: after every phase, write the network's training state
+        (lpp_surrogate_save_state), the next phase, the schedule generator's state and the
+        losses so far to this .npz file.  resume: continue from such a file (the same
+        TrainConfig; the training set is regenerated from its seed).  phases: stop after this
+        many phases in total (None: all)."""
         import time
         torch = self.torch
         cfg = self.cfg
@@ -155,16 +166,32 @@ class Emulator:
         rng = np.random.default_rng(cfg.seed + 1000)
         steps_per_epoch = cfg.n_train // cfg.batch
         losses = []
-        for epochs, lr in zip(cfg.epochs, cfg.lrs):
+        first = 0
+        if resume is not None:
+            ck = np.load(resume, allow_pickle=False)
+            if str(ck["config"]) != self._fingerprint():
+                raise ValueError("checkpoint was written for another TrainConfig")
+            self.net.load_state(ck["state"])
+            rng.bit_generator.state = json.loads(str(ck["rng"]))
+            first = int(ck["phase"])
+            if ck["losses"].size:
+                losses.append(torch.from_numpy(ck["losses"]).to(self.device))
+        last = len(cfg.epochs) if phases is None else min(phases, len(cfg.epochs))
+        for ph in range(first, last):
+            epochs, lr = cfg.epochs[ph], cfg.lrs[ph]
             sched = np.concatenate([rng.permutation(cfg.n_train)[: steps_per_epoch * cfg.batch]
                                     for _ in range(epochs)]).astype(np.int32)
             sd = torch.from_numpy(sched).to(self.device)
             ls = torch.zeros(epochs * steps_per_epoch, dtype=torch.float64, device=self.device)
             self.net.train(x, y, sd, lr, ls)
             losses.append(ls)
+            if checkpoint is not None:
+                np.savez(checkpoint, state=self.net.save_state(), phase=np.int64(ph + 1),
+                         rng=np.array(json.dumps(rng.bit_generator.state)), config=np.array(self._fingerprint()),
+                         losses=torch.cat(losses).cpu().numpy() if losses else np.zeros(0))
         torch.cuda.synchronize(self.device)
         t2 = time.perf_counter()
-        self.losses = torch.cat(losses).cpu().numpy()
+        self.losses = torch.cat(losses).cpu().numpy() if losses else np.zeros(0)
         self.data_seconds, self.train_seconds = t1 - t0, t2 - t1
         return t1 - t0, t2 - t1
 

@@ -246,3 +246,61 @@ def test_emulator_accuracy_and_speed():
     want = em.plain(torch.from_numpy(out_box).cuda()).double().cpu().numpy()
     np.testing.assert_array_equal(got, want)
     tm.close()
+
+
+def test_state_checkpoint_round_trip():
+    """lpp_surrogate_save_state / load_state: a network loaded from a checkpoint continues the
+    training as the saved one does (same Adam step count and moments), and a buffer with
+    another magic number is refused."""
+    import torch
+    L, net, layers, x, y, t = _setup(batch=64, seed=3)
+    rng = np.random.default_rng(12)
+    sched = lambda: t(rng.integers(0, 64, 64 * 20).astype(np.int32))
+    net.train(t(x), t(y), sched(), 1e-3)
+    state = net.save_state()
+    other = L.Surrogate(L.flatten_params(S.surrogate_init(9)), batch=64)
+    other.load_state(state)
+    np.testing.assert_array_equal(other.params(), net.params())
+    s2 = sched()
+    net.train(t(x), t(y), s2, 1e-3)
+    other.train(t(x), t(y), s2, 1e-3)
+    a, b = net.params(), other.params()
+    assert np.max(np.abs(a - b)) <= 1e-6 * np.max(np.abs(a))
+    # a fresh network (step 0, zero moments) trained on the same schedule ends elsewhere
+    fresh = L.Surrogate(L.flatten_params(S.surrogate_init(9)), batch=64)
+    fresh.load_state(state)
+    bad = state.copy()
+    bad[0] ^= 0xFF
+    with pytest.raises(L.LppError):
+        fresh.load_state(bad)
+    with pytest.raises(L.LppError):
+        fresh.load_state(state[:-4])
+    for m in (net, other, fresh):
+        m.close()
+
+
+def test_emulator_training_resumes_from_a_checkpoint(tmp_path):
+    """Emulator.train(checkpoint=...) after one phase, then train(resume=...) in a new
+    emulator, ends where an uninterrupted training ends (the schedules continue from the saved
+    generator state; the network from the saved Adam state)."""
+    from paper_2202_11839_gb300 import surrogate as SG
+    tm = _template()
+    cfg = SG.TrainConfig(n_train=2048, n_test=64, batch=256, epochs=(3, 3), lrs=(1e-3, 3e-4), base_nodes=4)
+    whole = SG.Emulator(tm, SG.survey_volume(), SURVEY_NOISE_G, cfg)
+    whole.train()
+    path = str(tmp_path / "emu.npz")
+    first = SG.Emulator(tm, SG.survey_volume(), SURVEY_NOISE_G, cfg)
+    first.train(checkpoint=path, phases=1)
+    second = SG.Emulator(tm, SG.survey_volume(), SURVEY_NOISE_G, cfg)
+    second.train(resume=path)
+    a, b = whole.net.params(), second.net.params()
+    assert second.losses.size == whole.losses.size
+    assert np.max(np.abs(a - b)) <= 1e-5 * np.max(np.abs(a))
+    other = SG.Emulator(tm, SG.survey_volume(), SURVEY_NOISE_G, SG.TrainConfig(n_train=4096, epochs=(3, 3),
+                                                                               lrs=(1e-3, 3e-4), base_nodes=4))
+    with pytest.raises(ValueError):
+        other.train(resume=path)
+    for e in (whole, first, second, other):
+        if e.net is not None:
+            e.net.close()
+    tm.close()
