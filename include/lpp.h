@@ -43,7 +43,9 @@ typedef enum {
     LPP_ERR_NOT_READY = 3,    /* workspace or required catalogue not supplied yet              */
     LPP_ERR_WORKSPACE = 4,    /* workspace smaller than lpp_plan_workspace_size()              */
     LPP_ERR_UNSUPPORTED = 5,  /* grid size or option combination not built                      */
-    LPP_ERR_DOMAIN = 6        /* a particle lies outside the box, on the observer or the pole  */
+    LPP_ERR_DOMAIN = 6,       /* a particle lies outside the box, on the observer or the pole  */
+    LPP_ERR_BOUNDS = 7        /* checking builds (liblpp_check.so, LPP_CHECK): a device index fell
+                                 outside its buffer; the access was skipped, the results are void */
 } lpp_status;
 
 /* assignment schemes: the exponent p of the window sinc^p */

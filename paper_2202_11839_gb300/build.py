@@ -17,6 +17,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblpp.so")
+# the bounds-checking build (-DLPP_CHECK): device indices checked, a violation recorded as
+# LPP_ERR_BOUNDS instead of an access; selected at load time by LPP_CHECK=1
+BUILD_CHECK = os.path.join(PKG, "_build_check")
+LIB_CHECK = os.path.join(PKG, "liblpp_check.so")
 SOURCES = ["lpp_capi.cu", "lpp_tables.cu", "lpp_assign.cu", "lpp_fft.cu", "lpp_combine.cu", "lpp_static.cu", "lpp_tiles.cu", "lpp_window.cu", "lpp_template.cu", "lpp_mlp.cu", "lpp_pairs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -28,8 +32,8 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build liblpp")
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+def _compile(src: str, extra: list[str], bdir: str = BUILD) -> str:
+    obj = os.path.join(bdir, src.replace(".cu", ".o"))
     cmd = [nvcc(), *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
            "-I", CSRC, "-c", os.path.join(CSRC, src), "-o", obj, *extra]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -38,21 +42,23 @@ def _compile(src: str, extra: list[str]) -> str:
     return obj
 
 
-def build(verbose: bool = False, extra: list[str] | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    extra = list(extra or [])
+def build(verbose: bool = False, extra: list[str] | None = None, check: bool = False) -> str:
+    bdir, lib = (BUILD_CHECK, LIB_CHECK) if check else (BUILD, LIB)
+    os.makedirs(bdir, exist_ok=True)
+    extra = list(extra or []) + (["-DLPP_CHECK"] if check else [])
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
-    tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda s: _compile(s, extra, bdir), SOURCES))
+    tmp = lib + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
-        print(f"built {LIB}")
-    return LIB
+        print(f"built {lib}")
+    return lib
 
 
 if __name__ == "__main__":
-    build(verbose=True, extra=sys.argv[1:])
+    args = sys.argv[1:]
+    build(verbose=True, extra=[a for a in args if a != "--check"], check="--check" in args)

@@ -206,6 +206,7 @@ __global__ void __launch_bounds__(256) k_coeffs(CoeffArgs<T> a) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.count;
          i += (long long)gridDim.x * blockDim.x) {
         const long long si = a.perm ? (long long)a.perm[i] : i;  // input index of output particle i
+        if (!LPP_IN_BOUNDS(si >= 0 && si < a.count, a.err)) continue;
         T xl[3];
         unit_los(a.pos, a.count, si, a.observer, xl, a.err);
         T xg[3] = {(T)a.los_global[0], (T)a.los_global[1], (T)a.los_global[2]};

@@ -752,6 +752,7 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
     cb.nky = plan->nky;
     cb.nzi = plan->nzi;
     cb.out = out;
+    cb.err = err;
     cb.items = plan->items.empty() ? nullptr : (const int4*)(plan->ws + plan->off_items);
     cb.n_items = (int)plan->items.size();
     const int n_ch = (int)plan->channels.size();
@@ -780,6 +781,7 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
     fa.pmask = pmask;
     fa.skip_empty = 1;
     fa.pstat = (int*)(plan->ws + plan->off_pstat);
+    fa.err = err;
     // harmonic weights of the density multipole channels: line of sight from the observer
     // (or the global direction when the estimator uses one)
     for (int a = 0; a < 3; ++a) {
@@ -883,6 +885,7 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         { lpp_status s0 = assign_fused(parts); if (s0 != LPP_OK) return s0; }
         FftGeom gp = geom;
         gp.pmask = pmask;
+        gp.err = err;
         gp.q_max = plan->thr[nb];
         double fr = 0.0;
         for (int i = 0; i < fa.n_slots; ++i) {
@@ -998,6 +1001,7 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
         fa.tranges = nullptr;
         FftGeom gc = geom;
         gc.pmask = pmask;
+        gc.err = err;
         gc.q_max = plan->thr[nb];
         for (int i = 0; i < ngr; ++i) gc.gmask[i] = bits;
         gc.yread_frac = (float)plane_frac(bits);
@@ -1024,6 +1028,8 @@ static lpp_status finish(lpp_plan_t plan, const double* h_out, const double* h_s
                          lpp_result* res) {
     const int nb = plan->nb;
     const int n_ch = (int)plan->channels.size();
+    if (h_err & ERRF_BOUNDS)
+        return fail(plan, LPP_ERR_BOUNDS, "a device index fell outside its buffer (checking build); access skipped");
     if (h_err) {
         std::string msg = "particle outside the domain:";
         if (h_err & ERRF_DOMAIN) msg += " outside the box";
@@ -1174,10 +1180,13 @@ static lpp_status run_window(lpp_plan_t plan, int nb, const double* s_edges, dou
                                    (T*)(plan->ws + plan->off_su[LPP_RANDOMS]),
                                    (T*)(plan->ws + plan->off_sw[LPP_RANDOMS]), nullptr, err, st));
     // forward transforms keep every frequency; the inverse keeps the separations of the shells
-    const FftGeom gfull = fft_geometry(n, n / 2 - 1, n / 2);
-    const FftGeom gs = fft_geometry(n, ns_pos, ns_neg);
+    FftGeom gfull = fft_geometry(n, n / 2 - 1, n / 2);
+    FftGeom gs = fft_geometry(n, ns_pos, ns_neg);
+    gfull.err = err;
+    gs.err = err;
     FusedArgs<T> fa;
     memset(&fa, 0, sizeof(fa));
+    fa.err = err;
     fa.cat[LPP_RANDOMS].su = plan->ws + plan->off_su[LPP_RANDOMS];
     fa.cat[LPP_RANDOMS].sw = plan->ws + plan->off_sw[LPP_RANDOMS];
     fa.cat[LPP_RANDOMS].off = (const int*)(plan->ws + plan->off_koff[LPP_RANDOMS]);
@@ -1267,6 +1276,8 @@ static lpp_status run_window(lpp_plan_t plan, int nb, const double* s_edges, dou
     LPP_CUDA(cudaMemcpyAsync(h_sums, sums, sizeof(h_sums), cudaMemcpyDeviceToHost, st));
     LPP_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     LPP_CUDA(cudaStreamSynchronize(st));
+    if (h_err & ERRF_BOUNDS)
+        return fail(plan, LPP_ERR_BOUNDS, "a device index fell outside its buffer (checking build); access skipped");
     if (h_err) return fail(plan, LPP_ERR_DOMAIN, "random outside the box");
     const double alpha = (de.set && h_sums[SUM_W_RAND] != 0.0) ? h_sums[SUM_W_DENS] / h_sums[SUM_W_RAND] : 1.0;
     const double I = alpha * h_sums[SUM_NW2_RAND];
@@ -1319,6 +1330,7 @@ extern "C" const char* lpp_status_string(lpp_status s) {
         case LPP_ERR_WORKSPACE: return "workspace too small";
         case LPP_ERR_UNSUPPORTED: return "unsupported";
         case LPP_ERR_DOMAIN: return "particle outside the domain";
+        case LPP_ERR_BOUNDS: return "device index out of bounds (checking build)";
     }
     return "unknown status";
 }

@@ -188,6 +188,10 @@ __global__ void __launch_bounds__(COMPACT ? 256 : 1024, COMPACT ? 3 : 1) k_combi
         if (own_pair) {
             c.im = ((long long)z * n + y) * n + x;
             c.ip = ((long long)zp * n + yp) * n + xp;
+            const long long n3 = (long long)n * n * n;
+            if (!LPP_IN_BOUNDS(c.im >= 0 && c.im < n3 && c.ip >= 0 && c.ip < n3 && bin < nb, a.err)) own_pair = false;
+        }
+        if (own_pair) {
             c.iw_m = iw[x] * iw[y] * iw[z];
             c.iw_p = iw[xp] * iw[yp] * iw[zp];
             c.ph_m = cmul<T>(cmul<T>(ph[x], ph[y]), ph[z]);

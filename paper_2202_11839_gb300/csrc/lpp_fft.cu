@@ -52,6 +52,7 @@ __device__ __forceinline__ void pencil_tile(c2<T>* grid, const c2<T>* twg, c2<T>
     const int o = tile_id / g.ntx;
     const int i = tile_id - o * g.ntx;
     const int x0 = (g.ntx == N / W || i < g.nlo) ? i * W : N - (g.ntx - i) * W;
+    if (!LPP_IN_BOUNDS(o >= 0 && o < (MODE == 1 ? N : g.nky) && x0 >= 0 && x0 + W <= N, g.err)) return;
     if (MODE == 1) {
         base += (size_t)o * N2 + x0;  // o = z
     } else {
@@ -123,6 +124,7 @@ __global__ void __launch_bounds__(PassShape<LOGN>::THREADS, sizeof(T) == 4 ? (LO
         for (int i = tid; i < N; i += S::THREADS) tw[i] = twg[i];
         const int ty = tile_id & (N / W - 1);
         const int z = tile_id >> (LOGN - S::LOGW);
+        if (!LPP_IN_BOUNDS(z < N, g.err)) return;
         c2<T>* base = grid + (size_t)z * N2 + (size_t)ty * W * N;
 #pragma unroll
         for (int k = 0; k < S::PER; ++k) {

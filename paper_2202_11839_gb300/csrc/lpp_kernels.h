@@ -69,6 +69,7 @@ struct FftGeom {
     // optional per-pencil reach [3][n*n] bytes (role, z * n + y): the y pass reads zeros for
     // x pencils that no particle of the grid's roles reaches (the fused pass stores nothing there)
     const unsigned char* plive = nullptr;
+    int* err = nullptr;   // ERRF_BOUNDS of LPP_CHECK builds
 };
 
 int fft_tile_width(int n);
@@ -129,7 +130,20 @@ enum SumSlot {
 };
 
 // error flag bits
-enum { ERRF_DOMAIN = 1, ERRF_POLE = 2, ERRF_OBSERVER = 4 };
+enum { ERRF_DOMAIN = 1, ERRF_POLE = 2, ERRF_OBSERVER = 4, ERRF_BOUNDS = 8 };
+
+// Bounds checks of LPP_CHECK builds (build.build(check=True), liblpp_check.so): there a false
+// condition records ERRF_BOUNDS in *err (the estimate then fails with LPP_ERR_BOUNDS) and the
+// caller skips the access instead of faulting; in other builds the condition is not evaluated.
+#ifdef LPP_CHECK
+__device__ __forceinline__ bool lpp_in_bounds(bool ok, int* err) {
+    if (!ok && err) atomicOr(err, (int)ERRF_BOUNDS);
+    return ok;
+}
+#define LPP_IN_BOUNDS(cond, err) ::lpp::lpp_in_bounds((cond), (err))
+#else
+#define LPP_IN_BOUNDS(cond, err) true
+#endif
 
 template <typename T>
 cudaError_t launch_coeffs(const CoeffArgs<T>& a, cudaStream_t st);
@@ -228,6 +242,7 @@ struct FusedArgs {
     const int* tranges;                  // two-slot launches: per-tile range records, or null
     int* work;                           // one-slot launches over trows: item counter, zeroed
                                          // before the launch (dynamic schedule), or null
+    int* err;                            // ERRF_BOUNDS of LPP_CHECK builds
     int* pstat;                          // optional tile counters: [0] two-slot fixed-point tiles,
                                          // [1] two-slot float tiles, [2] one-slot fixed-point
                                          // tiles, [3] one-slot float tiles (FP32 channel slots)
@@ -301,6 +316,7 @@ struct CombineArgs {
     // of the modes inside the last shell, 32 at a time; null: one CTA pass per whole row
     const int4* items;
     int n_items;
+    int* err;              // ERRF_BOUNDS of LPP_CHECK builds
 };
 
 template <typename T>

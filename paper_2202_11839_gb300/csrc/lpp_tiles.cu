@@ -127,11 +127,12 @@ __global__ void __launch_bounds__(256) k_pencil_scatter(const T* __restrict__ po
                                                         long long count, long long cap, T ih, T ox, T oy, T oz,
                                                         const int* __restrict__ key, int* __restrict__ cursor,
                                                         T* __restrict__ su, T* __restrict__ sw,
-                                                        int* __restrict__ perm) {
+                                                        int* __restrict__ perm, int* err) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
          i += (long long)gridDim.x * blockDim.x) {
         const int k = key[i];
         const int j = atomicAdd(cursor + k, 1);
+        if (!LPP_IN_BOUNDS(j >= 0 && j < cap, err)) continue;
         su[j] = (pos[i] - ox) * ih;
         su[cap + j] = (pos[count + i] - oy) * ih;
         su[2 * cap + j] = (pos[2 * count + i] - oz) * ih;
@@ -161,7 +162,7 @@ cudaError_t launch_pencil_sort(const T* pos, const T* w, long long count, long l
     k_scan_add<<<nb, 256, 0, st>>>(bsum, nk, off, cursor);
     if (count > 0)
         k_pencil_scatter<T><<<(int)blocks, 256, 0, st>>>(pos, w, count, cap, ih, ox, oy, oz, key, cursor, su, sw,
-                                                         perm);
+                                                         perm, err);
     return cudaGetLastError();
 }
 
@@ -208,7 +209,8 @@ __device__ __forceinline__ int fixed_round(float a, float b) {
 // The loops run to the fixed bound 3 with a guard on P so the stencil stays in registers.
 template <typename T, bool FIXED>
 __device__ __forceinline__ void scatter_one(T* tilef, int ld, int n, int P, T ux, T uy, T uz, T shift, int y0,
-                                            int z0, int ty, int tz, T va, T vb, bool two_fields, int im) {
+                                            int z0, int ty, int tz, T va, T vb, bool two_fields, int im,
+                                            int* err = nullptr) {
     int cx[3], cy[3], cz[3];
     T wx[3], wy[3], wz[3];
     stencil1<T>(ux - shift, n, P, cx, wx);
@@ -228,6 +230,7 @@ __device__ __forceinline__ void scatter_one(T* tilef, int ld, int n, int P, T ux
             for (int kx = 0; kx < 3; ++kx) {
                 if (kx >= P) continue;
                 const int idx = 2 * (cx[kx] * ld + line);
+                if (!LPP_IN_BOUNDS(cx[kx] >= 0 && cx[kx] < n && line >= 0 && line < ty * tz, err)) continue;
                 const T ww = wyz * wx[kx];
                 if constexpr (FIXED) {
                     // va, vb arrive pre-scaled to the tile's fixed-point unit
@@ -247,7 +250,7 @@ __device__ __forceinline__ void scatter_one(T* tilef, int ld, int n, int P, T ux
 // is added to both tiles (values v0, v1 already in the tiles' units).
 template <typename T, bool FIXED>
 __device__ __forceinline__ void scatter_two(T* t0, T* t1, int ld, int n, int P, T ux, T uy, T uz, T shift, int y0,
-                                            int z0, int ty, int tz, T v0, T v1, int im) {
+                                            int z0, int ty, int tz, T v0, T v1, int im, int* err = nullptr) {
     int cx[3], cy[3], cz[3];
     T wx[3], wy[3], wz[3];
     stencil1<T>(ux - shift, n, P, cx, wx);
@@ -267,6 +270,7 @@ __device__ __forceinline__ void scatter_two(T* t0, T* t1, int ld, int n, int P, 
             for (int kx = 0; kx < 3; ++kx) {
                 if (kx >= P) continue;
                 const int idx = 2 * (cx[kx] * ld + line) + im;
+                if (!LPP_IN_BOUNDS(cx[kx] >= 0 && cx[kx] < n && line >= 0 && line < ty * tz, err)) continue;
                 const T ww = wyz * wx[kx];
                 if constexpr (FIXED) {
                     atomicAdd(reinterpret_cast<int*>(t0) + idx, fixed_round((float)v0, (float)ww));
@@ -553,6 +557,9 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int slot, int 
                                     wmax, &wmax1);
     __syncthreads();
     const int nr = n_ranges;
+    if (!LPP_IN_BOUNDS(nr >= 0 && nr <= S::MAXR && tile_y >= 0 && tile_y < N / TY && tile_z >= 0 && tile_z < N / TZ,
+                       a.err))
+        return;   // CTA-uniform
     const int total = r_pref[nr];
     // kept x frequencies of a pencil: indices 0..nk_pos and n-nk_neg..n-1; LPL consecutive
     // threads write one pencil (coalesced along x)
@@ -636,6 +643,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int slot, int 
         const T* su = static_cast<const T*>(cat.su);
         const T* vals = src.vals ? static_cast<const T*>(src.vals) : static_cast<const T*>(cat.sw);
         const long long cap = cat.cap;
+        if (!LPP_IN_BOUNDS(j >= 0 && j < cap, a.err)) continue;
         const T ux = su[j], uy = su[cap + j], uz = su[2 * cap + j];
         const T base = vals[j];
         T va = base;
@@ -669,18 +677,18 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int slot, int 
             const T sh0 = odd ? (T)0.5 : (T)0, sh1 = odd ? (T)0 : (T)0.5;
             if (fixed) {
                 va *= fscale;
-                scatter_one<T, true>(tilef, LD, N, P, ux, uy, uz, sh0, y0, z0, TY, TZ, va, (T)0, false, odd);
-                scatter_one<T, true>(tilef, LD, N, P, ux, uy, uz, sh1, y0, z0, TY, TZ, va, (T)0, false, 1 - odd);
+                scatter_one<T, true>(tilef, LD, N, P, ux, uy, uz, sh0, y0, z0, TY, TZ, va, (T)0, false, odd, a.err);
+                scatter_one<T, true>(tilef, LD, N, P, ux, uy, uz, sh1, y0, z0, TY, TZ, va, (T)0, false, 1 - odd, a.err);
             } else {
-                scatter_one<T, false>(tilef, LD, N, P, ux, uy, uz, sh0, y0, z0, TY, TZ, va, (T)0, false, odd);
-                scatter_one<T, false>(tilef, LD, N, P, ux, uy, uz, sh1, y0, z0, TY, TZ, va, (T)0, false, 1 - odd);
+                scatter_one<T, false>(tilef, LD, N, P, ux, uy, uz, sh0, y0, z0, TY, TZ, va, (T)0, false, odd, a.err);
+                scatter_one<T, false>(tilef, LD, N, P, ux, uy, uz, sh1, y0, z0, TY, TZ, va, (T)0, false, 1 - odd, a.err);
             }
         } else if (fixed) {
             va *= fscale;
             vb *= fscale;
-            scatter_one<T, true>(tilef, LD, N, P, ux, uy, uz, (T)0, y0, z0, TY, TZ, va, vb, two, 0);
+            scatter_one<T, true>(tilef, LD, N, P, ux, uy, uz, (T)0, y0, z0, TY, TZ, va, vb, two, 0, a.err);
         } else {
-            scatter_one<T, false>(tilef, LD, N, P, ux, uy, uz, (T)0, y0, z0, TY, TZ, va, vb, two, 0);
+            scatter_one<T, false>(tilef, LD, N, P, ux, uy, uz, (T)0, y0, z0, TY, TZ, va, vb, two, 0, a.err);
         }
     }
     __syncthreads();
@@ -822,6 +830,9 @@ __device__ __forceinline__ void fused_tile2(const FusedArgs<T>& a, int tile_y, i
     const int* r_pref = rec ? rec + kRecPref : r_pref_s;
     const int nr = rec ? rec[0] : n_ranges_s;
     const int wmax = rec ? rec[1] : wmax_s;
+    if (!LPP_IN_BOUNDS(nr >= 0 && nr <= S::MAXR && tile_y >= 0 && tile_y < N / TY && tile_z >= 0 && tile_z < N / TZ,
+                       a.err))
+        return;   // CTA-uniform; the tiles stay as they are (zero)
     const int total = r_pref[nr];
     const int half = tid / S::THREADS, th = tid - half * S::THREADS;
     const FusedSlot& sh = half ? s1 : s0;
@@ -871,16 +882,17 @@ __device__ __forceinline__ void fused_tile2(const FusedArgs<T>& a, int tile_y, i
     for (int t = tid; t < total; t += NT) {
         while (r + 1 < nr && r_pref[r + 1] <= t) ++r;
         const int j = r_begin[r] + (t - r_pref[r]);
+        if (!LPP_IN_BOUNDS(j >= 0 && j < cap, a.err)) continue;
         const T ux = su[j], uy = su[cap + j], uz = su[2 * cap + j];
         T v0 = vals0[j], v1 = vals1[j];
         if (fixed) {
             v0 *= fs[0];
             v1 *= fs[1];
-            scatter_two<T, true>(t0, t1, LD, N, P, ux, uy, uz, sh0, y0, z0, TY, TZ, v0, v1, odd);
-            scatter_two<T, true>(t0, t1, LD, N, P, ux, uy, uz, sh1, y0, z0, TY, TZ, v0, v1, 1 - odd);
+            scatter_two<T, true>(t0, t1, LD, N, P, ux, uy, uz, sh0, y0, z0, TY, TZ, v0, v1, odd, a.err);
+            scatter_two<T, true>(t0, t1, LD, N, P, ux, uy, uz, sh1, y0, z0, TY, TZ, v0, v1, 1 - odd, a.err);
         } else {
-            scatter_two<T, false>(t0, t1, LD, N, P, ux, uy, uz, sh0, y0, z0, TY, TZ, v0, v1, odd);
-            scatter_two<T, false>(t0, t1, LD, N, P, ux, uy, uz, sh1, y0, z0, TY, TZ, v0, v1, 1 - odd);
+            scatter_two<T, false>(t0, t1, LD, N, P, ux, uy, uz, sh0, y0, z0, TY, TZ, v0, v1, odd, a.err);
+            scatter_two<T, false>(t0, t1, LD, N, P, ux, uy, uz, sh1, y0, z0, TY, TZ, v0, v1, 1 - odd, a.err);
         }
     }
     __syncthreads();

@@ -13,11 +13,13 @@ from dataclasses import dataclass, field
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "liblpp.so")
+# LPP_CHECK=1 in the environment selects the bounds-checking build (build.build(check=True))
+CHECK_LIB_PATH = os.path.join(_PKG, "liblpp_check.so")
+LIB_PATH = CHECK_LIB_PATH if os.environ.get("LPP_CHECK", "0") not in ("", "0") else os.path.join(_PKG, "liblpp.so")
 
 # ----------------------------------------------------------------- constants
 LPP_OK, LPP_ERR_INVALID_ARG, LPP_ERR_CUDA, LPP_ERR_NOT_READY, LPP_ERR_WORKSPACE, LPP_ERR_UNSUPPORTED, \
-    LPP_ERR_DOMAIN = range(7)
+    LPP_ERR_DOMAIN, LPP_ERR_BOUNDS = range(8)
 LPP_CIC, LPP_TSC = 2, 3
 LPP_FP32, LPP_FP64 = 0, 1
 LPP_LOS_LOCAL, LPP_LOS_GLOBAL = 0, 1
@@ -35,6 +37,7 @@ LPP_WANT_DD4 = 1 << LPP_MOM_DD4
 LPP_WANT_DENSITY = LPP_WANT_DD2 | LPP_WANT_DD4
 LPP_WANT_MINUS_HIGH = (1 << LPP_MOM_MINUS10) | (1 << LPP_MOM_MINUS12)
 TEMPLATE_EB_SLOTS = 0x3FE   # the template slots the derived E/B curves read
+GUARD_BYTES, GUARD_VALUE = 4096, 0xA5   # guard bands around a plan workspace that Plan allocates
 LPP_WANT_CROSS_B = 1 << 16
 KERNEL_KINDS = ["assign", "fft", "combine", "coeffs", "partner", "other"]
 
@@ -145,7 +148,7 @@ def load_library(path: str = LIB_PATH):
     if _lib is not None:
         return _lib
     if not os.path.exists(path):
-        raise ImportError(f"liblpp.so not built at {path}: run paper_2202_11839_gb300.build")
+        raise ImportError(f"{os.path.basename(path)} not built at {path}: run paper_2202_11839_gb300.build")
     lib = C.CDLL(path)
     for name, (res, args) in EXPORTS.items():
         fn = getattr(lib, name)
@@ -235,14 +238,32 @@ class Plan:
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         _check(self.lib, self.lib.lpp_plan_set_stream(h, C.c_void_p(self.stream.cuda_stream)), h)
+        self._guard = None
         if workspace is None:
-            workspace = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
-        addr = workspace.data_ptr()
-        off = (-addr) % 256
+            # own allocation: the workspace sits between two guard bands of a fixed byte pattern
+            # (GUARD_BYTES before, at least as many after) that guard_intact() checks
+            workspace = torch.empty(self.workspace_bytes + 256 + 2 * GUARD_BYTES, dtype=torch.uint8, device=self.device)
+            workspace.fill_(GUARD_VALUE)
+            addr = workspace.data_ptr()
+            off = (-(addr + GUARD_BYTES)) % 256 + GUARD_BYTES
+            self._guard = (off, off + self.workspace_bytes)
+        else:
+            addr = workspace.data_ptr()
+            off = (-addr) % 256
         self.workspace = workspace
-        _check(self.lib, self.lib.lpp_plan_set_workspace(h, C.c_void_p(addr + off),
-                                                         C.c_size_t(workspace.numel() - off)), h)
+        size = self.workspace_bytes if self._guard else workspace.numel() - off
+        _check(self.lib, self.lib.lpp_plan_set_workspace(h, C.c_void_p(addr + off), C.c_size_t(size)), h)
         self._keep = {}
+
+    def guard_intact(self) -> bool:
+        """True when the guard bands around a workspace this plan allocated still hold their
+        pattern (nothing of the library wrote outside its workspace); True for a caller's buffer."""
+        if self._guard is None:
+            return True
+        lo, hi = self._guard
+        self.torch.cuda.synchronize(self.device)
+        return bool((self.workspace[:lo] == GUARD_VALUE).all().item()) and \
+            bool((self.workspace[hi:] == GUARD_VALUE).all().item())
 
     def field_count(self) -> int:
         v = C.c_int()

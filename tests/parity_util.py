@@ -106,6 +106,7 @@ def run_gpu(cfg: dict, cat: dict, precision: int, device_inputs: bool = True):
         plan.assign(L.LPP_RANDOMS, conv(cat["rpos"]), conv(cat.get("rw")), conv(cat.get("rnbar")))
     est = plan.multipoles()
     est.extra["path"] = plan.path_stats()
+    assert plan.guard_intact(), "a kernel wrote outside the plan workspace"
     plan.close()
     return est
 
