@@ -328,10 +328,11 @@ lpp_status lpp_surrogate_set_workspace(lpp_surrogate_t net, void* device_ptr, si
 lpp_status lpp_surrogate_get_params(lpp_surrogate_t net, float* params, void* stream);
 /* Checkpoint of the training state: the Adam step counter, the FP32 master weights and biases
  * and both Adam moments (host buffer of lpp_surrogate_state_size bytes, caller-owned; a
- * 16-byte header with a magic number and a version, then the arrays).  save copies the state
- * out, load copies it in and rebuilds the BF16 copies, so training continues exactly where it
- * stopped.  Synchronous on `stream`; load returns LPP_ERR_INVALID_ARG for a buffer that is too
- * small or carries another magic number or version. */
+ * 32-byte header with a magic number, a version, the step and an FNV-1a 64-bit checksum of
+ * the arrays that follow).  save copies the state out, load copies it in and rebuilds the
+ * BF16 copies, so training continues where it stopped.  Synchronous on `stream`; load returns
+ * LPP_ERR_INVALID_ARG for a buffer that is too small, carries another magic number or version,
+ * or fails its checksum. */
 lpp_status lpp_surrogate_state_size(lpp_surrogate_t net, size_t* bytes);
 lpp_status lpp_surrogate_save_state(lpp_surrogate_t net, void* host, size_t bytes, void* stream);
 lpp_status lpp_surrogate_load_state(lpp_surrogate_t net, const void* host, size_t bytes, void* stream);

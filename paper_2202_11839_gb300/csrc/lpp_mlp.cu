@@ -462,14 +462,25 @@ extern "C" lpp_status lpp_surrogate_set_workspace(lpp_surrogate_t s, void* dev, 
     return LPP_OK;
 }
 
-// Training state (checkpoint): a 16-byte header (magic, version, Adam step), then per layer
-// the FP32 master W (rows padded to kInPad, the device layout), its Adam moments m and v, the
-// bias and its m and v.  The BF16 copies are derived and rebuilt on load.
+// Training state (checkpoint): a 32-byte header (magic, version, Adam step, FNV-1a 64-bit
+// checksum of the rest, 8 reserved bytes), then per layer the FP32 master W (rows padded to
+// kInPad, the device layout), its Adam moments m and v, the bias and its m and v.  The BF16
+// copies are derived and rebuilt on load.
 constexpr unsigned kStateMagic = 0x5350504Cu;   // "LPPS"
-constexpr unsigned kStateVersion = 1u;
+constexpr unsigned kStateVersion = 2u;
+constexpr size_t kStateHeader = 32;
+
+static unsigned long long fnv1a64(const unsigned char* p, size_t n) {
+    unsigned long long h = 1469598103934665603ull;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
 
 static size_t state_bytes() {
-    size_t b = 16;
+    size_t b = kStateHeader;
     for (int l = 0; l < kLayers; ++l) b += (size_t)3 * ((size_t)kOut[l] * kInPad[l] + kOut[l]) * 4;
     return b;
 }
@@ -502,7 +513,8 @@ extern "C" lpp_status lpp_surrogate_save_state(lpp_surrogate_t s, void* host, si
     memcpy(p, hdr, 8);
     const long long step = s->step;
     memcpy(p + 8, &step, 8);
-    size_t o = 16;
+    memset(p + 16, 0, 16);
+    size_t o = kStateHeader;
     std::vector<std::pair<size_t, size_t>> parts;
     state_parts(s, parts);
     for (const auto& q : parts) {
@@ -510,7 +522,10 @@ extern "C" lpp_status lpp_surrogate_save_state(lpp_surrogate_t s, void* host, si
             return LPP_ERR_CUDA;
         o += q.second;
     }
-    return cudaStreamSynchronize(st) == cudaSuccess ? LPP_OK : LPP_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return LPP_ERR_CUDA;
+    const unsigned long long sum = fnv1a64(p + kStateHeader, state_bytes() - kStateHeader);
+    memcpy(p + 16, &sum, 8);
+    return LPP_OK;
 }
 
 extern "C" lpp_status lpp_surrogate_load_state(lpp_surrogate_t s, const void* host, size_t bytes, void* stream) {
@@ -522,8 +537,11 @@ extern "C" lpp_status lpp_surrogate_load_state(lpp_surrogate_t s, const void* ho
     long long step = 0;
     memcpy(&step, p + 8, 8);
     if (step < 0) return LPP_ERR_INVALID_ARG;
+    unsigned long long sum = 0;
+    memcpy(&sum, p + 16, 8);
+    if (sum != fnv1a64(p + kStateHeader, state_bytes() - kStateHeader)) return LPP_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    size_t o = 16;
+    size_t o = kStateHeader;
     std::vector<std::pair<size_t, size_t>> parts;
     state_parts(s, parts);
     for (const auto& q : parts) {

@@ -146,7 +146,7 @@ def test_gaussian_sigma_matches_oracle():
 
 
 def test_surrogate_state_layout_on_host():
-    """The checkpoint size is the 16-byte header plus W (padded rows), b and both Adam moments
+    """The checkpoint size is the 32-byte header plus W (padded rows), b and both Adam moments
     of each layer in FP32; without a workspace there is no state to save or load."""
     L, lib = _lib()
     h = C.c_void_p()
@@ -155,7 +155,7 @@ def test_surrogate_state_layout_on_host():
     assert lib.lpp_surrogate_state_size(h, C.byref(sz)) == L.LPP_OK
     sizes = L.SURROGATE_SIZES
     pad = lambda k: (k + 15) // 16 * 16
-    want = 16 + sum(3 * (o * pad(i) + o) * 4 for i, o in zip(sizes[:-1], sizes[1:]))
+    want = 32 + sum(3 * (o * pad(i) + o) * 4 for i, o in zip(sizes[:-1], sizes[1:]))
     assert sz.value == want
     buf = (C.c_ubyte * sz.value)()
     assert lib.lpp_surrogate_save_state(h, buf, sz, None) == L.LPP_ERR_INVALID_ARG

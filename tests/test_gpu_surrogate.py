@@ -251,7 +251,7 @@ def test_emulator_accuracy_and_speed():
 def test_state_checkpoint_round_trip():
     """lpp_surrogate_save_state / load_state: a network loaded from a checkpoint continues the
     training as the saved one does (same Adam step count and moments), and a buffer with
-    another magic number is refused."""
+    another magic number, a short buffer or a flipped payload bit is refused."""
     import torch
     L, net, layers, x, y, t = _setup(batch=64, seed=3)
     rng = np.random.default_rng(12)
@@ -275,6 +275,10 @@ def test_state_checkpoint_round_trip():
         fresh.load_state(bad)
     with pytest.raises(L.LppError):
         fresh.load_state(state[:-4])
+    flipped = state.copy()
+    flipped[len(state) // 2] ^= 0x01   # one payload bit: the checksum refuses it
+    with pytest.raises(L.LppError):
+        fresh.load_state(flipped)
     for m in (net, other, fresh):
         m.close()
 
