@@ -78,7 +78,6 @@ struct lpp_plan_s {
     size_t off_work = 0;                 // item counter of the dynamically scheduled fused passes
     size_t off_pstat = 0;                // [4] tile counters of the fused passes (FusedArgs::pstat)
     size_t off_items = 0;                // the combine's work list
-    size_t off_wbound = 0;               // [3 roles][2] weight bounds (k_weight_bounds), FP32 plans
     int fty = 4, ftz = 4;
     int n_partner = 0;
     int out_rows = 0;
@@ -354,7 +353,6 @@ extern "C" lpp_status lpp_plan_create(const lpp_plan_desc* desc, lpp_plan_t* out
     plan->off_work = take(sizeof(int));
     plan->off_pstat = take(4 * sizeof(int));
     plan->off_items = take(std::max<size_t>(1, plan->items.size()) * sizeof(int4));
-    plan->off_wbound = take(6 * sizeof(unsigned));
     plan->off_wout = take((size_t)kWindowChannels * 256 * 2 * sizeof(double));
     plan->off_wthr = take(257 * sizeof(int));
     plan->off_partner = take((size_t)std::max(1, plan->n_partner) * n3 * cs);
@@ -854,19 +852,8 @@ static lpp_status enqueue(lpp_plan_t plan, double* host_out, double* host_sums, 
             dsl.n_src = 1;
             dsl.src[0] = FusedSrc{dens_cat, nullptr, 0};
             if (has_rand) dsl.src[dsl.n_src++] = FusedSrc{LPP_RANDOMS, nullptr, 1};
-            if (!plan->fp64) {
-                // weight bounds of the density field's catalogues: fixed-point tiles (FusedSlot::wb)
-                unsigned* wbd = (unsigned*)(plan->ws + plan->off_wbound);
-                const Catalogue& dc = plan->cat[dens_cat];
-                LPP_CUDA(launch_weight_bounds<T>((const T*)dc.w, dc.count, wbd + 2 * dens_cat, st));
-                nl += dc.count > 0 ? 1 : 0;
-                dsl.wb[0] = wbd + 2 * dens_cat;
-                if (has_rand) {
-                    LPP_CUDA(launch_weight_bounds<T>((const T*)ra.w, ra.count, wbd + 2 * LPP_RANDOMS, st));
-                    nl += ra.count > 0 ? 1 : 0;
-                    dsl.wb[1] = wbd + 2 * LPP_RANDOMS;
-                }
-            }
+            // the density field data - alpha randoms accumulates in float atomics: it nearly
+            // cancels over large scales, where a fixed-point quantum's rounding bias would show
             dsl.grid = pgrids++;
             fa.slots[fa.n_slots++] = dsl;
             parts += de.count + (has_rand ? ra.count : 0);

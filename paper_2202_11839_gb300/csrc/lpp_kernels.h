@@ -215,10 +215,6 @@ struct FusedSlot {
     // (integer shared-memory atomics) with a per-tile scale that no cell can overflow
     const float* amax_a;
     const float* amax_b;
-    // FP32 weight slots (the density field of the partner pass): per source, the bit patterns
-    // of max |w| and of the smallest nonzero |w| (k_weight_bounds); when set, a tile whose
-    // fixed-point unit passes the guard accumulates in 32-bit fixed point
-    const unsigned* wb[2];
 };
 template <typename T>
 struct FusedArgs {
@@ -267,10 +263,6 @@ cudaError_t launch_pencil_sort(const T* pos, const T* w, long long count, long l
                                T* su, T* sw, int* perm, int* err, cudaStream_t st);
 template <typename T>
 cudaError_t launch_assign_xfft(const FusedArgs<T>& a, cudaStream_t st);
-// out[0] = bits of max |w|, out[1] = bits of the smallest nonzero |w| over w[0 .. count) (w null:
-// every weight 1); out[1] stays 0x7f7f7f7f (a huge float) when every weight is zero
-template <typename T>
-cudaError_t launch_weight_bounds(const T* w, long long count, unsigned* out, cudaStream_t st);
 // Range records (particle ranges and fixed-point bound) of every tile of the two-slot
 // persistent enumeration over a.trows, for the sources of a.slots[0]; FP32, n = 256 or 512.
 // out: tile_range_bytes(n, ty, tz) bytes.  One launch.

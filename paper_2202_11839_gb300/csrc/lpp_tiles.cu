@@ -341,8 +341,7 @@ __device__ __forceinline__ void fill_twr(const c2<T>* tw, c2<T>* twr, int first,
 template <typename T, int LOGN>
 __device__ __forceinline__ void warp_ranges(const FusedArgs<T>& a, const FusedSlot& sl, int y0, int z0, int lane,
                                             int* r_begin, int* r_pref, int* r_src, int& n_ranges,
-                                            int (*rcount)[FusedShape<T, LOGN>::TY + 3], int& wmax, bool want_wmax,
-                                            int* wmax1 = nullptr) {
+                                            int (*rcount)[FusedShape<T, LOGN>::TY + 3], int& wmax, bool want_wmax) {
     using S = FusedShape<T, LOGN>;
     constexpr int N = S::N, TY = S::TY, TZ = S::TZ;
     int bb[2] = {0, 0}, ee[2] = {0, 0}, m = 0, s_idx = 0;
@@ -380,14 +379,11 @@ __device__ __forceinline__ void warp_ranges(const FusedArgs<T>& a, const FusedSl
         r_pref[nr_inc] = cnt_inc;
         n_ranges = nr_inc;
     }
-    // a cell (y, z) of the tile receives only from the key rows y-2..y+1, z-2..z+1: the
-    // largest such 4 x 4 window sum bounds the contributions of any one cell (source 0, and
-    // with wmax1 source 1 as well)
-    const int n_bound = want_wmax ? ((wmax1 && sl.n_src > 1) ? 2 : 1) : 0;
-    for (int sb = 0; sb < n_bound; ++sb) {
-        if (sb) __syncwarp();   // rcount is reused
+    if (want_wmax) {
+        // a cell (y, z) of the tile receives only from the key rows y-2..y+1, z-2..z+1:
+        // the largest such 4 x 4 window sum bounds the contributions of any one cell
         if (lane < TZ + 3) {
-            const int* off = a.cat[sl.src[sb].cat].off;
+            const int* off = a.cat[sl.src[0].cat].off;
             const int zr = (z0 - 2 + lane) & (N - 1);
 #pragma unroll
             for (int dy = 0; dy < TY + 3; ++dy) {
@@ -406,9 +402,7 @@ __device__ __forceinline__ void warp_ranges(const FusedArgs<T>& a, const FusedSl
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) wsum = max(wsum, __shfl_down_sync(0xffffffffu, wsum, o));
-        if (lane == 0) {
-            if (sb) *wmax1 = wsum; else wmax = wsum;
-        }
+        if (lane == 0) wmax = wsum;
     }
 }
 
@@ -419,7 +413,7 @@ template <typename T, int LOGN, int NT>
 __device__ __forceinline__ void tile_setup(const FusedArgs<T>& a, const FusedSlot& sl, int y0, int z0, c2<T>* tw,
                                            c2<T>* twr, c2<T>* tiles, int tile_elems, int* r_begin, int* r_pref,
                                            int* r_src, int& n_ranges, int (*rcount)[FusedShape<T, LOGN>::TY + 3],
-                                           int& wmax, int* wmax1 = nullptr) {
+                                           int& wmax) {
     using S = FusedShape<T, LOGN>;
     constexpr int N = S::N, TY = S::TY, TZ = S::TZ;
     const int tid = threadIdx.x;
@@ -450,13 +444,12 @@ __device__ __forceinline__ void tile_setup(const FusedArgs<T>& a, const FusedSlo
             r_pref[nr] = acc;
             n_ranges = nr;
             wmax = acc;   // every particle of the tile: a looser but valid per-cell bound
-            if (wmax1) *wmax1 = acc;
         }
         for (int i = tid; i < N; i += NT) tw[i] = a.tw[i];
         for (int i = tid; i < tile_elems; i += NT) tiles[i] = mk<T>((T)0, (T)0);
     } else if (tid < 32) {
         warp_ranges<T, LOGN>(a, sl, y0, z0, tid, r_begin, r_pref, r_src, n_ranges, rcount, wmax,
-                             sl.amax_a != nullptr || sl.wb[0] != nullptr, wmax1);
+                             sl.amax_a != nullptr);
     } else {
         for (int i = tid - 32; i < N; i += NT - 32) tw[i] = a.tw[i];
         fill_twr<T, LOGN>(a.tw, twr, tid - 32, NT - 32);
@@ -542,7 +535,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int slot, int 
     __shared__ int n_ranges;
     // particles per key row around the tile (fixed-point bound; rows of source 0)
     __shared__ int rcount[TZ + 3][TY + 3];
-    __shared__ int wmax, wmax1;
+    __shared__ int wmax;
     c2<T>* tw = reinterpret_cast<c2<T>*>(smem_raw);
     c2<T>* tile = tw + N;
     c2<T>* twr = tile + N * LD;
@@ -554,7 +547,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int slot, int 
     c2<T>* out = a.grids + (size_t)sl.grid * a.grid_stride + ((size_t)z0 * N + y0) * N;
 
     tile_setup<T, LOGN, S::THREADS>(a, sl, y0, z0, tw, twr, tile, N * LD, r_begin, r_pref, r_src, n_ranges, rcount,
-                                    wmax, &wmax1);
+                                    wmax);
     __syncthreads();
     const int nr = n_ranges;
     if (!LPP_IN_BOUNDS(nr >= 0 && nr <= S::MAXR && tile_y >= 0 && tile_y < N / TY && tile_z >= 0 && tile_z < N / TZ,
@@ -608,26 +601,6 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T>& a, int slot, int 
         if (bound == 0.f) {
             fixed = true;                        // every value is zero
         } else if (bound * (1.f / 1073741824.f) <= rms * (1.f / 65536.f)) {
-            fixed = true;
-            fscale = 1073741824.f / bound;
-            finv = bound / 1073741824.f;
-        }
-        if (a.pstat && tid == 0) atomicAdd(a.pstat + (fixed ? 2 : 3), 1);
-    } else if (sizeof(T) == 4 && sl.wb[0] != nullptr) {
-        // weight slots: a cell sums at most wmax_q contributions of source q, each at most
-        // max |w_q| (times alpha for the randoms); the guard compares the unit with the smallest
-        // nonzero contribution scale, so one heavy weight cannot make the unit coarse for the rest
-        float bound = 0.f, small = 3.0e38f, big = 0.f;
-        for (int q = 0; q < sl.n_src && q < 2; ++q) {
-            const float sc = sl.src[q].neg_alpha ? fabsf((float)alpha) : 1.f;
-            bound += (float)(q == 0 ? wmax : wmax1) * __uint_as_float(sl.wb[q][0]) * sc;
-            small = fminf(small, __uint_as_float(sl.wb[q][1]) * sc);
-            big = fmaxf(big, __uint_as_float(sl.wb[q][0]) * sc);
-        }
-        bound = fmaxf(bound, (float)kMinWindow * big);   // every contribution within 2^21 units
-        if (bound == 0.f) {
-            fixed = true;
-        } else if (bound * (1.f / 1073741824.f) <= small * (1.f / 65536.f)) {
             fixed = true;
             fscale = 1073741824.f / bound;
             finv = bound / 1073741824.f;
@@ -1028,40 +1001,6 @@ __global__ void __launch_bounds__(256) k_tile_rows(const int* __restrict__ pmask
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_weight_bounds(const T* __restrict__ w, long long count,
-                                                      unsigned* __restrict__ out) {
-    unsigned mx = 0u, mn = 0x7f7f7f7fu;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
-         i += (long long)gridDim.x * blockDim.x) {
-        const float v = fabsf(w ? (float)w[i] : 1.f);
-        const unsigned b = __float_as_uint(v);   // nonnegative floats order as their bit patterns
-        mx = max(mx, b);
-        if (v > 0.f) mn = min(mn, b);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
-        mn = min(mn, __shfl_down_sync(0xffffffffu, mn, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicMax(out, mx);
-        atomicMin(out + 1, mn);
-    }
-}
-
-template <typename T>
-cudaError_t launch_weight_bounds(const T* w, long long count, unsigned* out, cudaStream_t st) {
-    // out[0] = 0 (max), out[1] = 0x7f7f7f7f (min, about 3.4e38 as a float)
-    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(out + 1, 0x7f, sizeof(unsigned), st);
-    if (e != cudaSuccess) return e;
-    if (count <= 0) return cudaSuccess;
-    long long blocks = (count + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    k_weight_bounds<T><<<(int)blocks, 256, 0, st>>>(w, count, out);
-    return cudaGetLastError();
-}
-
-template <typename T>
 cudaError_t launch_tile_ranges(const FusedArgs<T>& a, int* out, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
         if (a.trows == nullptr || a.trow_count == nullptr) return cudaErrorInvalidValue;
@@ -1148,8 +1087,6 @@ template cudaError_t launch_pencil_sort<double>(const double*, const double*, lo
 template cudaError_t launch_tile_ranges<float>(const FusedArgs<float>&, int*, cudaStream_t);
 template cudaError_t launch_tile_ranges<double>(const FusedArgs<double>&, int*, cudaStream_t);
 template cudaError_t launch_assign_xfft<float>(const FusedArgs<float>&, cudaStream_t);
-template cudaError_t launch_weight_bounds<float>(const float*, long long, unsigned*, cudaStream_t);
-template cudaError_t launch_weight_bounds<double>(const double*, long long, unsigned*, cudaStream_t);
 template cudaError_t launch_assign_xfft<double>(const FusedArgs<double>&, cudaStream_t);
 
 }  // namespace lpp
