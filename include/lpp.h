@@ -264,9 +264,10 @@ lpp_status lpp_batch_launch_count(lpp_batch_t batch, long long* counted, long lo
 /* ------------------------------------------------------------------ templates
  * Window-convolved theory templates (Sec. 3.2, Eqs. window_convolution_X_hankel and
  * def_of_Q_llp; Appendix D): for every parameter set (A, b_g, sigma_8, tilt, Gamma,
- * shot-noise scale) the twelve native moment slots (the estimator's order; the density
- * quadrupole and hexadecapole are the leakage of the monopole through the window, the
- * mixtures Q^dd_20 = Q_2 and Q^dd_40 = Q_4 of Sec. 4.3)
+ * shot-noise scale) the LPP_N_MOMENTS native moment slots (the estimator's order; the
+ * density quadrupole and hexadecapole are the leakage of the monopole through the window,
+ * the mixtures Q^dd_20 = Q_2 and Q^dd_40 = Q_4 of Sec. 4.3, and the minus moments L = 10, 12
+ * the leakage of the minus hexadecapole through Q_6 and Q_8)
  *   Pt^(L)_X(k) = H_L[ sum_L' Q^X_LL'(r) xi^(L')_X(r) ](k),  xi^(L')_X = H^-1_L'[P^(L')_X],
  * of the tidal-alignment model (shapes e = -A T_ij, galaxies b_g delta; Eq.
  * power_for_validation scaled): P_dd^(0) = b^2 P, P_gd^(2) = -A b P / 6,
