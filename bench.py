@@ -254,17 +254,37 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------- GPU arm
-def template_leg(plan, est, wl, dev):
-    """Window-convolved templates for the survey: Q_l(s) from its randoms, then templates/s of
-    the FFTLog path and of the trained surrogate (20k Latin-hypercube training templates),
-    and the surrogate's error on 2k held-out parameter sets in Gaussian error bars."""
+def padded_window(wl, d_pos, d_rpos, d_rnbar, dev, s_edges):
+    """Q_l(s) of the survey's randoms on a grid of twice the box, shifted by half a box, so that
+    no separation up to the last shell wraps around (the estimate's own grid is periodic with
+    the survey's box, shorter than its extent plus 3800 Mpc/h): 512^3 over 8000 Mpc/h
+    (h = 15.6 Mpc/h).  The data catalogue is assigned for alpha (the normalisation I)."""
+    from paper_2202_11839_gb300 import lpp as L
+    origin = tuple(o - wl.box / 2 for o in wl.origin)
+    wp = L.Plan(wl.n, 2 * wl.box, np.linspace(0.0, 0.01, 2), origin=origin, observer=wl.observer, pole=wl.pole,
+                scheme=L.LPP_TSC, interlace=False, compensate=True, precision=L.LPP_FP32,
+                moments=1 << L.LPP_MOM_DD0, max_density=int(d_pos.shape[1]), max_randoms=int(d_rpos.shape[1]),
+                device=dev)
+    wp.assign(L.LPP_DENSITY, d_pos)
+    wp.assign(L.LPP_RANDOMS, d_rpos, None, d_rnbar)
+    out = wp.window_q(s_edges)
+    wp.close()
+    return out
+
+
+def template_leg(plan, est, wl, dev, d_pos, d_rpos, d_rnbar):
+    """Window-convolved templates for the survey: Q_l(s) from its randoms (on a padded grid),
+    then templates/s of the FFTLog path and of the trained surrogate (20k Latin-hypercube
+    training templates), and the surrogate's error on 2k held-out parameter sets in Gaussian
+    error bars."""
     import torch
 
     from paper_2202_11839_gb300 import lpp as L
     from paper_2202_11839_gb300 import surrogate as SG
     from paper_2202_11839_gb300 import synthetic as S
     s_edges = np.linspace(0.0, 3800.0, 191)
-    q, s_mean, npts, _ = plan.window_q(s_edges)
+    q, s_mean, npts, _ = padded_window(wl, d_pos, d_rpos, d_rnbar, dev, s_edges)
+    torch.cuda.empty_cache()
     keep = npts > 0
     tm = L.Template(q[:, keep], s_mean[keep], wl.k_edges, shot_plus=est.shot_plus, stream=plan.stream, device=dev)
     em = SG.Emulator(tm, SG.survey_volume(), est.shot_dd)
@@ -290,7 +310,8 @@ def template_leg(plan, est, wl, dev):
            "baseline_only_sigma": {"rms": rep.baseline_rms_sigma, "max": rep.baseline_max_sigma},
            "n_train": em.cfg.n_train, "n_test": em.cfg.n_test, "train_s": rep.train_seconds,
            "data_s": rep.data_seconds, "outputs": "gE_0,2 EE_0,2,4 BB_0,2,4 x 40 shells",
-           "window": "Q_l(s) of the survey randoms on the same grid", "dtype": "bf16 network, f64 FFTLog"}
+           "window": "Q_l(s) of the survey randoms, 512^3 over a padded 8000 Mpc/h box (no wrap-around)",
+           "dtype": "bf16 network, f64 FFTLog"}
     net.close()
     em.net.close()
     tm.close()
@@ -464,7 +485,7 @@ def run_lpp(args):
 
     templates = None
     if rank == 0 and not args.no_surrogate:
-        templates = template_leg(plan, est, wl, dev)
+        templates = template_leg(plan, est, wl, dev, d_pos, d_rpos, d_rnbar)
     precision = None
     if rank == 0 and not args.no_fp64:
         precision = precision_leg(wl, est, common, dev)
@@ -514,11 +535,25 @@ def run_lpp(args):
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     default_cfg = (args.n == 512 and args.data == 1_500_000 and args.randoms == 15_000_000 and args.batch == 0
                    and args.moment_mask < 0)
+    tr = {}
     if default_cfg and os.path.exists(prof):
         with open(prof) as f:
             tr = json.load(f)
         if tr.get("workload") == wl.name:
             traffic = tr.get("kernels", {}).get(dom, {}).get("bytes_per_launch")
+    # the same roofline figures for every kernel kind (the two largest, the fused assignment
+    # and the passes, take nearly equal time, so the dominant one can change between runs)
+    kinds_roof = {}
+    for k, v in stats.items():
+        if k == "other" or v["launches"] == 0 or v["ms"] <= 0:
+            continue
+        t_s = v["ms"] / v["launches"] / 1000.0
+        b_l = v["bytes"] / v["launches"]
+        tk = None
+        if tr.get("workload") == wl.name:
+            tk = tr.get("kernels", {}).get(k, {}).get("bytes_per_launch")
+        kinds_roof[k] = {"achieved": round(b_l / t_s / 1e9, 1), "frac": round(b_l / t_s / 1e9 / hbm, 4),
+                         "bytes_per_launch": b_l, "avg_launch_ms": round(t_s * 1000.0, 4), "traffic": tk}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -529,7 +564,8 @@ def run_lpp(args):
                    "l2": "inputs larger than L2 (each grid 1 GiB)", "parallelism": f"replicas{world}"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_source": peak_src, "traffic": traffic,
-                     "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_s * 1000.0},
+                     "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_s * 1000.0,
+                     "kinds": kinds_roof},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,

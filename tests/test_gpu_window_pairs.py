@@ -85,3 +85,24 @@ def test_pair_count_agrees_with_fft_window_on_a_cap():
     plan.close()
     np.testing.assert_allclose(qp[0], qf[0], rtol=0.03, atol=0.01 * np.abs(qf[0]).max())
     np.testing.assert_allclose(qp[1], qf[1], rtol=0.1, atol=0.03 * np.abs(qf[0]).max())
+
+
+def test_padded_fft_window_agrees_with_pair_counts_at_large_separations():
+    """The FFT window on a grid twice the survey box (origin moved by half a box, as the
+    benchmark computes its template window) has no wrap-around: it agrees with the pair count
+    out to 3500 Mpc/h, beyond the survey box's half size (the cap spans about 3100 Mpc/h)."""
+    import torch
+    L = _L()
+    obs = (2000.0, 2000.0, 200.0)
+    _, rand = S.survey_mock(10, 60000, 32, 4000.0, S.bbks_pk(0.2, 0.8), 1.0, 0.25, 9, obs, dtype=np.float64)
+    edges = np.linspace(100.0, 3500.0, 35)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    qp = L.window_q_pairs(t(rand.pos), None, t(rand.nbar), obs, edges, alpha=1.0)
+    plan = L.Plan(256, 8000.0, np.linspace(0, 0.1, 3), origin=(-2000.0, -2000.0, -2000.0), observer=obs,
+                  scheme=L.LPP_TSC, compensate=True, precision=L.LPP_FP64, moments=1, max_shapes=1,
+                  max_randoms=rand.pos.shape[1])
+    plan.assign(L.LPP_RANDOMS, t(rand.pos), None, t(rand.nbar))
+    qf, _, _, _ = plan.window_q(edges)
+    plan.close()
+    np.testing.assert_allclose(qp[0], qf[0], rtol=0.03, atol=0.01 * np.abs(qf[0]).max())
+    np.testing.assert_allclose(qp[1], qf[1], rtol=0.1, atol=0.03 * np.abs(qf[0]).max())
