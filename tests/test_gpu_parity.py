@@ -196,6 +196,83 @@ def test_on_node_512_matches_direct_sum(L):
         assert np.max(np.abs(got - want) / (np.abs(want) + ref_scale)) < TOL32, (kind, Lm)
 
 
+def test_on_node_1024_matches_direct_sum(L):
+    """The largest grid the library takes, 1024^3 (its own pass shapes: 8-pencil y/z tiles, a
+    1024-point x transform of 2 x 8 x 8 x 8 in the fused kernel), particles on nodes, CIC, no
+    deconvolution: the lowest shells equal the direct per-mode sums to FP32 rounding."""
+    n, box = 1024, 8000.0
+    rng = np.random.default_rng(13)
+    cnt = 300
+    cells = rng.integers(0, n, (3, cnt))
+    h = box / n
+    pos = (cells * h).astype(np.float32)
+    shape = rng.standard_normal((6, cnt)).astype(np.float32)
+    w = rng.uniform(0.5, 1.5, cnt).astype(np.float32)
+    edges = np.array([0.0, 0.002, 0.0035, 0.005])
+    obs = (4000.0, 4000.0, -500.0)
+    moments = (1 << L.LPP_MOM_DD0) | (1 << L.LPP_MOM_CROSS2) | (1 << L.LPP_MOM_PLUS2) | (1 << L.LPP_MOM_MINUS4)
+    cfg = dict(n=n, box=box, observer=obs, scheme=2, interlace=False, compensate=False, k_edges=edges,
+               norm_override=1.0, subtract_shot=False, cross_b=True, gpu_moments=moments, batch=2)
+    gpu = U.run_gpu(cfg, dict(pos=pos, w=w, shape=shape), L.LPP_FP32)
+    kf = 2 * math.pi / box
+    m = int(edges[-1] / kf) + 1
+    f = np.arange(-m, m + 1)
+    fx, fy, fz = np.meshgrid(f, f, f, indexing="ij")
+    q = (fx ** 2 + fy ** 2 + fz ** 2).ravel()
+    kint = np.stack([fx.ravel(), fy.ravel(), fz.ravel()], 1)
+    kmag = kf * np.sqrt(q)
+    b = np.searchsorted(edges, kmag, side="right") - 1
+    sel = (q > 0) & (b >= 0) & (b < len(edges) - 1)
+    kint, b = kint[sel], b[sel]
+    kvec = kint * kf
+    khat = kint / np.linalg.norm(kint, axis=1)[:, None]
+    p64 = pos.astype(np.float64)
+    xh = O.line_of_sight(p64, obs)
+    et, ep = O.sky_frame(xh, (-1, 0, 0))
+    g = O.shear(shape.astype(np.float64), None, O.helicity_tensor(et, ep))
+    w64 = w.astype(np.float64)
+    D = O.direct_ft(kvec, p64, np.broadcast_to(w64, (len(kvec), cnt)))
+    G = O.direct_ft(kvec, p64, np.broadcast_to(w64 * g, (len(kvec), cnt)))
+    Gc = O.direct_ft(kvec, p64, np.broadcast_to(w64 * np.conj(g), (len(kvec), cnt)))
+    nmodes = np.bincount(b, minlength=3)
+    np.testing.assert_array_equal(gpu.n_modes, nmodes)
+    shell = lambda v: (np.bincount(b, weights=v.real, minlength=3) + 1j * np.bincount(b, weights=v.imag, minlength=3)) / nmodes
+    ref_scale = np.sqrt(shell(np.abs(G) ** 2).real * shell(np.abs(D) ** 2).real)
+    want_dd = shell(np.abs(D) ** 2)
+    assert np.max(np.abs(gpu.p[L.LPP_MOM_DD0] - want_dd) / np.abs(want_dd)) < TOL32
+    partner = {"cross": np.conj(D), "plus": np.conj(G), "minus": np.conj(Gc)}
+    for (kind, Lm) in [("cross", 2), ("plus", 2), ("minus", 4)]:
+        F = O.direct_ft(kvec, p64, w64[None, :] * O.direct_kernel(kind, Lm, khat, xh, et, ep, g))
+        fac = O.norm_factor({"cross": 2, "plus": 0, "minus": 4}[kind], Lm)
+        want = fac * shell(F * partner[kind])
+        got = gpu.p[L.MOMENT_NAMES.index(f"{kind}{Lm}")]
+        assert np.max(np.abs(got - want) / (np.abs(want) + ref_scale)) < TOL32, (kind, Lm)
+
+
+def test_empty_shape_catalogue(L):
+    """No shape galaxies (count 0) beside a density catalogue and randoms: every tensor slot
+    is exactly zero (their normalisation has no weight), nothing is NaN, and the density
+    monopole equals the one of the same density and randoms with shapes present."""
+    cfg, ck = CASES64["tsc_interlaced_randoms_density"]
+    cat = U.make_case("empty", cfg["n"], seed=4, box=cfg["box"], dtype=np.float64, **ck)
+    full = U.run_gpu(cfg, cat, L.LPP_FP64)
+    empty = dict(cat, pos=cat["pos"][:, :0].copy(), w=cat["w"][:0].copy(), shape=cat["shape"][:, :0].copy())
+    import torch
+    plan = L.Plan(cfg["n"], cfg["box"], cfg["k_edges"], observer=cfg["observer"], scheme=cfg["scheme"],
+                  interlace=cfg["interlace"], precision=L.LPP_FP64, moments=L.LPP_WANT_ALL | L.LPP_WANT_CROSS_B,
+                  max_shapes=cat["pos"].shape[1], max_density=cat["dpos"].shape[1], max_randoms=cat["rpos"].shape[1])
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    plan.assign(L.LPP_SHAPES, t(empty["pos"]), t(empty["w"]), None, t(empty["shape"]), L.LPP_SHAPE_TENSOR6)
+    plan.assign(L.LPP_DENSITY, t(cat["dpos"]), t(cat["dw"]))
+    plan.assign(L.LPP_RANDOMS, t(cat["rpos"]), t(cat["rw"]), t(cat["rnbar"]))
+    est = plan.multipoles()
+    plan.close()
+    assert np.all(np.isfinite(est.p)) and np.all(np.isfinite(est.raw))
+    for s in range(1, 10):
+        assert np.all(est.p[s] == 0), L.MOMENT_NAMES[s]
+    np.testing.assert_allclose(est.p[L.LPP_MOM_DD0], full.p[L.LPP_MOM_DD0], rtol=1e-12, atol=0)
+
+
 @pytest.mark.parametrize("cross_b", [True, False])
 def test_fp32_interlaced_256_matches_fp64(L, cross_b):
     """256^3, TSC + interlacing, catalogue confined in y and z: the FP32 path (two slots per
