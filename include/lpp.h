@@ -364,7 +364,10 @@ lpp_status lpp_surrogate_infer(lpp_surrogate_t net, const float* x, int n, float
  * mu, sd, shot (= s) are device FP64 [320]; base device FP64 [nodes^2][320]; ref and sigma
  * device FP64 [320] or NULL (0, 1) standardise the prediction as (t - ref) / sigma, as
  * lpp_convolve_template_eb does.  The pointers are borrowed and must outlive the surrogate's
- * use of them.  nodes in 2..8. */
+ * use of them; the first lpp_surrogate_predict after lpp_surrogate_set_map copies base into
+ * the surrogate's workspace as float pairs (hi + lo) for the decoding, which sums the
+ * baseline in float-float arithmetic (the FP64 sum to about 2^-44 relative), so a changed
+ * base needs lpp_surrogate_set_map again.  nodes in 2..8. */
 typedef struct {
     double lo[6], hi[6];
     int feed[6];

@@ -264,6 +264,11 @@ struct MapArgs {
     const double* base;               // [nodes^2][320] or null
     int nodes, base_in[2];
     double N[2][3], M[3][3];          // native moments -> derived multipoles
+    // the decoding's copy of base as float pairs (hi + lo = base to 2^-48), and the Lobatto
+    // nodes with the Lagrange normalisations 1 / prod_{j != i} (x_i - x_j), for k_decode
+    const float* base_hi;
+    const float* base_lo;
+    double xs[kMaxNodes], cw[kMaxNodes];
 };
 
 __global__ void k_encode(const double* __restrict__ theta, int n, float* __restrict__ x, MapArgs m) {
@@ -285,6 +290,27 @@ __device__ void lobatto_basis(double x, int n, double* l) {
     }
 }
 
+// The same Lagrange basis from the map's nodes and normalisations: products only.
+__device__ __forceinline__ void lobatto_basis_fast(double x, const MapArgs& a, double* l) {
+    for (int i = 0; i < a.nodes; ++i) {
+        double v = a.cw[i];
+        for (int j = 0; j < a.nodes; ++j)
+            if (j != i) v *= x - a.xs[j];
+        l[i] = v;
+    }
+}
+
+// base -> (hi, lo) float pairs, hi = rn(b), lo = rn(b - hi)
+__global__ void k_split_base(const double* __restrict__ base, int count, float* __restrict__ hi,
+                             float* __restrict__ lo) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const double b = base[i];
+        const float h = (float)b;
+        hi[i] = h;
+        lo[i] = (float)(b - (double)h);
+    }
+}
+
 // baseline mu_j + sum_ab l_a(x_p) l_b(x_q) base[a n + b][j] for one parameter row
 __device__ double baseline(const MapArgs& a, const double* t, int j) {
     double u = a.mu[j];
@@ -300,12 +326,15 @@ __device__ double baseline(const MapArgs& a, const double* t, int j) {
 
 // network outputs y [m][320] -> standardised curves (pre_c (baseline + sd y) + theta_5 s - ref) / sigma.
 // One CTA of kNout threads per parameter row at a time: the row's Lagrange weights
-// l_a(x_p) l_b(x_q) are formed once in shared memory, then thread j sums its baseline output
-// (the same terms in the same order as baseline()).
+// l_a(x_p) l_b(x_q) are formed once in FP64 in shared memory and split into float pairs; thread
+// j sums its baseline output in float-float arithmetic (error-free products and sums, Dekker
+// and Knuth): the FP64 sum of baseline() to about 2^-44 relative, on the FP32 pipes (GB300
+// runs FP64 at a small fraction of the FP32 rate).
 __global__ void __launch_bounds__(kNout) k_decode(const double* __restrict__ theta, int m, const float* __restrict__ y,
                                                   float* __restrict__ out, MapArgs a) {
     constexpr int nb = kNout / 8;
-    __shared__ double la[kMaxNodes], lb[kMaxNodes], wab[kMaxNodes * kMaxNodes];
+    __shared__ double la[kMaxNodes], lb[kMaxNodes];
+    __shared__ float whi[kMaxNodes * kMaxNodes], wlo[kMaxNodes * kMaxNodes];
     const int j = threadIdx.x;
     const int nn = a.base ? a.nodes * a.nodes : 0;
     for (int r = blockIdx.x; r < m; r += gridDim.x) {
@@ -313,14 +342,33 @@ __global__ void __launch_bounds__(kNout) k_decode(const double* __restrict__ the
         if (a.base) {
             if (j < 2) {
                 const int c = a.base_in[j];
-                lobatto_basis(t[c] * a.dscale[c] + a.dshift[c], a.nodes, j == 0 ? la : lb);
+                lobatto_basis_fast(t[c] * a.dscale[c] + a.dshift[c], a, j == 0 ? la : lb);
             }
             __syncthreads();
-            for (int q = j; q < nn; q += blockDim.x) wab[q] = la[q / a.nodes] * lb[q % a.nodes];
+            for (int q = j; q < nn; q += blockDim.x) {
+                const double w = la[q / a.nodes] * lb[q % a.nodes];
+                const float h = (float)w;
+                whi[q] = h;
+                wlo[q] = (float)(w - (double)h);
+            }
             __syncthreads();
         }
-        double u = a.mu[j];
-        for (int q = 0; q < nn; ++q) u += wab[q] * a.base[(size_t)q * kNout + j];
+        float s_hi = 0.f, s_lo = 0.f;
+        for (int q = 0; q < nn; ++q) {
+            const float bh = a.base_hi[(size_t)q * kNout + j], bl = a.base_lo[(size_t)q * kNout + j];
+            const float wh = whi[q], wl = wlo[q];
+            // the _rn intrinsics are never contracted into FMAs, which the exact
+            // transformations need
+            const float p = __fmul_rn(wh, bh);
+            float e = fmaf(wh, bh, -p);              // wh bh = p + e exactly
+            e += fmaf(wh, bl, wl * bh);              // the cross terms (wl bl is below 2^-48)
+            const float s = __fadd_rn(s_hi, p);      // s_hi + p = s + err exactly
+            const float bb = __fsub_rn(s, s_hi);
+            const float err = __fadd_rn(__fsub_rn(s_hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+            s_hi = s;
+            s_lo += err + e;
+        }
+        double u = a.mu[j] + ((double)s_hi + (double)s_lo);
         const size_t i = (size_t)r * kNout + j;
         const double amp = t[2] * t[2] * ((j / nb) < 2 ? t[0] * t[1] : t[0] * t[0]);
         double v = amp * (u + a.sd[j] * (double)y[i]) + t[5] * a.shot[j];
@@ -364,7 +412,9 @@ struct lpp_surrogate_s {
     size_t w[kLayers], b[kLayers], mw[kLayers], vw[kLayers], mb[kLayers], vb[kLayers], dw[kLayers], db[kLayers];
     size_t w16[kLayers], w16t[kLayers], act[kLayers + 1], actt[kLayers], z[kLayers];
     size_t g32[2], g16[2], g16t[2], loss, xin;
+    size_t base_hi, base_lo;          // the decoding's float-pair copy of the map's base
     bool has_map = false;
+    bool base_split = false;          // base_hi/base_lo hold the current map's base
     MapArgs map;
 };
 
@@ -398,6 +448,8 @@ extern "C" lpp_status lpp_surrogate_create(int batch, lpp_surrogate_t* out) {
     }
     s->loss = take(8);
     s->xin = take((size_t)batch * kNin * 4);
+    s->base_hi = take((size_t)kMaxNodes * kMaxNodes * kNout * 4);
+    s->base_lo = take((size_t)kMaxNodes * kMaxNodes * kNout * 4);
     s->need = off;
     *out = s;
     return LPP_OK;
@@ -644,6 +696,14 @@ extern "C" lpp_status lpp_surrogate_set_map(lpp_surrogate_t s, const lpp_surroga
         a.nodes = m->base_nodes;
         a.base_in[0] = m->base_in[0];
         a.base_in[1] = m->base_in[1];
+        const double pi = 3.14159265358979323846;
+        for (int i = 0; i < a.nodes; ++i) a.xs[i] = -cos(pi * i / (a.nodes - 1));
+        for (int i = 0; i < a.nodes; ++i) {
+            double d = 1.0;
+            for (int k = 0; k < a.nodes; ++k)
+                if (k != i) d *= a.xs[i] - a.xs[k];
+            a.cw[i] = 1.0 / d;
+        }
     }
     a.mu = m->mu;
     a.sd = m->sd;
@@ -653,6 +713,7 @@ extern "C" lpp_status lpp_surrogate_set_map(lpp_surrogate_t s, const lpp_surroga
     lpp::eb_matrices(a.N, a.M);
     s->map = a;
     s->has_map = true;
+    s->base_split = false;
     return LPP_OK;
 }
 
@@ -677,6 +738,17 @@ extern "C" lpp_status lpp_surrogate_predict(lpp_surrogate_t s, const double* the
     if (!s || !s->ws || !s->has_map || n < 0 || (n > 0 && (!theta || !out))) return LPP_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     float* x = (float*)(s->ws + s->xin);
+    if (s->map.base) {
+        s->map.base_hi = (const float*)(s->ws + s->base_hi);
+        s->map.base_lo = (const float*)(s->ws + s->base_lo);
+        if (!s->base_split) {
+            const int count = s->map.nodes * s->map.nodes * kNout;
+            k_split_base<<<(count + 255) / 256, 256, 0, st>>>(s->map.base, count, (float*)(s->ws + s->base_hi),
+                                                             (float*)(s->ws + s->base_lo));
+            if (cudaGetLastError() != cudaSuccess) return LPP_ERR_CUDA;
+            s->base_split = true;
+        }
+    }
     for (int r0 = 0; r0 < n; r0 += s->batch) {
         const int m = n - r0 < s->batch ? n - r0 : s->batch;
         const double* th = theta + (size_t)r0 * kNin;

@@ -308,3 +308,48 @@ def test_emulator_training_resumes_from_a_checkpoint(tmp_path):
         if e.net is not None:
             e.net.close()
     tm.close()
+
+
+def test_predict_baseline_matches_fp64_decoding():
+    """With an 8 x 8 Lobatto baseline: lpp_surrogate_predict (the baseline summed in
+    float-float arithmetic on the FP32 pipes) against the same decoding in FP64 on the host.
+    The base is 1e5 plus O(1) values and mu = -1e5 (the Lagrange weights sum to 1), so the
+    baseline cancels to O(1): a plain FP32 sum would be off by about 1e-2 there, the float-float
+    sum agrees to the FP32 rounding of the stored prediction.  A second set_map with another
+    base is picked up."""
+    import torch
+    from paper_2202_11839_gb300 import lpp as L
+    L.load_library()
+    net = L.Surrogate(L.flatten_params(S.surrogate_init(5)), batch=64)
+    rng = np.random.default_rng(21)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    nodes = 8
+    mu, sd, shot = -1e5 + rng.standard_normal(320), rng.uniform(0.5, 2.0, 320), rng.uniform(0, 5, 320)
+    sig = rng.uniform(1.0, 3.0, 320)
+    lo, hi = S.SURROGATE_RANGES[:, 0], S.SURROGATE_RANGES[:, 1]
+    feed = (0, 0, 0, 1, 1, 0)
+    theta = S.latin_hypercube(150, seed=6)
+    th = dev(theta)
+    xs = -np.cos(np.pi * np.arange(nodes) / (nodes - 1))
+
+    def lag(v):
+        return np.array([np.prod([(v - xs[j]) / (xs[i] - xs[j]) for j in range(nodes) if j != i])
+                         for i in range(nodes)])
+
+    x = 2 * (theta - lo) / (hi - lo) - 1
+    A, b, s8, sh = theta[:, 0:1], theta[:, 1:2], theta[:, 2:3], theta[:, 5:6]
+    pre = np.concatenate([np.repeat(A * b * s8 ** 2, 80, 1), np.repeat(A * A * s8 ** 2, 240, 1)], axis=1)
+    for seed in (1, 2):
+        base = 1e5 + np.random.default_rng(seed).standard_normal((nodes * nodes, 320))
+        keep = [dev(mu), dev(sd), dev(shot), dev(sig), dev(base.reshape(-1))]
+        net.set_map(lo, hi, feed, keep[0], keep[1], keep[2], None, keep[3], base=keep[4], base_nodes=nodes,
+                    base_in=(3, 4))
+        xin = net.encode(th)
+        y = net.infer(xin).double().cpu().numpy()
+        got = net.predict(th).double().cpu().numpy()
+        bl = np.stack([np.einsum("a,b,abj->j", lag(x[r, 3]), lag(x[r, 4]), base.reshape(nodes, nodes, 320))
+                       for r in range(len(theta))])
+        want = (pre * (mu + bl + sd * y) + sh * shot) / sig
+        # the prediction is stored in FP32: compare to its rounding
+        assert np.max(np.abs(got - want) / (np.abs(want) + 1.0)) < 1e-5, (seed, np.max(np.abs(got - want)))
+    net.close()
