@@ -325,57 +325,75 @@ __device__ double baseline(const MapArgs& a, const double* t, int j) {
 }
 
 // network outputs y [m][320] -> standardised curves (pre_c (baseline + sd y) + theta_5 s - ref) / sigma.
-// One CTA of kNout threads per parameter row at a time: the row's Lagrange weights
+// One CTA of kNout threads per kDecodeRows parameter rows at a time: the rows' Lagrange weights
 // l_a(x_p) l_b(x_q) are formed once in FP64 in shared memory and split into float pairs; thread
-// j sums its baseline output in float-float arithmetic (error-free products and sums, Dekker
-// and Knuth): the FP64 sum of baseline() to about 2^-44 relative, on the FP32 pipes (GB300
-// runs FP64 at a small fraction of the FP32 rate).
+// j loads its base column once for the rows and sums each row's baseline output in float-float
+// arithmetic (error-free products and sums, Dekker and Knuth): the FP64 sum of baseline() to
+// about 2^-44 relative, on the FP32 pipes (GB300 runs FP64 at a small fraction of the FP32 rate).
+constexpr int kDecodeRows = 4;
 __global__ void __launch_bounds__(kNout) k_decode(const double* __restrict__ theta, int m, const float* __restrict__ y,
                                                   float* __restrict__ out, MapArgs a) {
-    constexpr int nb = kNout / 8;
-    __shared__ double la[kMaxNodes], lb[kMaxNodes];
-    __shared__ float whi[kMaxNodes * kMaxNodes], wlo[kMaxNodes * kMaxNodes];
+    constexpr int nb = kNout / 8, R = kDecodeRows;
+    __shared__ double la[R][kMaxNodes], lb[R][kMaxNodes];
+    __shared__ float whi[R][kMaxNodes * kMaxNodes], wlo[R][kMaxNodes * kMaxNodes];
     const int j = threadIdx.x;
     const int nn = a.base ? a.nodes * a.nodes : 0;
-    for (int r = blockIdx.x; r < m; r += gridDim.x) {
-        const double* t = theta + (size_t)r * kNin;
+    for (int r0 = blockIdx.x * R; r0 < m; r0 += gridDim.x * R) {
+        const int nr = m - r0 < R ? m - r0 : R;
         if (a.base) {
-            if (j < 2) {
-                const int c = a.base_in[j];
-                lobatto_basis_fast(t[c] * a.dscale[c] + a.dshift[c], a, j == 0 ? la : lb);
+            if (j < 2 * R && (j >> 1) < nr) {
+                const int rr = j >> 1, c = a.base_in[j & 1];
+                const double* t = theta + (size_t)(r0 + rr) * kNin;
+                lobatto_basis_fast(t[c] * a.dscale[c] + a.dshift[c], a, (j & 1) ? lb[rr] : la[rr]);
             }
             __syncthreads();
-            for (int q = j; q < nn; q += blockDim.x) {
-                const double w = la[q / a.nodes] * lb[q % a.nodes];
-                const float h = (float)w;
-                whi[q] = h;
-                wlo[q] = (float)(w - (double)h);
+            for (int q = j; q < R * nn; q += blockDim.x) {
+                const int rr = q / nn, qq = q - rr * nn;
+                float h = 0.f, l = 0.f;
+                if (rr < nr) {
+                    const double w = la[rr][qq / a.nodes] * lb[rr][qq % a.nodes];
+                    h = (float)w;
+                    l = (float)(w - (double)h);
+                }
+                whi[rr][qq] = h;
+                wlo[rr][qq] = l;
             }
             __syncthreads();
         }
-        float s_hi = 0.f, s_lo = 0.f;
+        float s_hi[R], s_lo[R];
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) s_hi[rr] = s_lo[rr] = 0.f;
         for (int q = 0; q < nn; ++q) {
             const float bh = a.base_hi[(size_t)q * kNout + j], bl = a.base_lo[(size_t)q * kNout + j];
-            const float wh = whi[q], wl = wlo[q];
-            // the _rn intrinsics are never contracted into FMAs, which the exact
-            // transformations need
-            const float p = __fmul_rn(wh, bh);
-            float e = fmaf(wh, bh, -p);              // wh bh = p + e exactly
-            e += fmaf(wh, bl, wl * bh);              // the cross terms (wl bl is below 2^-48)
-            const float s = __fadd_rn(s_hi, p);      // s_hi + p = s + err exactly
-            const float bb = __fsub_rn(s, s_hi);
-            const float err = __fadd_rn(__fsub_rn(s_hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-            s_hi = s;
-            s_lo += err + e;
+#pragma unroll
+            for (int rr = 0; rr < R; ++rr) {
+                const float wh = whi[rr][q], wl = wlo[rr][q];
+                // the _rn intrinsics are never contracted into FMAs, which the exact
+                // transformations need
+                const float p = __fmul_rn(wh, bh);
+                float e = fmaf(wh, bh, -p);              // wh bh = p + e exactly
+                e += fmaf(wh, bl, wl * bh);              // the cross terms (wl bl is below 2^-48)
+                const float s = __fadd_rn(s_hi[rr], p);  // s_hi + p = s + err exactly
+                const float bb = __fsub_rn(s, s_hi[rr]);
+                const float err = __fadd_rn(__fsub_rn(s_hi[rr], __fsub_rn(s, bb)), __fsub_rn(p, bb));
+                s_hi[rr] = s;
+                s_lo[rr] += err + e;
+            }
         }
-        double u = a.mu[j] + ((double)s_hi + (double)s_lo);
-        const size_t i = (size_t)r * kNout + j;
-        const double amp = t[2] * t[2] * ((j / nb) < 2 ? t[0] * t[1] : t[0] * t[0]);
-        double v = amp * (u + a.sd[j] * (double)y[i]) + t[5] * a.shot[j];
-        if (a.ref) v -= a.ref[j];
-        if (a.sigma) v /= a.sigma[j];
-        out[i] = (float)v;
-        __syncthreads();   // la, lb, wab are rewritten for the next row
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) {
+            if (rr >= nr) break;
+            const int r = r0 + rr;
+            const double* t = theta + (size_t)r * kNin;
+            const double u = a.mu[j] + ((double)s_hi[rr] + (double)s_lo[rr]);
+            const size_t i = (size_t)r * kNout + j;
+            const double amp = t[2] * t[2] * ((j / nb) < 2 ? t[0] * t[1] : t[0] * t[0]);
+            double v = amp * (u + a.sd[j] * (double)y[i]) + t[5] * a.shot[j];
+            if (a.ref) v -= a.ref[j];
+            if (a.sigma) v /= a.sigma[j];
+            out[i] = (float)v;
+        }
+        __syncthreads();   // la, lb, whi, wlo are rewritten for the next rows
     }
 }
 
@@ -758,7 +776,8 @@ extern "C" lpp_status lpp_surrogate_predict(lpp_surrogate_t s, const double* the
         {
             int dev = 0, sms = 152;
             if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            const int blocks = m < sms * 6 ? (m > 0 ? m : 1) : sms * 6;
+            const int groups = (m + kDecodeRows - 1) / kDecodeRows;
+            const int blocks = groups < sms * 6 ? (groups > 0 ? groups : 1) : sms * 6;
             k_decode<<<blocks, kNout, 0, st>>>(th, m, y, y, s->map);
         }
     }
