@@ -17,7 +17,9 @@ compile time.)
 """
 from __future__ import annotations
 
+import json
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -117,10 +119,45 @@ class Tuning:
     ms: dict = field(default_factory=dict)      # "grids/slots" -> ms per estimate
 
 
-def autotune(mock: Mock, candidates=(4, 6, 8, 16), slot_modes=(0, 1), repeats: int = 2) -> Tuning:
+def _cache_key(mock: Mock, candidates, slot_modes) -> str:
+    """The tuning's identity: the grid, the sample's size to two significant digits, the
+    searched shapes and the device."""
+    import torch
+    dev = torch.cuda.get_device_name(mock.pos.device) if torch.cuda.is_available() else "cpu"
+    count = float(f"{mock.count:.2g}")
+    return json.dumps([mock.n, count, list(candidates), list(slot_modes), dev])
+
+
+def autotune(mock: Mock, candidates=(4, 6, 8, 16), slot_modes=(0, 1), repeats: int = 2,
+             cache: str | None = None, tuner=None) -> Tuning:
     """Plan shape for the mock's grid size: grids per pass x the fused pass's channel fields per
     CTA (library choice, or always one), the combination with the shortest estimate, timed by
-    the library's own kernel timers on the sample mock."""
+    the library's own kernel timers on the sample mock.  cache (default: the LPP_AUTOTUNE_CACHE
+    environment variable) names a JSON file of earlier tunings: a tuning found there for the
+    same key (_cache_key) is returned without timing, a new one is added to it.  tuner: the
+    timing function (default _tune)."""
+    cache = cache if cache is not None else os.environ.get("LPP_AUTOTUNE_CACHE") or None
+    tuner = tuner or _tune
+    if cache is None:
+        return tuner(mock, candidates, slot_modes, repeats)
+    key = _cache_key(mock, candidates, slot_modes)
+    table = {}
+    if os.path.exists(cache):
+        with open(cache) as f:
+            table = json.load(f)
+    if key in table:
+        t = table[key]
+        return Tuning(mock.n, int(t["batch"]), int(t["fused_slots"]), dict(t.get("ms", {})))
+    res = tuner(mock, candidates, slot_modes, repeats)
+    table[key] = {"batch": res.batch, "fused_slots": res.fused_slots, "ms": res.ms}
+    tmp = cache + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(table, f, indent=1)
+    os.replace(tmp, cache)
+    return res
+
+
+def _tune(mock: Mock, candidates, slot_modes, repeats: int) -> Tuning:
     import torch
     res = Tuning(mock.n, candidates[0])
     best = None
@@ -184,3 +221,51 @@ class BatchRun:
     def close(self):
         self.batch.close()
         self.plans.clear()
+
+
+# ------------------------------------------------------------------ persisted results
+def _result_name(mock: Mock) -> str:
+    return f"mock_{mock.seed}_n{mock.n}_c{mock.count}.npz"
+
+
+def save_estimate(path: str, est: L.Estimate):
+    """One mock's estimate (FP64 rows, shells and normalisations) to an .npz file, written to
+    a temporary name and moved into place, so a file that exists is complete."""
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, p=est.p, raw=est.raw, k_mean=est.k_mean, n_modes=est.n_modes,
+             scalars=np.array([est.norm_auto, est.norm_cross, est.norm_dd, est.shot_plus, est.shot_dd, est.alpha]))
+    os.replace(tmp, path)
+
+
+def load_estimate(path: str) -> L.Estimate:
+    with np.load(path) as z:
+        sc = z["scalars"]
+        return L.Estimate(z["p"], z["raw"], z["k_mean"], z["n_modes"], *[float(v) for v in sc])
+
+
+def run_resumable(mocks, tuning: dict, out_dir: str, chunk: int = 16, slots_per_grid: dict | None = None,
+                  use_graph: bool = True, runner=None):
+    """The estimates of every mock (in the order of mocks), persisted per mock in out_dir as they
+    complete: mocks whose result file exists are read back instead of run (a rerun after an
+    interruption skips the finished seeds); the others run in batches of `chunk` mocks (one
+    lpp_batch launch each), and each batch's results are written before the next starts, so an
+    interruption loses at most one batch.  runner(mocks) -> estimates replaces the batch
+    executor (default: BatchRun with the tuning)."""
+    os.makedirs(out_dir, exist_ok=True)
+
+    def default_runner(ms):
+        run = BatchRun(ms, tuning, slots_per_grid, use_graph=use_graph)
+        try:
+            return run.run()
+        finally:
+            run.close()
+
+    runner = runner or default_runner
+    paths = [os.path.join(out_dir, _result_name(m)) for m in mocks]
+    todo = [j for j, p in enumerate(paths) if not os.path.exists(p)]
+    for c0 in range(0, len(todo), max(1, chunk)):
+        part = todo[c0:c0 + max(1, chunk)]
+        ests = runner([mocks[j] for j in part])
+        for j, est in zip(part, ests):
+            save_estimate(paths[j], est)
+    return [load_estimate(p) for p in paths]

@@ -179,8 +179,8 @@ def _ptr(a):
 
 @dataclass
 class Estimate:
-    p: np.ndarray          # (10, nb) complex, normalised
-    raw: np.ndarray        # (10, nb) complex
+    p: np.ndarray          # (LPP_N_MOMENTS, nb) complex, normalised
+    raw: np.ndarray        # (LPP_N_MOMENTS, nb) complex
     k_mean: np.ndarray
     n_modes: np.ndarray
     norm_auto: float
@@ -254,6 +254,8 @@ class Plan:
         size = self.workspace_bytes if self._guard else workspace.numel() - off
         _check(self.lib, self.lib.lpp_plan_set_workspace(h, C.c_void_p(addr + off), C.c_size_t(size)), h)
         self._keep = {}
+        if os.environ.get("LPP_TIMING", "0") not in ("", "0"):
+            self.set_timing(True)   # per-kernel CUDA-event timers from the start (kernel_stats)
 
     def guard_intact(self) -> bool:
         """True when the guard bands around a workspace this plan allocated still hold their

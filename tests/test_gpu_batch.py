@@ -123,3 +123,20 @@ def test_batch_bad_arguments():
     bad = (C.c_int * 1)(3)
     assert lib.lpp_batch_create(one, 1, bad, parts, None, 1, 1, C.byref(h)) == L.LPP_ERR_INVALID_ARG
     assert lib.lpp_batch_launch(None, None) == L.LPP_ERR_INVALID_ARG
+
+
+def test_resumable_batch_matches_one_batch(tmp_path):
+    """run_resumable (batches of two mocks, each result written as its batch completes) gives
+    the estimates of one batch over all mocks; a rerun reads the files back."""
+    from paper_2202_11839_gb300 import batch as B
+    mocks = _mocks(5)
+    tuning = {32: B.Tuning(32, 8), 64: B.Tuning(64, 8)}
+    run = B.BatchRun(mocks, tuning)
+    whole = run.run()
+    run.close()
+    out = str(tmp_path / "res")
+    parts = B.run_resumable(mocks, tuning, out, chunk=2)
+    again = B.run_resumable(mocks, tuning, out, chunk=2, runner=lambda ms: pytest.fail("nothing to rerun"))
+    for a, b, c in zip(whole, parts, again):
+        assert _close(b, a, 1e-5)
+        np.testing.assert_array_equal(b.p, c.p)
