@@ -132,3 +132,44 @@ def test_two_gloo_ranks_gather_the_whole_estimate(moments):
     assert any(mask == 0 for _, mask, *_ in out) == (world == 3)
     for rank, mask, p_ok, n_ok, meta_ok in out:
         assert p_ok and n_ok and meta_ok, rank
+
+
+def _dropout_rank(rank, world, port, q):
+    """Rank 1 leaves between steps (after joining the group, before the exchange); rank 0's
+    gather must end with an error, not wait for it."""
+    import datetime
+    import time
+
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        os._exit(0)
+    L, SH = _sh()
+    nb = 4
+    zero = np.zeros((L.LPP_N_MOMENTS, nb), dtype=np.complex128)
+    est = L.Estimate(zero, zero.copy(), np.zeros(nb), np.zeros(nb, dtype=np.int64), 1.0, 1.0, 1.0, 0.0, 0.0, 0.0)
+    t0 = time.time()
+    try:
+        SH.gather(est, L.LPP_WANT_ALL, dist, "cpu")
+        q.put(("no error", time.time() - t0))
+    except Exception as e:   # the peer is gone: the collective fails
+        q.put((type(e).__name__, time.time() - t0))
+    os._exit(0)
+
+
+def test_a_rank_that_leaves_ends_the_exchange_with_an_error():
+    """Failure detection on the host: one of two gloo ranks exits without joining the
+    exchange of a sharded estimate; the other's gather raises within the group's timeout
+    (10 s) instead of hanging."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dropout_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    kind, elapsed = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert kind != "no error", kind
+    assert elapsed < 60.0, elapsed
