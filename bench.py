@@ -29,6 +29,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "LPP tensor-multipole estimates/sec at 512^3; templates/sec surrogate vs plain"
+# instruction issue peak of the GB300: 152 SMs x 4 warp schedulers x 1 warp instruction per
+# cycle x 2070 MHz (the maximum SM clock)
+ISSUE_PEAK_WARP_INSTR_S = 152 * 4 * 1.0 * 2070e6
 UNIT = "estimates/s"
 
 
@@ -554,6 +557,15 @@ def run_lpp(args):
             tk = tr.get("kernels", {}).get(k, {}).get("bytes_per_launch")
         kinds_roof[k] = {"achieved": round(b_l / t_s / 1e9, 1), "frac": round(b_l / t_s / 1e9 / hbm, 4),
                          "bytes_per_launch": b_l, "avg_launch_ms": round(t_s * 1000.0, 4), "traffic": tk}
+        # issue-rate roofline of the instruction-bound kinds: warp instructions per launch (ncu,
+        # profiles/traffic.json) over the launch's event time, against 152 SMs x 4 schedulers x
+        # one warp instruction per cycle at the maximum SM clock
+        wi = tr.get("kernels", {}).get(k, {}).get("warp_instructions_per_launch") if tr.get("workload") == wl.name else None
+        if wi:
+            peak_issue = ISSUE_PEAK_WARP_INSTR_S
+            kinds_roof[k]["issue"] = {"achieved": round(wi / t_s / 1e12, 4), "peak": round(peak_issue / 1e12, 4),
+                                      "unit": "T warp-instr/s", "frac": round(wi / t_s / peak_issue, 4),
+                                      "warp_instructions_per_launch": wi}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
