@@ -183,12 +183,23 @@ __global__ void k_loss(const float* __restrict__ out, const float* __restrict__ 
 }
 
 // db[n] = sum over rows of g[m][n]
-__global__ void k_bias_grad(const float* __restrict__ g, int m, int n, float* db) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
+// db[c] = sum_r g[r][c]: 32 columns per CTA (a warp reads 32 consecutive columns of a row),
+// eight warps each over every eighth row, then the eight partial sums in a fixed order
+__global__ void __launch_bounds__(256) k_bias_grad(const float* __restrict__ g, int m, int n, float* db) {
+    __shared__ float part[8][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
     float s = 0.f;
-    for (int r = 0; r < m; ++r) s += g[(size_t)r * n + c];
-    db[c] = s;
+    if (c < n)
+        for (int r = w; r < m; r += 8) s += g[(size_t)r * n + c];
+    part[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && c < n) {
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t += part[k][lane];
+        db[c] = t;
+    }
 }
 
 struct AdamLayer {
@@ -810,7 +821,7 @@ static cudaError_t train_step(lpp_surrogate_t s, const float* x, const float* y,
         gw.z = (float*)(s->ws + s->dw[l]);
         gw.ldz = kInPad[l];
         if ((e = gemm(gw, st)) != cudaSuccess) return e;
-        k_bias_grad<<<(kOut[l] + 127) / 128, 128, 0, st>>>((const float*)(s->ws + s->g32[cur]), B, kOut[l],
+        k_bias_grad<<<(kOut[l] + 31) / 32, 256, 0, st>>>((const float*)(s->ws + s->g32[cur]), B, kOut[l],
                                                            (float*)(s->ws + s->db[l]));
         if (l > 0) {
             // g_{l-1} = (g_l W_l) * GELU'(z_{l-1}) : [B x inp] = [B x out] . [inp x out]^T
